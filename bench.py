@@ -1,0 +1,357 @@
+"""Benchmark of the AS-ICP hot path (one grasp set = one step).
+
+A step is one full AS-ICP optimisation of one object: Fibonacci initial poses,
+k_max iterations of transform / matching / cost+gradient / collision / SVGD or
+SGD update for every preshape and particle, the final evaluation and the
+ranking, then the top-k read-back (asicp_run + asicp_best_grasps).
+
+Default workload: 3 preshapes x 256 particles, gripper contact cloud of 2048
+points, 8192-point single-view partial object clouds of seeded procedural
+shapes, 64^3 SDF grids, 100 iterations (38 SVGD + 62 SGD).  The metric is
+forward matching throughput in particle*point pairs per second
+(P * K * N * M pairs per iteration, k_max + 1 evaluations per step) plus the
+milliseconds per grasp set.
+
+N > 1 GPUs (torchrun): every rank optimises its own object (weak scaling, no
+data-path collective); the step time is the maximum over ranks.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (a few particles of one iteration per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_NOMINAL = 2070.0
+OPS_PER_PAIR = 4          # algorithmic FP32-pipe work per particle*point pair (3 FFMA + 1 min)
+TOPK = 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="asicp", choices=["asicp", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work for the oracle sample")
+    ap.add_argument("--small", action="store_true", help="small workload (debugging only)")
+    return ap.parse_args()
+
+
+def workload(rank: int, small: bool):
+    from paper_2412_08346_gb300 import synth
+    if small:
+        return synth.custom_case(P=3, K=64, N=512, M=2048, grid=32, k_max=20, seed=synth.BASE_SEED + 2)
+    w = synth.paper_scale_case(seed=synth.BASE_SEED + 2)
+    if rank:
+        w.objects = [synth.partial_object(8192, synth.BASE_SEED + 2 + 1000 * (rank + 1))]
+    return w
+
+
+def pairs_per_step(w) -> int:
+    P, N, M = len(w.preshapes), w.preshapes[0].S.shape[0], len(w.objects[0].points)
+    return P * w.K * N * M * (w.k_max + 1)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clocks, power, throttle reasons)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(w, seconds: float, nthreads: int, max_iters: int | None = None):
+    """Time the FP64 oracle on a bounded sample: a few particles per preshape for one iteration at
+    a time (the first SVGD iteration's work: matching, cost/gradient and collision for every pair)."""
+    import oracle
+    P, N, M = len(w.preshapes), w.preshapes[0].S.shape[0], len(w.objects[0].points)
+    Ks = max(1, min(w.K, nthreads))
+    orc = oracle.Oracle(np.stack([p.S for p in w.preshapes]), [(p.sdf, p.origin, p.voxel) for p in w.preshapes],
+                        w.objects[0].points, K=Ks)
+    th = np.tile(oracle.fibonacci_init(Ks, orc.R.mean(0), 0.15), (P, 1))
+    sched = orc.schedule(k_max=w.k_max, k_stein=w.k_stein, schedule=w.schedule, N=N)
+    st = orc.new_state(th[None].reshape(P, Ks, 7))
+    pairs = 0
+    iters = 0
+    t0 = time.perf_counter()
+    while True:
+        orc.step(st, sched, iters % w.k_max, nthreads)
+        pairs += P * Ks * N * M
+        iters += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_iters and iters >= max_iters):
+            break
+    return pairs / el, {"particles_per_preshape": Ks, "iterations": iters, "seconds": el, "pairs": pairs}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = workload(0, args.small)
+    nthreads = os.cpu_count() or 1
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
+    for _ in range(args.warmup):
+        oracle_sample(w, 0.0, nthreads, max_iters=1)
+    vals, secs, total_pairs = [], 0.0, 0
+    for _ in range(args.steps):
+        v, info = oracle_sample(w, per_step, nthreads)
+        vals.append(v)
+        secs += info["seconds"]
+        total_pairs += info["pairs"]
+    value = total_pairs / secs
+    sample = (f"{info['particles_per_preshape']} particles per preshape x {len(w.preshapes)} preshapes, "
+              f"whole iterations (N={w.preshapes[0].S.shape[0]}, M={len(w.objects[0].points)}), "
+              f"~{per_step:.0f} s per step")
+    line = {"impl": "reference", "metric": "AS-ICP particle*point pairs/s (forward matching)", "value": value,
+            "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": nthreads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2412_08346_gb300 import asicp
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    w = workload(rank, args.small)
+    P, K, N, M = len(w.preshapes), w.K, w.preshapes[0].S.shape[0], len(w.objects[0].points)
+    cfg = asicp.asicp_config_default(P=P, K=K, k_max=w.k_max, k_stein=w.k_stein, schedule=w.schedule,
+                                     profile=1, cuda_stream=stream.cuda_stream)
+    ctx = asicp.asicp_create(cfg)
+    obj = w.objects[0].points
+    R_dev = torch.from_numpy(obj).to(dev)
+    pre_dev = [(torch.from_numpy(p.S).to(dev), torch.from_numpy(p.sdf).to(dev)) for p in w.preshapes]
+    asicp.asicp_set_object(ctx, R_dev)
+    for p, (S, g) in enumerate(pre_dev):
+        asicp.asicp_set_gripper_sdf(ctx, p, S, g, w.preshapes[p].origin, w.preshapes[p].voxel)
+    best = np.zeros(TOPK * 7, np.float32)
+    best_c = np.zeros(TOPK, np.float32)
+    best_p = np.zeros(TOPK, np.int32)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+
+    def one_step():
+        asicp.asicp_run(ctx)
+        asicp.asicp_best_grasps(ctx, TOPK, best, best_c, best_p)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    asicp.asicp_kernel_times(ctx, reset=True)
+
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()                     # L2 flush between timed steps, outside the timed interval
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one_step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms, launches = asicp.asicp_kernel_times(ctx, reset=True)
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    pairs = pairs_per_step(w)
+    value = pairs * args.steps * world / (max_ms / 1e3)
+
+    # dominant kernel: forward matching; algorithmic work per launch = P*K*N*M pairs
+    match_avg_s = ms[0] / max(1, launches[0]) / 1e3
+    pairs_per_launch = P * K * N * M
+    achieved = pairs_per_launch / match_avg_s / 1e9
+    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / OPS_PER_PAIR / 1e9
+    launches_per_step = 4 * (w.k_max + 1) + 4   # match, collide, collide_nn, update per pass + init/reset/select/gather
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(args, ctx, w, stream, best, best_c, best_p, world, dev)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        nthreads = os.cpu_count() or 1
+        v, info = oracle_sample(w, args.cpu_seconds, nthreads)
+        cpu = {"value": v, "unit": "pairs/s", "cores": nthreads, "kind": "oracle",
+               "sample": (f"FP64 oracle, {info['particles_per_preshape']} particles per preshape x {P} preshapes, "
+                          f"{info['iterations']} whole iterations (N={N}, M={M}), {info['seconds']:.1f} s")}
+    asicp.asicp_destroy(ctx)
+    if rank == 0:
+        line = {
+            "metric": "AS-ICP particle*point pairs/s (forward matching) and ms per grasp set",
+            "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "P": P, "K": K, "N": N, "M": M,
+                       "sdf": int(w.preshapes[0].sdf.shape[0]), "iterations": w.k_max, "k_stein": w.k_stein,
+                       "pairs_per_step": pairs, "l2": "flushed between steps (512 MB write)",
+                       "parallelism": f"replicas x{world} (one object per GPU)"},
+            "ms_per_grasp_set": max_ms / args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpairs/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "fwd_match_kernel", "peak_basis":
+                             f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz / "
+                             f"{OPS_PER_PAIR} ops per pair",
+                         "launch_ms": match_avg_s * 1e3,
+                         "kernel_share": ms[0] / max(1e-9, sum(ms))},
+            "kernel_ms_per_step": {k: v / args.steps for k, v in
+                                   zip(("match", "collide", "collide_nn", "update"), ms)},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+        }
+        if e2e:
+            line["e2e"] = e2e
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+
+
+def measure_e2e(args, ctx, w, stream, best, best_c, best_p, world, dev):
+    """Same metric through the public API with host inputs: every step uploads the object, the
+    preshape clouds and SDFs from pinned host memory and reads the top-k back."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2412_08346_gb300 import asicp
+    R_h = torch.from_numpy(w.objects[0].points).pin_memory()
+    pre_h = [(torch.from_numpy(p.S).pin_memory(), torch.from_numpy(p.sdf).pin_memory()) for p in w.preshapes]
+    out7 = torch.zeros(TOPK * 7, dtype=torch.float32).pin_memory()
+    outc = torch.zeros(TOPK, dtype=torch.float32).pin_memory()
+    outp = torch.zeros(TOPK, dtype=torch.int32).pin_memory()
+    h2d = R_h.numel() * 4 + sum(S.numel() * 4 + g.numel() * 4 for S, g in pre_h)
+    d2h = TOPK * (7 * 4 + 4 + 4)
+
+    def one():
+        asicp.asicp_set_object(ctx, R_h)
+        for p, (S, g) in enumerate(pre_h):
+            asicp.asicp_set_gripper_sdf(ctx, p, S, g, w.preshapes[p].origin, w.preshapes[p].voxel)
+        asicp.asicp_run(ctx)
+        asicp.asicp_best_grasps(ctx, TOPK, out7, outc, outp)
+
+    for _ in range(max(1, args.warmup)):
+        one()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    t = torch.tensor([el], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    el = float(t.item())
+    return {"value": pairs_per_step(w) * args.steps * world / el, "unit": "pairs/s",
+            "ms_per_step": 1e3 * el / args.steps, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * libasicp: GB300 (sm_103a) implementation of the data-parallel hot path of
+ * Annealed Stein ICP (AS-ICP) grasp matching, from "Grasping by Parallel Shape
+ * Matching" (arXiv 2412.08346).  For every gripper preshape and every pose
+ * particle it transforms the gripper contact cloud, finds nearest-neighbour
+ * correspondences in the object cloud, evaluates the cost and gradient of the
+ * paper's loss (matching term, TCP-CoM term, SDF collision term) and applies
+ * the annealed SVGD / SGD-ICP update (Algorithm 1).
+ *
+ * Conventions for every call below
+ *  - Units are metres in the object frame (Section IV-A).  A pose is
+ *    theta = (t_x, t_y, t_z, q_w, q_x, q_y, q_z): a translation and a unit
+ *    quaternion, scalar first (Section III-A).  Point arrays are packed xyz
+ *    float32 triples, row-major.
+ *  - Input and output arrays may live in host memory (pageable or pinned) or in
+ *    device memory of the context's GPU; the library tells them apart through
+ *    unified addressing.  The caller keeps ownership; the library copies what it
+ *    keeps, so an input may be freed or reused as soon as the call returns.
+ *  - All device work is issued on asicp_config.cuda_stream (NULL: the legacy
+ *    default stream).  Calls that produce host-visible results
+ *    (asicp_best_grasps, asicp_get_state, asicp_kernel_times) and the input
+ *    calls that validate their data (asicp_set_object, asicp_set_gripper_sdf)
+ *    synchronise that stream; asicp_step and asicp_run only enqueue work.
+ *  - Errors are returned as asicp_status; no C++ exception crosses this
+ *    boundary.  A failing call leaves the context valid and records a message
+ *    readable with asicp_last_error.  A context is not thread-safe: use one
+ *    context per host thread.
+ */
+#ifndef ASICP_H
+#define ASICP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct asicp_ctx asicp_ctx;
+
+typedef enum {
+    ASICP_OK = 0,
+    ASICP_ERR_INVALID_ARG = 1, /* bad pointer, size, index or non-finite input value      */
+    ASICP_ERR_STATE = 2,       /* call order: e.g. asicp_step before the inputs are set   */
+    ASICP_ERR_CUDA = 3,        /* a CUDA runtime call or a kernel launch failed            */
+    ASICP_ERR_OOM = 4,         /* device or host allocation failed                         */
+    ASICP_ERR_TIMEOUT = 5      /* a bounded device-side wait expired                       */
+} asicp_status;
+
+/* Parameters of Algorithm 1.  asicp_config_default fills Table I's values and the
+ * readings the paper leaves open:
+ *   P, K          preshapes and particles per preshape (K <= 1024)
+ *   k_max, k_stein total iterations and SVGD iterations (Algorithm 1; Table I
+ *                  gives 15 SVGD + 25 SGD, default k_stein = round(0.375 k_max))
+ *   schedule      0: cyclic annealing gamma = (mod(k, k_max/C) / (k_max/C))^p
+ *                  (Eq. 11, Table I: C = 5, p = 2); 1: linear g0 -> g1
+ *   eta_sgd       SGD-ICP learning rate (Eq. 3, Table I: 1); the preconditioner A is I
+ *   eta_svgd      SVGD step (Eq. 7); <= 0 selects 1/N
+ *   w_com         weight of the TCP-CoM term inside the 1/N of Eqs. 16-17 (Table I: 1)
+ *   bandwidth_mode 0: median heuristic h = med_{i<j}|t_i - t_j|^2 / ln K; 1: h_fixed (Eq. 9)
+ *   conv_tol      relative cost change that freezes a particle in the SGD phase
+ *                  (Section IV-D, Table I: 0.02 %); < 0 disables freezing
+ *   init_radius   radius of the Fibonacci-sphere initial poses around the CoM (Section V)
+ *   debug         1: keep per-query correspondences, transformed points and collision
+ *                  lists so asicp_get_state can return them (costs memory and bandwidth)
+ *   profile       1: time the main kernels with CUDA events (asicp_kernel_times)
+ *   cuda_stream   cudaStream_t for all work, NULL for the default stream            */
+typedef struct {
+    int P, K;
+    int k_max, k_stein;
+    int schedule;
+    float C_cycles, p_exp, g0, g1;
+    float eta_sgd, eta_svgd;
+    float w_com;
+    int bandwidth_mode;
+    float h_fixed;
+    float conv_tol;
+    float init_radius;
+    int debug;
+    int profile;
+    void *cuda_stream;
+} asicp_config;
+
+/* Host pointers (or device pointers) the library fills in asicp_get_state; any
+ * may be NULL.  Flat particle index = p * K + j.
+ *   theta     P*K*7 float   poses (after the last step's update)
+ *   cost      P*K   double  cost at the poses the last step started from: the match
+ *                           cost L (Eqs. 13-15) or, for a colliding particle, L_col (Eq. 18)
+ *   grad      P*K*7 double  gradient used by the last step (Eqs. 16-17, or Eq. 18 via 4-5)
+ *   phi       P*K*7 float   Stein direction of the last step (Eq. 8; zero in the SGD phase)
+ *   ncol      P*K   int     colliding points of C at those poses (Eq. 12)
+ *   frozen    P*K   int     convergence flag
+ *   h         P     float   RBF bandwidth of the last SVGD step (Eq. 9)
+ * needing config.debug = 1:
+ *   nn_idx    P*K*N int     forward correspondence index into R per gripper point (Eq. 1)
+ *   nn_d2     P*K*N float   its squared distance
+ *   s_prime   P*K*N*3 float transformed gripper points exactly as matched
+ *   col_list  P*K*Mc int    colliding C indices, ascending, first ncol entries valid
+ *   col_nn    P*K*Mc int    nearest gripper point per colliding point (Eq. 18)     */
+typedef struct {
+    float *theta;
+    double *cost;
+    double *grad;
+    float *phi;
+    int *ncol;
+    int *frozen;
+    float *h;
+    int *nn_idx;
+    float *nn_d2;
+    float *s_prime;
+    int *col_list;
+    int *col_nn;
+} asicp_state_view;
+
+/* Fill *cfg with the defaults described above for P = 1, K = 32, k_max = 40. */
+void asicp_config_default(asicp_config *cfg);
+
+/* Create a context for one GPU (the current device).  *out receives the handle.
+ * Errors: INVALID_ARG for NULL pointers or out-of-range parameters, OOM. */
+asicp_status asicp_create(const asicp_config *cfg, asicp_ctx **out);
+
+/* Release every device and host resource of ctx (NULL is accepted). */
+asicp_status asicp_destroy(asicp_ctx *ctx);
+
+/* Object cloud R (M x 3) used for matching (Eq. 1, the reference cloud R of
+ * Section III-A) and collision cloud C (Mc x 3; object and table, Section IV-A).
+ * C_xyz = NULL uses C = R.  Computes CoM = centroid of R (Algorithm 1, line 1).
+ * Errors: INVALID_ARG (NULL R, M < 1, Mc < 1 when C is given, non-finite value). */
+asicp_status asicp_set_object(asicp_ctx *ctx, const float *R_xyz, int M, const float *C_xyz, int Mc);
+
+/* Preshape `preshape` (0 <= preshape < P): contact-surface cloud S (N x 3, gripper
+ * frame; the source cloud of Section IV-A) and the gripper's signed distance field
+ * sampled on a node-centred grid of nx*ny*nz float32 values, x fastest, positive
+ * inside the gripper (Eq. 12), node (0,0,0) at origin, spacing voxel.  Computes
+ * TCP = centroid of S (Section IV-B).  Every preshape must have the same N.
+ * Errors: INVALID_ARG (index, N < 1, a grid dimension < 2, voxel <= 0, N differing
+ * from an earlier preshape, non-finite value). */
+asicp_status asicp_set_gripper_sdf(asicp_ctx *ctx, int preshape, const float *S_xyz, int N,
+                                   const float *sdf, int nx, int ny, int nz,
+                                   const float origin[3], float voxel);
+
+/* Set all P*K poses (P*K*7 floats; quaternions are normalised) and the iteration
+ * counter, clearing the convergence state.  Used for warm starts and to
+ * teacher-force a single step.  Errors: INVALID_ARG, STATE (inputs not set). */
+asicp_status asicp_set_state(asicp_ctx *ctx, const float *theta, int k);
+
+/* One iteration k (0 <= k < k_max) of Algorithm 1 for all preshapes and
+ * particles: transform, match, cost/gradient, collision test and collision
+ * gradient, then the SVGD update (k < k_stein, Eqs. 7-11) or the SGD-ICP update
+ * (Eq. 3).  Errors: STATE (inputs or poses not set), INVALID_ARG (k), CUDA. */
+asicp_status asicp_step(asicp_ctx *ctx, int k);
+
+/* Full optimisation of one grasp set: initial poses theta0 (P*K*7, normalised
+ * here) or, for theta0 = NULL, the Fibonacci sphere of radius init_radius around
+ * the CoM (Section V); k_max steps; a final evaluation of cost and collisions at
+ * the last poses; and the ranking used by asicp_best_grasps (Algorithm 1's
+ * argmin).  Errors: STATE, INVALID_ARG, CUDA. */
+asicp_status asicp_run(asicp_ctx *ctx, const float *theta0);
+
+/* The topk best particles of the last asicp_run: non-colliding first, then by
+ * ascending final cost, ties to the lower flat index.  theta: topk*7 floats,
+ * cost: topk floats, preshape: topk ints (any may be NULL); *n_out = entries
+ * written (min(topk, P*K)).  Errors: STATE (no completed run), INVALID_ARG. */
+asicp_status asicp_best_grasps(asicp_ctx *ctx, int topk, float *theta, float *cost, int *preshape, int *n_out);
+
+/* Copy the current particle state into the arrays of *view (see above).
+ * Errors: STATE (debug arrays requested without config.debug, or no step yet). */
+asicp_status asicp_get_state(asicp_ctx *ctx, const asicp_state_view *view);
+
+/* With config.profile = 1: accumulated device time (ms) and launch count of the
+ * forward matching kernel, the collision kernels and the update kernel since the
+ * last reset.  ms[4] / launches[4] order: match, collide, collide_nn, update.
+ * reset = 1 clears the counters after reading.  Errors: STATE (profile off). */
+asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[4], long long launches[4], int reset);
+
+/* Message of the last failing call on ctx (owned by ctx, valid until its next call). */
+const char *asicp_last_error(const asicp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

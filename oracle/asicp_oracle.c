@@ -119,15 +119,16 @@ static void project_tangent(const double q[4], double g[4])
     for (int a = 0; a < 4; ++a) g[a] -= d * q[a];
 }
 
-/* Match cost and gradient of one particle (Eqs. 13-17).
+/* Match cost and gradient of one particle (Eqs. 13-17) for given pairs
+ * (gripper point i <-> object point nn_idx[i]).
  * Readings: the pairs are one per gripper point (N of them) matched against the
  * whole object cloud; the TCP-CoM term sits inside the 1/N with weight w_com as
  * Eqs. 16-17 print it, and the cost is the matching function of that gradient,
  * L = (1/N)(sum |s'_i - r_i|^2 + w_com |R TCP + t - CoM|^2), so the gradient is
  * half of dL/dtheta.  The quaternion block is projected onto the tangent space
  * of the unit sphere at q. */
-void orc_match_cost_grad(const orc_problem *pb, int p, const double theta[7],
-                         double *cost, double g[7], int *nn_idx)
+void orc_match_terms(const orc_problem *pb, int p, const double theta[7], const int *nn_idx,
+                     double *cost, double g[7])
 {
     const int N = pb->N;
     const double *S = pb->S + (size_t)p * N * 3;
@@ -139,11 +140,8 @@ void orc_match_cost_grad(const orc_problem *pb, int p, const double theta[7],
     double se = 0.0, ge[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0};
     for (int i = 0; i < N; ++i) {
         double sp[3], J[12];
-        int r;
-        double d2;
+        const int r = nn_idx[i];
         transform(Rm, t, S + i * 3, sp);
-        orc_nn(sp, 1, pb->R, pb->M, &r, &d2);
-        if (nn_idx) nn_idx[i] = r;
         double e[3] = {sp[0] - pb->R[r * 3 + 0], sp[1] - pb->R[r * 3 + 1], sp[2] - pb->R[r * 3 + 2]};
         se += e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
         for (int a = 0; a < 3; ++a) ge[a] += e[a];
@@ -166,6 +164,25 @@ void orc_match_cost_grad(const orc_problem *pb, int p, const double theta[7],
     for (int k = 0; k < 4; ++k) gq[k] /= N;
     project_tangent(q, gq);
     for (int k = 0; k < 4; ++k) g[3 + k] = gq[k];
+}
+
+/* Algorithm 1 for one particle: transform the contact cloud, pair every point
+ * with its nearest object point (Eq. 1), then the cost and gradient above. */
+void orc_match_cost_grad(const orc_problem *pb, int p, const double theta[7],
+                         double *cost, double g[7], int *nn_idx)
+{
+    const int N = pb->N;
+    const double *S = pb->S + (size_t)p * N * 3;
+    double Rm[9];
+    orc_rotation(theta + 3, Rm);
+    int *idx = nn_idx ? nn_idx : (int *)malloc(sizeof(int) * (size_t)N);
+    for (int i = 0; i < N; ++i) {
+        double sp[3], d2;
+        transform(Rm, theta, S + i * 3, sp);
+        orc_nn(sp, 1, pb->R, pb->M, idx + i, &d2);
+    }
+    orc_match_terms(pb, p, theta, idx, cost, g);
+    if (!nn_idx) free(idx);
 }
 
 /* Collision test (Eq. 12, Section IV-C): each point c of the collision cloud is
@@ -197,41 +214,58 @@ int orc_collision_points(const orc_problem *pb, int p, const double theta[7],
     return n;
 }
 
-/* Collision cost and gradient (Eq. 18): every colliding point is paired with
- * its nearest transformed contact point s' (ties to the lowest gripper index),
- * L_col = (1/N_col) sum |c - s'|^2, and the gradient follows Eqs. 4-5 with the
- * residual e = s' - c taken with respect to the gripper point s' = R s + t,
- * normalised by N_col and projected like the match gradient. */
-void orc_collision_cost_grad(const orc_problem *pb, int p, const double theta[7],
-                             const int *list, int ncol, double *cost, double g[7], int *col_nn)
+/* Collision cost and gradient (Eq. 18) for given pairs: colliding point
+ * list[l] <-> gripper point nn[l].  L_col = (1/N_col) sum |c - s'|^2, and the
+ * gradient follows Eqs. 4-5 with the residual e = s' - c taken with respect to
+ * the gripper point s' = R s + t, normalised by N_col and projected like the
+ * match gradient. */
+void orc_collision_terms(const orc_problem *pb, int p, const double theta[7], const int *list,
+                         const int *nn, int ncol, double *cost, double g[7])
 {
     const int N = pb->N;
     const double *S = pb->S + (size_t)p * N * 3;
     const double *t = theta, *q = theta + 3;
     double Rm[9];
     orc_rotation(q, Rm);
-    double *Sp = (double *)malloc(sizeof(double) * 3 * (size_t)N);
-    for (int i = 0; i < N; ++i) transform(Rm, t, S + i * 3, Sp + i * 3);
     double se = 0.0, ge[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0};
     for (int l = 0; l < ncol; ++l) {
         const double *c = pb->C + (size_t)list[l] * 3;
-        int i;
-        double d2, J[12];
-        orc_nn(c, 1, Sp, N, &i, &d2);
-        if (col_nn) col_nn[l] = i;
-        double e[3] = {Sp[i * 3 + 0] - c[0], Sp[i * 3 + 1] - c[1], Sp[i * 3 + 2] - c[2]};
+        const int i = nn[l];
+        double sp[3], J[12];
+        transform(Rm, t, S + i * 3, sp);
+        double e[3] = {sp[0] - c[0], sp[1] - c[1], sp[2] - c[2]};
         se += e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
         for (int a = 0; a < 3; ++a) ge[a] += e[a];
         orc_rot_jacobian(q, S + i * 3, J);
         for (int k = 0; k < 4; ++k)
             gq[k] += J[0 * 4 + k] * e[0] + J[1 * 4 + k] * e[1] + J[2 * 4 + k] * e[2];
     }
-    free(Sp);
     *cost = se / ncol;
     for (int a = 0; a < 3; ++a) g[a] = ge[a] / ncol;
     for (int k = 0; k < 4; ++k) gq[k] /= ncol;
     project_tangent(q, gq);
     for (int k = 0; k < 4; ++k) g[3 + k] = gq[k];
+}
+
+/* Section IV-C: every colliding point is paired with its nearest transformed
+ * contact point s' (ties to the lowest gripper index), then the terms above. */
+void orc_collision_cost_grad(const orc_problem *pb, int p, const double theta[7],
+                             const int *list, int ncol, double *cost, double g[7], int *col_nn)
+{
+    const int N = pb->N;
+    const double *S = pb->S + (size_t)p * N * 3;
+    double Rm[9];
+    orc_rotation(theta + 3, Rm);
+    double *Sp = (double *)malloc(sizeof(double) * 3 * (size_t)N);
+    for (int i = 0; i < N; ++i) transform(Rm, theta, S + i * 3, Sp + i * 3);
+    int *nn = col_nn ? col_nn : (int *)malloc(sizeof(int) * (size_t)(ncol > 0 ? ncol : 1));
+    for (int l = 0; l < ncol; ++l) {
+        double d2;
+        orc_nn(pb->C + (size_t)list[l] * 3, 1, Sp, N, nn + l, &d2);
+    }
+    free(Sp);
+    orc_collision_terms(pb, p, theta, list, nn, ncol, cost, g);
+    if (!col_nn) free(nn);
 }
 
 /* Eq. 11: gamma(t) = (mod(t, T/C) / (T/C))^p with T = k_max (cyclic), or the

@@ -57,6 +57,10 @@ void orc_rot_jacobian(const double q[4], const double s[3], double J[12]);
 void orc_nn(const double *Q, int nq, const double *ref, int m, int *idx, double *d2);
 double orc_trilinear(const double *grid, const int dims[3], const double origin[3],
                      double voxel, const double x[3], int *inside);
+void orc_match_terms(const orc_problem *pb, int p, const double theta[7], const int *nn_idx,
+                     double *cost, double g[7]);
+void orc_collision_terms(const orc_problem *pb, int p, const double theta[7], const int *list,
+                         const int *nn, int ncol, double *cost, double g[7]);
 void orc_match_cost_grad(const orc_problem *pb, int p, const double theta[7],
                          double *cost, double g[7], int *nn_idx);
 int orc_collision_points(const orc_problem *pb, int p, const double theta[7],

@@ -65,6 +65,8 @@ def _load():
         lib.orc_collision_points.argtypes = [C.POINTER(_Problem), C.c_int, _dp, _ip, _dp]
         lib.orc_collision_points.restype = C.c_int
         lib.orc_collision_cost_grad.argtypes = [C.POINTER(_Problem), C.c_int, _dp, _ip, C.c_int, _dp, _dp, _ip]
+        lib.orc_match_terms.argtypes = [C.POINTER(_Problem), C.c_int, _dp, _ip, _dp, _dp]
+        lib.orc_collision_terms.argtypes = [C.POINTER(_Problem), C.c_int, _dp, _ip, _ip, C.c_int, _dp, _dp]
         lib.orc_gamma.argtypes = [C.POINTER(_Schedule), C.c_int]
         lib.orc_gamma.restype = C.c_double
         lib.orc_bandwidth.argtypes = [_dp, C.c_int, C.POINTER(_Schedule)]
@@ -210,6 +212,26 @@ class Oracle:
         _load().orc_match_cost_grad(C.byref(self._pb), int(p), tp, C.byref(cost), g.ctypes.data_as(_dp),
                                     idx.ctypes.data_as(_ip))
         return cost.value, g, idx
+
+    def match_terms(self, p, theta, nn_idx):
+        """Cost and gradient for given pairs (gripper point i <-> object point nn_idx[i])."""
+        th, tp = _d(theta)
+        idx, ip = _i(nn_idx)
+        cost = C.c_double(0)
+        g = np.zeros(7)
+        _load().orc_match_terms(C.byref(self._pb), int(p), tp, ip, C.byref(cost), g.ctypes.data_as(_dp))
+        return cost.value, g
+
+    def collision_terms(self, p, theta, lst, nn_):
+        """Collision cost and gradient for given pairs (C[lst[l]] <-> gripper point nn_[l])."""
+        th, tp = _d(theta)
+        lst, lp = _i(lst)
+        nn_, np_ = _i(nn_)
+        cost = C.c_double(0)
+        g = np.zeros(7)
+        _load().orc_collision_terms(C.byref(self._pb), int(p), tp, lp, np_, len(lst), C.byref(cost),
+                                    g.ctypes.data_as(_dp))
+        return cost.value, g
 
     def collision_points(self, p, theta):
         th, tp = _d(theta)

@@ -1,0 +1,601 @@
+// C-ABI of libasicp (declared in include/asicp.h): context, inputs, the
+// iteration loop of Algorithm 1 and result read-back.  Host code only; every
+// arithmetic step of the method runs in the kernels of k_match.cu,
+// k_collision.cu and k_update.cu.
+#include "../../include/asicp.h"
+#include "asicp_internal.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace asicp;
+
+namespace {
+
+struct Err {
+    asicp_status st;
+    std::string msg;
+};
+
+[[noreturn]] void fail(asicp_status st, const std::string &msg) { throw Err{st, msg}; }
+
+void ck(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        fail(ASICP_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    fail(ASICP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Device allocation owned by the context; grows on demand, never shrinks.
+struct DevMem {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(const DevMem &) = delete;
+    DevMem &operator=(const DevMem &) = delete;
+    DevMem(DevMem &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    ~DevMem() { if (p) cudaFree(p); }
+    void ensure(size_t want, const char *what)
+    {
+        if (want <= bytes && p) return;
+        if (p) { cudaFree(p); p = nullptr; bytes = 0; }
+        if (want == 0) want = 16;
+        ck(cudaMalloc(&p, want), what);
+        bytes = want;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+enum { kTimeMatch = 0, kTimeCollide = 1, kTimeCollideNN = 2, kTimeUpdate = 3 };
+
+}  // namespace
+
+struct asicp_ctx {
+    asicp_config cfg{};
+    cudaStream_t st = nullptr;
+    std::string err;
+    int M = 0, Mc = 0, N = 0;
+    bool object_set = false, theta_set = false, stepped = false, run_done = false;
+    std::vector<char> pre_set;
+    std::vector<SdfMeta> meta;
+    std::vector<DevMem> grids;
+    int k_next = 0;
+
+    DevMem stage, R, C, S, com, pconst, dmeta, theta, fsums, csums, ncol, colidx, cost, grad, prev, frozen,
+        phi, h, order, errw, out7, outc, outi, dbg_idx, dbg_d2, dbg_sp, dbg_colnn;
+
+    // profiling: events recorded around launches (kind, start, stop)
+    struct Ev { int kind; cudaEvent_t a, b; };
+    std::vector<Ev> events;
+    std::vector<cudaEvent_t> pool;
+    double acc_ms[4] = {0, 0, 0, 0};
+    long long acc_n[4] = {0, 0, 0, 0};
+
+    int PK() const { return cfg.P * cfg.K; }
+    int nb() const { return (N + fwd_queries_per_block() - 1) / fwd_queries_per_block(); }
+    bool ready() const
+    {
+        if (!object_set || N == 0) return false;
+        for (char c : pre_set) if (!c) return false;
+        return true;
+    }
+    cudaEvent_t take_event()
+    {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e;
+        ck(cudaEventCreate(&e), "cudaEventCreate");
+        return e;
+    }
+    ~asicp_ctx()
+    {
+        for (auto &e : events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+template <class F>
+asicp_status guarded(asicp_ctx *ctx, F &&f)
+{
+    if (!ctx) return ASICP_ERR_INVALID_ARG;
+    try {
+        f();
+        ctx->err.clear();
+        return ASICP_OK;
+    } catch (const Err &e) {
+        ctx->err = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        ctx->err = "host allocation failed";
+        return ASICP_ERR_OOM;
+    } catch (...) {
+        ctx->err = "unexpected internal error";
+        return ASICP_ERR_CUDA;
+    }
+}
+
+void sync_and_check_err(asicp_ctx *c, const char *what)
+{
+    ck(cudaStreamSynchronize(c->st), what);
+    int e = 0;
+    ck(cudaMemcpy(&e, c->errw.p, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+    if (e == kDevNonFinite) {
+        ck(cudaMemsetAsync(c->errw.p, 0, sizeof(int), c->st), "clear error word");
+        fail(ASICP_ERR_INVALID_ARG, std::string(what) + ": non-finite value in the input");
+    }
+    if (e == kDevTimeout) {
+        ck(cudaMemsetAsync(c->errw.p, 0, sizeof(int), c->st), "clear error word");
+        fail(ASICP_ERR_TIMEOUT, std::string(what) + ": a bounded device wait expired");
+    }
+}
+
+double gamma_of(const asicp_config &c, int k)
+{
+    if (c.schedule == 1) {
+        if (c.k_max <= 1) return c.g1;
+        return c.g0 + (double)(c.g1 - c.g0) * k / (double)(c.k_max - 1);
+    }
+    const double period = (double)c.k_max / c.C_cycles;          // Eq. 11 with T = k_max
+    return std::pow(std::fmod((double)k, period) / period, (double)c.p_exp);
+}
+
+void ensure_work(asicp_ctx *c)
+{
+    const size_t PK = c->PK();
+    c->fsums.ensure(sizeof(double) * PK * c->nb() * kFwdSums, "fsums");
+    c->csums.ensure(sizeof(double) * PK * kColSums, "csums");
+    c->ncol.ensure(sizeof(int) * PK, "ncol");
+    c->colidx.ensure(sizeof(int) * PK * (size_t)c->Mc, "colidx");
+    c->cost.ensure(sizeof(double) * PK, "cost");
+    c->grad.ensure(sizeof(double) * PK * 8, "grad");
+    c->prev.ensure(sizeof(double) * PK, "prev_cost");
+    c->frozen.ensure(sizeof(int) * PK, "frozen");
+    c->phi.ensure(sizeof(float) * PK * 8, "phi");
+    c->h.ensure(sizeof(float) * c->cfg.P, "h");
+    c->order.ensure(sizeof(int) * PK, "order");
+    c->out7.ensure(sizeof(float) * PK * 8, "out7");
+    c->outc.ensure(sizeof(float) * PK, "outc");
+    c->outi.ensure(sizeof(int) * PK, "outi");
+    if (c->cfg.debug) {
+        c->dbg_idx.ensure(sizeof(int) * PK * c->N, "dbg_idx");
+        c->dbg_d2.ensure(sizeof(float) * PK * c->N, "dbg_d2");
+        c->dbg_sp.ensure(sizeof(float) * PK * c->N * 3, "dbg_sp");
+        c->dbg_colnn.ensure(sizeof(int) * PK * (size_t)c->Mc, "dbg_colnn");
+    }
+}
+
+__global__ void reset_convergence_kernel(double *prev, int *frozen, float *phi, int PK)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= PK) return;
+    prev[i] = -1.0;     // no previous cost
+    frozen[i] = 0;
+    for (int a = 0; a < 8; ++a) phi[(size_t)i * 8 + a] = 0.f;
+}
+
+void reset_convergence(asicp_ctx *c)
+{
+    const int PK = c->PK();
+    reset_convergence_kernel<<<(PK + 255) / 256, 256, 0, c->st>>>(c->prev.as<double>(), c->frozen.as<int>(),
+                                                                  c->phi.as<float>(), PK);
+    ck(cudaGetLastError(), "reset convergence state");
+}
+
+template <class L>
+void timed(asicp_ctx *c, int kind, L &&launch, const char *what)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c->cfg.profile) {
+        a = c->take_event();
+        b = c->take_event();
+        ck(cudaEventRecord(a, c->st), "cudaEventRecord");
+    }
+    ck(launch(), what);
+    if (c->cfg.profile) {
+        ck(cudaEventRecord(b, c->st), "cudaEventRecord");
+        c->events.push_back({kind, a, b});
+    }
+}
+
+// One pass of cost/gradient evaluation (+ update for mode 1/2).
+void iterate(asicp_ctx *c, int mode, float gamma)
+{
+    const int PK = c->PK();
+    FwdArgs fa{};
+    fa.S = c->S.as<float4>();
+    fa.theta = c->theta.as<float>();
+    fa.R = c->R.as<float4>();
+    fa.M = c->M; fa.N = c->N; fa.K = c->cfg.K; fa.PK = PK; fa.nb = c->nb();
+    fa.fsums = c->fsums.as<double>();
+    if (c->cfg.debug) {
+        fa.dbg_idx = c->dbg_idx.as<int>();
+        fa.dbg_d2 = c->dbg_d2.as<float>();
+        fa.dbg_sp = c->dbg_sp.as<float>();
+    }
+    timed(c, kTimeMatch, [&] { return launch_fwd_match(fa, c->st); }, "forward matching kernel");
+
+    CollideArgs ca{};
+    ca.C = c->C.p ? c->C.as<float4>() : c->R.as<float4>();
+    ca.Mc = c->Mc; ca.K = c->cfg.K; ca.PK = PK; ca.N = c->N;
+    ca.theta = c->theta.as<float>();
+    ca.meta = c->dmeta.as<SdfMeta>();
+    ca.ncol = c->ncol.as<int>();
+    ca.colidx = c->colidx.as<int>();
+    ca.S = c->S.as<float4>();
+    ca.csums = c->csums.as<double>();
+    if (c->cfg.debug) ca.dbg_colnn = c->dbg_colnn.as<int>();
+    timed(c, kTimeCollide, [&] { return launch_collide(ca, c->st); }, "collision kernel");
+    timed(c, kTimeCollideNN, [&] { return launch_collide_nn(ca, c->st); }, "collision matching kernel");
+
+    UpdateArgs ua{};
+    ua.P = c->cfg.P; ua.K = c->cfg.K; ua.N = c->N; ua.nb = c->nb();
+    ua.theta = c->theta.as<float>();
+    ua.fsums = c->fsums.as<double>();
+    ua.csums = c->csums.as<double>();
+    ua.ncol = c->ncol.as<int>();
+    ua.pconst = c->pconst.as<double>();
+    ua.com = c->com.as<double>();
+    ua.w_com = c->cfg.w_com;
+    ua.mode = mode;
+    ua.gamma = gamma;
+    ua.eta_svgd = c->cfg.eta_svgd > 0.f ? c->cfg.eta_svgd : 1.f / (float)c->N;
+    ua.eta_sgd = c->cfg.eta_sgd;
+    ua.bandwidth_mode = c->cfg.bandwidth_mode;
+    ua.h_fixed = c->cfg.h_fixed;
+    ua.conv_tol = c->cfg.conv_tol;
+    ua.cost = c->cost.as<double>();
+    ua.grad = c->grad.as<double>();
+    ua.prev_cost = c->prev.as<double>();
+    ua.frozen = c->frozen.as<int>();
+    ua.phi = c->phi.as<float>();
+    ua.h = c->h.as<float>();
+    timed(c, kTimeUpdate, [&] { return launch_update(ua, c->st); }, "update kernel");
+}
+
+void step_impl(asicp_ctx *c, int k)
+{
+    const int mode = k < c->cfg.k_stein ? 1 : 2;
+    iterate(c, mode, (float)gamma_of(c->cfg, k));
+    c->k_next = k + 1;
+    c->stepped = true;
+}
+
+void copy_out(void *dst, const void *src, size_t bytes, cudaStream_t st, const char *what)
+{
+    if (!dst || bytes == 0) return;
+    ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st), what);
+}
+
+__global__ void repack_kernel(const float *src8, int n, float *dst7)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int a = 0; a < 7; ++a) dst7[(size_t)i * 7 + a] = src8[(size_t)i * 8 + a];
+}
+
+__global__ void repack_f64_kernel(const double *src8, int n, double *dst7)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int a = 0; a < 7; ++a) dst7[(size_t)i * 7 + a] = src8[(size_t)i * 8 + a];
+}
+
+__global__ void gather_best_kernel(const int *order, int n, int K, const float *theta8, const double *cost,
+                                   float *o7, float *oc, int *oi)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int i = order[r];
+    for (int a = 0; a < 7; ++a) o7[(size_t)r * 7 + a] = theta8[(size_t)i * 8 + a];
+    oc[r] = (float)cost[i];
+    oi[r] = i / K;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------- ABI
+extern "C" {
+
+void asicp_config_default(asicp_config *cfg)
+{
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->P = 1;
+    cfg->K = 32;
+    cfg->k_max = 40;
+    cfg->k_stein = 15;          // Table I: 15 SVGD + 25 SGD iterations
+    cfg->schedule = 0;
+    cfg->C_cycles = 5.f;        // Table I annealing factor (mod(k, k_max/5) / (k_max/5))^2
+    cfg->p_exp = 2.f;
+    cfg->g0 = 0.1f;
+    cfg->g1 = 1.f;
+    cfg->eta_sgd = 1.f;         // Table I learning rate
+    cfg->eta_svgd = 0.f;        // 1/N
+    cfg->w_com = 1.f;           // Table I cost weights
+    cfg->bandwidth_mode = 0;
+    cfg->h_fixed = 1.f;
+    cfg->conv_tol = 2e-4f;      // Table I convergence criterion 0.02 %
+    cfg->init_radius = 0.15f;
+    cfg->debug = 0;
+    cfg->profile = 0;
+    cfg->cuda_stream = nullptr;
+}
+
+asicp_status asicp_create(const asicp_config *cfg, asicp_ctx **out)
+{
+    if (!cfg || !out) return ASICP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (cfg->P < 1 || cfg->P > 64 || cfg->K < 1 || cfg->K > kMaxK || cfg->k_max < 0 || cfg->k_stein < 0 ||
+        cfg->k_stein > cfg->k_max || (cfg->schedule != 0 && cfg->schedule != 1) ||
+        (cfg->schedule == 0 && !(cfg->C_cycles > 0.f)) || !(cfg->eta_sgd >= 0.f) ||
+        (cfg->bandwidth_mode == 1 && !(cfg->h_fixed > 0.f)) || !std::isfinite(cfg->w_com) ||
+        !(cfg->init_radius >= 0.f))
+        return ASICP_ERR_INVALID_ARG;
+    asicp_ctx *c = new (std::nothrow) asicp_ctx();
+    if (!c) return ASICP_ERR_OOM;
+    c->cfg = *cfg;
+    c->st = static_cast<cudaStream_t>(cfg->cuda_stream);
+    c->pre_set.assign(cfg->P, 0);
+    c->meta.assign(cfg->P, SdfMeta{});
+    c->grids.resize(cfg->P);
+    asicp_status s = guarded(c, [&] {
+        c->com.ensure(sizeof(double) * 3, "com");
+        c->pconst.ensure(sizeof(double) * 12 * cfg->P, "pconst");
+        c->dmeta.ensure(sizeof(SdfMeta) * cfg->P, "sdf meta");
+        c->theta.ensure(sizeof(float) * 8 * (size_t)c->PK(), "theta");
+        c->errw.ensure(sizeof(int), "error word");
+        ck(cudaMemsetAsync(c->errw.p, 0, sizeof(int), c->st), "clear error word");
+        ck(cudaStreamSynchronize(c->st), "create");
+    });
+    if (s != ASICP_OK) {
+        delete c;
+        return s;
+    }
+    *out = c;
+    return ASICP_OK;
+}
+
+asicp_status asicp_destroy(asicp_ctx *ctx)
+{
+    if (!ctx) return ASICP_OK;
+    cudaStreamSynchronize(ctx->st);
+    delete ctx;
+    return ASICP_OK;
+}
+
+asicp_status asicp_set_object(asicp_ctx *ctx, const float *R_xyz, int M, const float *C_xyz, int Mc)
+{
+    return guarded(ctx, [&] {
+        if (!R_xyz || M < 1) fail(ASICP_ERR_INVALID_ARG, "set_object: R must be non-NULL with M >= 1");
+        if (C_xyz && Mc < 1) fail(ASICP_ERR_INVALID_ARG, "set_object: Mc must be >= 1 when C is given");
+        const int mc = C_xyz ? Mc : M;
+        ctx->object_set = false;
+        ctx->run_done = false;
+        ctx->stage.ensure(sizeof(float) * 3 * (size_t)(M > mc ? M : mc), "staging");
+        ctx->R.ensure(sizeof(float4) * M, "object cloud");
+        ck(cudaMemcpyAsync(ctx->stage.p, R_xyz, sizeof(float) * 3 * (size_t)M, cudaMemcpyDefault, ctx->st), "copy R");
+        ck(launch_pack_points(ctx->stage.as<float>(), M, ctx->R.as<float4>(), ctx->errw.as<int>(), ctx->st), "pack R");
+        if (C_xyz) {
+            ctx->C.ensure(sizeof(float4) * mc, "collision cloud");
+            ck(cudaMemcpyAsync(ctx->stage.p, C_xyz, sizeof(float) * 3 * (size_t)mc, cudaMemcpyDefault, ctx->st),
+               "copy C");
+            ck(launch_pack_points(ctx->stage.as<float>(), mc, ctx->C.as<float4>(), ctx->errw.as<int>(), ctx->st),
+               "pack C");
+        } else if (ctx->C.p) {
+            cudaFree(ctx->C.p);
+            ctx->C.p = nullptr;
+            ctx->C.bytes = 0;
+        }
+        ck(launch_centroid(ctx->R.as<float4>(), M, ctx->com.as<double>(), ctx->st), "centroid");
+        sync_and_check_err(ctx, "set_object");
+        ctx->M = M;
+        ctx->Mc = mc;
+        ctx->object_set = true;
+        if (ctx->N > 0) ensure_work(ctx);
+    });
+}
+
+asicp_status asicp_set_gripper_sdf(asicp_ctx *ctx, int preshape, const float *S_xyz, int N, const float *sdf,
+                                   int nx, int ny, int nz, const float origin[3], float voxel)
+{
+    return guarded(ctx, [&] {
+        if (preshape < 0 || preshape >= ctx->cfg.P) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: preshape out of range");
+        if (!S_xyz || !sdf || !origin) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: NULL array");
+        if (N < 1 || N > 8192) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: N must be in [1, 8192]");
+        if (nx < 2 || ny < 2 || nz < 2) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: every grid dimension must be >= 2");
+        if (!(voxel > 0.f) || !std::isfinite(voxel)) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: voxel must be > 0");
+        float org[3];
+        ck(cudaMemcpy(org, origin, sizeof(org), cudaMemcpyDefault), "copy origin");
+        for (float o : org)
+            if (!std::isfinite(o)) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: non-finite origin");
+        bool any_set = false;
+        for (char s : ctx->pre_set) any_set = any_set || s;
+        if (any_set && N != ctx->N) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: every preshape must have the same N");
+        if (!any_set && N != ctx->N) ctx->N = N;
+        ctx->pre_set[preshape] = 0;
+        ctx->run_done = false;
+        ctx->S.ensure(sizeof(float4) * (size_t)ctx->cfg.P * N, "gripper clouds");
+        ctx->stage.ensure(sizeof(float) * 3 * (size_t)N, "staging");
+        ck(cudaMemcpyAsync(ctx->stage.p, S_xyz, sizeof(float) * 3 * (size_t)N, cudaMemcpyDefault, ctx->st), "copy S");
+        float4 *Sp = ctx->S.as<float4>() + (size_t)preshape * N;
+        ck(launch_pack_points(ctx->stage.as<float>(), N, Sp, ctx->errw.as<int>(), ctx->st), "pack S");
+        ck(launch_preshape_consts(Sp, N, ctx->pconst.as<double>() + 12 * preshape, ctx->st), "preshape sums");
+        const size_t nv = (size_t)nx * ny * nz;
+        ctx->grids[preshape].ensure(sizeof(float) * nv, "sdf grid");
+        ck(cudaMemcpyAsync(ctx->grids[preshape].p, sdf, sizeof(float) * nv, cudaMemcpyDefault, ctx->st), "copy sdf");
+        ck(launch_check_finite(ctx->grids[preshape].as<float>(), (long long)nv, ctx->errw.as<int>(), ctx->st), "check sdf");
+        SdfMeta m{};
+        m.grid = ctx->grids[preshape].as<float>();
+        m.nx = nx; m.ny = ny; m.nz = nz;
+        m.ox = org[0]; m.oy = org[1]; m.oz = org[2];
+        m.voxel = voxel;
+        ctx->meta[preshape] = m;
+        ck(cudaMemcpyAsync(ctx->dmeta.as<SdfMeta>() + preshape, &ctx->meta[preshape], sizeof(SdfMeta),
+                           cudaMemcpyHostToDevice, ctx->st), "copy sdf meta");
+        sync_and_check_err(ctx, "set_gripper_sdf");
+        ctx->pre_set[preshape] = 1;
+        if (ctx->object_set) ensure_work(ctx);
+    });
+}
+
+asicp_status asicp_set_state(asicp_ctx *ctx, const float *theta, int k)
+{
+    return guarded(ctx, [&] {
+        if (!ctx->ready()) fail(ASICP_ERR_STATE, "set_state: object and every preshape must be set first");
+        if (!theta || k < 0 || k > ctx->cfg.k_max) fail(ASICP_ERR_INVALID_ARG, "set_state: bad theta or k");
+        ensure_work(ctx);
+        const size_t PK = ctx->PK();
+        ctx->stage.ensure(sizeof(float) * 7 * PK, "staging");
+        ck(cudaMemcpyAsync(ctx->stage.p, theta, sizeof(float) * 7 * PK, cudaMemcpyDefault, ctx->st), "copy theta");
+        ck(launch_set_theta(ctx->stage.as<float>(), (int)PK, ctx->theta.as<float>(), ctx->errw.as<int>(), ctx->st),
+           "set theta");
+        reset_convergence(ctx);
+        sync_and_check_err(ctx, "set_state");
+        ctx->k_next = k;
+        ctx->theta_set = true;
+        ctx->stepped = false;
+        ctx->run_done = false;
+    });
+}
+
+asicp_status asicp_step(asicp_ctx *ctx, int k)
+{
+    return guarded(ctx, [&] {
+        if (!ctx->ready() || !ctx->theta_set) fail(ASICP_ERR_STATE, "step: inputs and poses must be set first");
+        if (k < 0 || k >= ctx->cfg.k_max) fail(ASICP_ERR_INVALID_ARG, "step: k out of [0, k_max)");
+        step_impl(ctx, k);
+        ctx->run_done = false;
+    });
+}
+
+asicp_status asicp_run(asicp_ctx *ctx, const float *theta0)
+{
+    return guarded(ctx, [&] {
+        if (!ctx->ready()) fail(ASICP_ERR_STATE, "run: object and every preshape must be set first");
+        ensure_work(ctx);
+        const int PK = ctx->PK();
+        if (theta0) {
+            ctx->stage.ensure(sizeof(float) * 7 * PK, "staging");
+            ck(cudaMemcpyAsync(ctx->stage.p, theta0, sizeof(float) * 7 * (size_t)PK, cudaMemcpyDefault, ctx->st),
+               "copy theta0");
+            ck(launch_set_theta(ctx->stage.as<float>(), PK, ctx->theta.as<float>(), ctx->errw.as<int>(), ctx->st),
+               "set theta0");
+        } else {
+            ck(launch_fibonacci(ctx->cfg.P, ctx->cfg.K, ctx->com.as<double>(), ctx->cfg.init_radius,
+                                ctx->theta.as<float>(), ctx->st), "fibonacci init");
+        }
+        reset_convergence(ctx);
+        if (theta0) sync_and_check_err(ctx, "run");
+        ctx->theta_set = true;
+        for (int k = 0; k < ctx->cfg.k_max; ++k) step_impl(ctx, k);
+        iterate(ctx, 0, 0.f);   // final evaluation at the last poses
+        ck(launch_select(ctx->cost.as<double>(), ctx->ncol.as<int>(), PK, ctx->order.as<int>(), ctx->st), "select");
+        ctx->run_done = true;
+    });
+}
+
+asicp_status asicp_best_grasps(asicp_ctx *ctx, int topk, float *theta, float *cost, int *preshape, int *n_out)
+{
+    return guarded(ctx, [&] {
+        if (!ctx->run_done) fail(ASICP_ERR_STATE, "best_grasps: no completed run");
+        if (topk < 0) fail(ASICP_ERR_INVALID_ARG, "best_grasps: topk < 0");
+        const int n = topk < ctx->PK() ? topk : ctx->PK();
+        if (n > 0) {
+            gather_best_kernel<<<(n + 127) / 128, 128, 0, ctx->st>>>(ctx->order.as<int>(), n, ctx->cfg.K,
+                                                                     ctx->theta.as<float>(), ctx->cost.as<double>(),
+                                                                     ctx->out7.as<float>(), ctx->outc.as<float>(),
+                                                                     ctx->outi.as<int>());
+            ck(cudaGetLastError(), "gather best");
+            copy_out(theta, ctx->out7.p, sizeof(float) * 7 * n, ctx->st, "copy best theta");
+            copy_out(cost, ctx->outc.p, sizeof(float) * n, ctx->st, "copy best cost");
+            copy_out(preshape, ctx->outi.p, sizeof(int) * n, ctx->st, "copy best preshape");
+        }
+        ck(cudaStreamSynchronize(ctx->st), "best_grasps");
+        if (n_out) *n_out = n;
+    });
+}
+
+asicp_status asicp_get_state(asicp_ctx *ctx, const asicp_state_view *v)
+{
+    return guarded(ctx, [&] {
+        if (!v) fail(ASICP_ERR_INVALID_ARG, "get_state: NULL view");
+        if (!ctx->theta_set) fail(ASICP_ERR_STATE, "get_state: no poses yet");
+        const bool dbg = v->nn_idx || v->nn_d2 || v->s_prime || v->col_list || v->col_nn;
+        if (dbg && !ctx->cfg.debug) fail(ASICP_ERR_STATE, "get_state: debug arrays need config.debug = 1");
+        const int PK = ctx->PK();
+        if (v->theta) {
+            repack_kernel<<<(PK + 127) / 128, 128, 0, ctx->st>>>(ctx->theta.as<float>(), PK, ctx->out7.as<float>());
+            ck(cudaGetLastError(), "repack theta");
+            copy_out(v->theta, ctx->out7.p, sizeof(float) * 7 * PK, ctx->st, "copy theta");
+            ck(cudaStreamSynchronize(ctx->st), "get_state");
+        }
+        if (v->phi) {
+            repack_kernel<<<(PK + 127) / 128, 128, 0, ctx->st>>>(ctx->phi.as<float>(), PK, ctx->out7.as<float>());
+            ck(cudaGetLastError(), "repack phi");
+            copy_out(v->phi, ctx->out7.p, sizeof(float) * 7 * PK, ctx->st, "copy phi");
+            ck(cudaStreamSynchronize(ctx->st), "get_state");
+        }
+        if (v->grad) {
+            ctx->stage.ensure(sizeof(double) * 7 * PK, "staging");
+            repack_f64_kernel<<<(PK + 127) / 128, 128, 0, ctx->st>>>(ctx->grad.as<double>(), PK, ctx->stage.as<double>());
+            ck(cudaGetLastError(), "repack grad");
+            copy_out(v->grad, ctx->stage.p, sizeof(double) * 7 * PK, ctx->st, "copy grad");
+            ck(cudaStreamSynchronize(ctx->st), "get_state");
+        }
+        if (ctx->stepped || ctx->run_done) {
+            copy_out(v->cost, ctx->cost.p, sizeof(double) * PK, ctx->st, "copy cost");
+            copy_out(v->ncol, ctx->ncol.p, sizeof(int) * PK, ctx->st, "copy ncol");
+            copy_out(v->h, ctx->h.p, sizeof(float) * ctx->cfg.P, ctx->st, "copy h");
+            if (ctx->cfg.debug) {
+                copy_out(v->nn_idx, ctx->dbg_idx.p, sizeof(int) * (size_t)PK * ctx->N, ctx->st, "copy nn_idx");
+                copy_out(v->nn_d2, ctx->dbg_d2.p, sizeof(float) * (size_t)PK * ctx->N, ctx->st, "copy nn_d2");
+                copy_out(v->s_prime, ctx->dbg_sp.p, sizeof(float) * 3 * (size_t)PK * ctx->N, ctx->st, "copy s_prime");
+                copy_out(v->col_list, ctx->colidx.p, sizeof(int) * (size_t)PK * ctx->Mc, ctx->st, "copy col_list");
+                copy_out(v->col_nn, ctx->dbg_colnn.p, sizeof(int) * (size_t)PK * ctx->Mc, ctx->st, "copy col_nn");
+            }
+        } else if (v->cost || v->ncol || v->h || dbg) {
+            fail(ASICP_ERR_STATE, "get_state: no step has run since the poses were set");
+        }
+        copy_out(v->frozen, ctx->frozen.p, sizeof(int) * PK, ctx->st, "copy frozen");
+        ck(cudaStreamSynchronize(ctx->st), "get_state");
+    });
+}
+
+asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[4], long long launches[4], int reset)
+{
+    return guarded(ctx, [&] {
+        if (!ctx->cfg.profile) fail(ASICP_ERR_STATE, "kernel_times: config.profile is 0");
+        ck(cudaStreamSynchronize(ctx->st), "kernel_times");
+        for (auto &e : ctx->events) {
+            float t = 0.f;
+            ck(cudaEventElapsedTime(&t, e.a, e.b), "cudaEventElapsedTime");
+            ctx->acc_ms[e.kind] += t;
+            ctx->acc_n[e.kind] += 1;
+            ctx->pool.push_back(e.a);
+            ctx->pool.push_back(e.b);
+        }
+        ctx->events.clear();
+        for (int i = 0; i < 4; ++i) {
+            if (ms) ms[i] = ctx->acc_ms[i];
+            if (launches) launches[i] = ctx->acc_n[i];
+        }
+        if (reset)
+            for (int i = 0; i < 4; ++i) { ctx->acc_ms[i] = 0; ctx->acc_n[i] = 0; }
+    });
+}
+
+const char *asicp_last_error(const asicp_ctx *ctx)
+{
+    if (!ctx) return "NULL context";
+    return ctx->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// Internal declarations shared by the kernels and the C-ABI of libasicp.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace asicp {
+
+constexpr int kFwdThreads = 256;       // threads of the matching kernel
+constexpr int kRefTile = 2048;         // object points staged in shared memory per tile
+constexpr int kFwdSums = 13;           // per-particle matching sums (see match kernel)
+constexpr int kColSums = 22;           // per-particle collision sums (see collision kernel)
+constexpr int kMaxK = 1024;            // particles per preshape (one update CTA per preshape)
+
+// error word written by device code (host reads it back after synchronising)
+enum : int { kDevOk = 0, kDevNonFinite = 1, kDevTimeout = 2 };
+
+struct SdfMeta {           // one preshape's grid
+    const float *grid;     // nx*ny*nz values, x fastest, positive inside the gripper
+    int nx, ny, nz;
+    float ox, oy, oz;      // position of node (0,0,0)
+    float voxel;
+};
+
+// Rotation of a (unit) quaternion in the homogeneous form
+// R = (w^2 - |v|^2) I + 2 v v^T + 2 w [v]_x, evaluated with explicit
+// round-to-nearest operations so every kernel gets bit-identical matrices.
+__device__ __forceinline__ void quat_rot_f32(float w, float x, float y, float z, float R[9])
+{
+    float a = __fsub_rn(__fmul_rn(w, w), __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z)));
+    float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
+    float xy = __fmul_rn(x, y), xz = __fmul_rn(x, z), yz = __fmul_rn(y, z);
+    float wx = __fmul_rn(w, x), wy = __fmul_rn(w, y), wz = __fmul_rn(w, z);
+    R[0] = __fadd_rn(a, __fmul_rn(2.f, xx));
+    R[1] = __fmul_rn(2.f, __fsub_rn(xy, wz));
+    R[2] = __fmul_rn(2.f, __fadd_rn(xz, wy));
+    R[3] = __fmul_rn(2.f, __fadd_rn(xy, wz));
+    R[4] = __fadd_rn(a, __fmul_rn(2.f, yy));
+    R[5] = __fmul_rn(2.f, __fsub_rn(yz, wx));
+    R[6] = __fmul_rn(2.f, __fsub_rn(xz, wy));
+    R[7] = __fmul_rn(2.f, __fadd_rn(yz, wx));
+    R[8] = __fadd_rn(a, __fmul_rn(2.f, zz));
+}
+
+__device__ __forceinline__ void quat_rot_f64(double w, double x, double y, double z, double R[9])
+{
+    double a = w * w - (x * x + y * y + z * z);
+    R[0] = a + 2 * x * x;         R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);   R[4] = a + 2 * y * y;       R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);   R[7] = 2 * (y * z + w * x); R[8] = a + 2 * z * z;
+}
+
+// s' = R s + t in float32, fixed operation order (shared by every kernel that
+// needs transformed gripper points, so forward and reverse matching agree).
+__device__ __forceinline__ float3 xform_f32(const float R[9], float tx, float ty, float tz, float sx, float sy, float sz)
+{
+    float3 o;
+    o.x = __fmaf_rn(R[0], sx, __fmaf_rn(R[1], sy, __fmaf_rn(R[2], sz, tx)));
+    o.y = __fmaf_rn(R[3], sx, __fmaf_rn(R[4], sy, __fmaf_rn(R[5], sz, ty)));
+    o.z = __fmaf_rn(R[6], sx, __fmaf_rn(R[7], sy, __fmaf_rn(R[8], sz, tz)));
+    return o;
+}
+
+// Exact-form squared distance |a - b|^2 in float32, fixed order.
+__device__ __forceinline__ float dist2_f32(float ax, float ay, float az, float bx, float by, float bz)
+{
+    float dx = __fsub_rn(ax, bx), dy = __fsub_rn(ay, by), dz = __fsub_rn(az, bz);
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
+template <int N>
+__device__ __forceinline__ void warp_sum_f64(double (&v)[N])
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < N; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+}
+
+// ---------------------------------------------------------------- launchers
+// Every launcher enqueues on `st` and returns the launch status.
+struct FwdArgs {
+    const float4 *S;         // [P][N] gripper points (gripper frame)
+    const float *theta;      // [P*K][8]
+    const float4 *R;         // [M] object points
+    int M, N, K, PK, nb;     // nb = query blocks per particle
+    double *fsums;           // [PK][nb][kFwdSums]
+    int *dbg_idx;            // [PK][N] or null
+    float *dbg_d2;           // [PK][N] or null
+    float *dbg_sp;           // [PK][N][3] or null
+};
+int fwd_queries_per_block();
+cudaError_t launch_fwd_match(const FwdArgs &a, cudaStream_t st);
+
+struct CollideArgs {
+    const float4 *C;          // [Mc]
+    int Mc, K, PK, N;
+    const float *theta;       // [PK][8]
+    const SdfMeta *meta;      // [P]
+    int *ncol;                // [PK]
+    int *colidx;              // [PK][Mc]
+    const float4 *S;          // [P][N]
+    double *csums;            // [PK][kColSums]
+    int *dbg_colnn;           // [PK][Mc] or null
+};
+cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st);
+cudaError_t launch_collide_nn(const CollideArgs &a, cudaStream_t st);
+
+struct UpdateArgs {
+    int P, K, N, nb;
+    float *theta;             // [PK][8] in/out
+    const double *fsums;      // [PK][nb][kFwdSums]
+    const double *csums;      // [PK][kColSums]
+    const int *ncol;          // [PK]
+    const double *pconst;     // [P][12]: sum s (3), sum s s^T (xx,xy,xz,yy,yz,zz), pad
+    const double *com;        // [3]
+    double w_com;
+    int mode;                 // 0: evaluate only, 1: SVGD step, 2: SGD step
+    float gamma, eta_svgd, eta_sgd;
+    int bandwidth_mode;
+    float h_fixed;
+    float conv_tol;           // < 0 disables
+    double *cost;             // [PK]
+    double *grad;             // [PK][8]
+    double *prev_cost;        // [PK]
+    int *frozen;              // [PK]
+    float *phi;               // [PK][8]
+    float *h;                 // [P]
+};
+cudaError_t launch_update(const UpdateArgs &a, cudaStream_t st);
+
+cudaError_t launch_pack_points(const float *xyz, int n, float4 *out, int *err, cudaStream_t st);
+cudaError_t launch_check_finite(const float *v, long long n, int *err, cudaStream_t st);
+cudaError_t launch_centroid(const float4 *X, int n, double *out3, cudaStream_t st);
+cudaError_t launch_preshape_consts(const float4 *S, int N, double *out12, cudaStream_t st);
+cudaError_t launch_fibonacci(int P, int K, const double *com, float radius, float *theta, cudaStream_t st);
+cudaError_t launch_set_theta(const float *theta7, int PK, float *theta8, int *err, cudaStream_t st);
+cudaError_t launch_select(const double *cost, const int *ncol, int total, int *order, cudaStream_t st);
+
+}  // namespace asicp

@@ -1,0 +1,440 @@
+// Per-particle cost and gradient, Stein direction and the particle update
+// (Eqs. 3, 7-11, 13-18), plus the small set-up kernels (packing, centroids,
+// Fibonacci initial poses, ranking).
+#include "asicp_internal.cuh"
+
+namespace asicp {
+
+namespace {
+
+// Quaternion gradient g_k = sum_ab (dR_ab/dq_k) E_ab for the homogeneous form
+// R = (w^2 - |v|^2) I + 2 v v^T + 2 w [v]_x, with E = sum_i e_i s_i^T:
+//   dR/dw   = 2 w I + 2 [v]_x
+//   dR/dv_k = -2 v_k I + 2 (e_k v^T + v e_k^T) + 2 w [e_k]_x
+// This equals sum_i J(s_i)^T e_i, the rotation gradient of Eqs. 5 and 17.
+__device__ void quat_grad_from_E(const double q[4], const double E[9], double g[4])
+{
+    const double w = q[0], v[3] = {q[1], q[2], q[3]};
+    const double tr = E[0] + E[4] + E[8];
+    const double kx = E[7] - E[5], ky = E[2] - E[6], kz = E[3] - E[1];   // <[e_k]_x, E>
+    g[0] = 2 * w * tr + 2 * (v[0] * kx + v[1] * ky + v[2] * kz);
+    const double ks[3] = {kx, ky, kz};
+    for (int k = 0; k < 3; ++k) {
+        double rowv = E[k * 3 + 0] * v[0] + E[k * 3 + 1] * v[1] + E[k * 3 + 2] * v[2];
+        double colv = E[0 * 3 + k] * v[0] + E[1 * 3 + k] * v[1] + E[2 * 3 + k] * v[2];
+        g[1 + k] = -2 * v[k] * tr + 2 * rowv + 2 * colv + 2 * w * ks[k];
+    }
+}
+
+// sum_i |R s_i + t - x_i|^2, sum_i (R s_i + t - x_i) and sum_i (R s_i + t - x_i) s_i^T
+// from the linear sums: ss = sum s (3), SS = sum s s^T (9, full), xs = sum x,
+// XS = sum x s^T (9), xx = sum |x|^2, n terms.
+__device__ void residual_moments(const double R[9], const double t[3], double n, const double ss[3],
+                                 const double SS[9], const double xs[3], const double XS[9], double xx,
+                                 double *se2, double Se[3], double E[9])
+{
+    double Rs[3], RtR[9];
+    for (int a = 0; a < 3; ++a) Rs[a] = R[a * 3 + 0] * ss[0] + R[a * 3 + 1] * ss[1] + R[a * 3 + 2] * ss[2];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            RtR[a * 3 + b] = R[0 * 3 + a] * R[0 * 3 + b] + R[1 * 3 + a] * R[1 * 3 + b] + R[2 * 3 + a] * R[2 * 3 + b];
+    double quad = 0.0, cross = 0.0;
+    for (int a = 0; a < 9; ++a) { quad += RtR[a] * SS[a]; cross += R[a] * XS[a]; }
+    const double tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    const double tRs = t[0] * Rs[0] + t[1] * Rs[1] + t[2] * Rs[2];
+    const double tx = t[0] * xs[0] + t[1] * xs[1] + t[2] * xs[2];
+    *se2 = quad + n * tt + xx + 2 * tRs - 2 * tx - 2 * cross;
+    for (int a = 0; a < 3; ++a) Se[a] = Rs[a] + n * t[a] - xs[a];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            E[a * 3 + b] = R[a * 3 + 0] * SS[0 * 3 + b] + R[a * 3 + 1] * SS[1 * 3 + b] + R[a * 3 + 2] * SS[2 * 3 + b] +
+                           t[a] * ss[b] - XS[a * 3 + b];
+}
+
+__device__ __forceinline__ void sym_full(const double *s6, double S[9])
+{
+    S[0] = s6[0]; S[1] = s6[1]; S[2] = s6[2];
+    S[3] = s6[1]; S[4] = s6[3]; S[5] = s6[4];
+    S[6] = s6[2]; S[7] = s6[4]; S[8] = s6[5];
+}
+
+__device__ __forceinline__ float pair_d2(float4 a, float4 b)
+{
+    return dist2_f32(a.x, a.y, a.z, b.x, b.y, b.z);
+}
+
+}  // namespace
+
+// One CTA per preshape, one thread per particle.
+//  1. cost and gradient from the matching sums (Eqs. 13-17) or, for a particle
+//     with colliding points, from the collision sums (Eq. 18 with Eqs. 4-5),
+//     quaternion block projected onto the tangent space at q;
+//  2. convergence bookkeeping (SGD phase);
+//  3. mode 1: median-heuristic bandwidth (exact radix select of the lower
+//     median of |t_i - t_j|^2, i < j), Stein direction of Eq. 8 read as the mean
+//     of Eq. 6 with the kernels of Eqs. 9-10 per block, update of Eq. 7;
+//     mode 2: SGD-ICP update of Eq. 3 (A = I); mode 0: no update.
+__global__ void __launch_bounds__(kMaxK) update_kernel(const UpdateArgs a)
+{
+    extern __shared__ float4 sm[];
+    float4 *sT = sm;                  // [K] t (xyz)
+    float4 *sQ = sm + a.K;            // [K] q (wxyz)
+    float4 *sDt = sm + 2 * a.K;       // [K] -gamma N g_t
+    float4 *sDq = sm + 3 * a.K;       // [K] -gamma N g_q
+    __shared__ unsigned hist[256];
+    __shared__ unsigned s_prefix, s_mask, s_rank;
+
+    const int p = blockIdx.x, j = threadIdx.x, K = a.K;
+    const bool active = j < K;
+    const size_t pk = (size_t)p * K + j;
+    double t[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, g[7] = {0, 0, 0, 0, 0, 0, 0};
+    int frozen = 0;
+    if (active) {
+        const float *th = a.theta + pk * 8;
+        for (int c = 0; c < 3; ++c) t[c] = th[c];
+        for (int c = 0; c < 4; ++c) q[c] = th[3 + c];
+        double R[9];
+        quat_rot_f64(q[0], q[1], q[2], q[3], R);
+        const int nc = a.ncol[pk];
+        double se2, Se[3], E[9], cnt;
+        if (nc == 0) {
+            double fs[kFwdSums];
+            for (int c = 0; c < kFwdSums; ++c) fs[c] = 0.0;
+            for (int b = 0; b < a.nb; ++b)
+                for (int c = 0; c < kFwdSums; ++c) fs[c] += a.fsums[(pk * a.nb + b) * kFwdSums + c];
+            const double *pc = a.pconst + (size_t)p * 12;
+            double SS[9];
+            sym_full(pc + 3, SS);
+            residual_moments(R, t, (double)a.N, pc, SS, fs, fs + 3, fs[12], &se2, Se, E);
+            // TCP-CoM term (Eq. 15) inside the 1/N, weight w_com (Eqs. 16-17)
+            const double tcp[3] = {pc[0] / a.N, pc[1] / a.N, pc[2] / a.N};
+            double ec[3];
+            for (int u = 0; u < 3; ++u)
+                ec[u] = R[u * 3 + 0] * tcp[0] + R[u * 3 + 1] * tcp[1] + R[u * 3 + 2] * tcp[2] + t[u] - a.com[u];
+            se2 += a.w_com * (ec[0] * ec[0] + ec[1] * ec[1] + ec[2] * ec[2]);
+            for (int u = 0; u < 3; ++u) {
+                Se[u] += a.w_com * ec[u];
+                for (int v = 0; v < 3; ++v) E[u * 3 + v] += a.w_com * ec[u] * tcp[v];
+            }
+            cnt = (double)a.N;
+        } else {
+            const double *cs = a.csums + pk * kColSums;
+            double SS[9];
+            sym_full(cs + 3, SS);
+            residual_moments(R, t, (double)nc, cs, SS, cs + 9, cs + 12, cs[21], &se2, Se, E);
+            cnt = (double)nc;
+        }
+        double gq[4];
+        quat_grad_from_E(q, E, gq);
+        for (int u = 0; u < 3; ++u) g[u] = Se[u] / cnt;
+        for (int u = 0; u < 4; ++u) gq[u] /= cnt;
+        const double dq = gq[0] * q[0] + gq[1] * q[1] + gq[2] * q[2] + gq[3] * q[3];
+        for (int u = 0; u < 4; ++u) g[3 + u] = gq[u] - dq * q[u];
+        const double cost = se2 / cnt;
+        a.cost[pk] = cost;
+        for (int u = 0; u < 7; ++u) a.grad[pk * 8 + u] = g[u];
+        frozen = a.frozen[pk];
+        if (a.mode == 2 && a.conv_tol >= 0.f) {
+            const double prev = a.prev_cost[pk];
+            if (nc > 0) frozen = 0;
+            else if (prev >= 0.0 && fabs(cost - prev) <= (double)a.conv_tol * prev) frozen = 1;
+            a.frozen[pk] = frozen;
+        }
+        if (a.mode != 0) a.prev_cost[pk] = cost;
+    }
+    if (a.mode == 0) return;
+
+    if (a.mode == 2) {
+        if (active) {
+            float *th = a.theta + pk * 8;
+            for (int u = 0; u < 7; ++u) a.phi[pk * 8 + u] = 0.f;
+            if (!frozen) {
+                double nt[3], nq[4];
+                for (int u = 0; u < 3; ++u) nt[u] = t[u] - (double)a.eta_sgd * g[u];
+                for (int u = 0; u < 4; ++u) nq[u] = q[u] - (double)a.eta_sgd * g[3 + u];
+                const double nn = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
+                for (int u = 0; u < 3; ++u) th[u] = (float)nt[u];
+                for (int u = 0; u < 4; ++u) th[3 + u] = (float)(nq[u] / nn);
+            }
+        }
+        if (j == 0) a.h[p] = 0.f;
+        return;
+    }
+
+    // ---------------------------------------------------------- SVGD phase
+    const float gN = -a.gamma * (float)a.N;
+    if (active) {
+        const float *th = a.theta + pk * 8;
+        sT[j] = make_float4(th[0], th[1], th[2], 0.f);
+        sQ[j] = make_float4(th[3], th[4], th[5], th[6]);
+        sDt[j] = make_float4(gN * (float)g[0], gN * (float)g[1], gN * (float)g[2], 0.f);
+        sDq[j] = make_float4(gN * (float)g[3], gN * (float)g[4], gN * (float)g[5], gN * (float)g[6]);
+    }
+    __syncthreads();
+
+    float h;
+    if (a.bandwidth_mode == 1) {
+        h = a.h_fixed;
+    } else if (K < 2) {
+        h = 1.f;
+    } else {
+        // exact lower median of the K(K-1)/2 squared distances by 4 passes of
+        // 8-bit radix selection on their (non-negative) float bit patterns
+        if (j == 0) {
+            const unsigned long long L = (unsigned long long)K * (K - 1) / 2;
+            s_rank = (unsigned)((L - 1) / 2);
+            s_prefix = 0u;
+            s_mask = 0u;
+        }
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            for (int b = j; b < 256; b += blockDim.x) hist[b] = 0u;
+            __syncthreads();
+            const unsigned prefix = s_prefix, mask = s_mask;
+            if (active) {
+                const float4 ti = sT[j];
+                for (int jj = j + 1; jj < K; ++jj) {
+                    const unsigned bits = __float_as_uint(pair_d2(ti, sT[jj]));
+                    if ((bits & mask) == prefix) atomicAdd(&hist[(bits >> shift) & 255u], 1u);
+                }
+            }
+            __syncthreads();
+            if (j == 0) {
+                unsigned rank = s_rank, cum = 0u;
+                int b = 0;
+                for (; b < 255; ++b) {
+                    if (rank < cum + hist[b]) break;
+                    cum += hist[b];
+                }
+                s_rank = rank - cum;
+                s_prefix = prefix | ((unsigned)b << shift);
+                s_mask = mask | (255u << shift);
+            }
+            __syncthreads();
+        }
+        const double med = (double)__uint_as_float(s_prefix);
+        h = (float)(med / log((double)K));
+        h = fmaxf(h, 1e-12f);
+    }
+    if (j == 0) a.h[p] = h;
+
+    if (active) {
+        const float4 ti = sT[j], qi = sQ[j];
+        const float inv_h = 1.f / h, two_h = 2.f / h;
+        float ft0 = 0.f, ft1 = 0.f, ft2 = 0.f, fq0 = 0.f, fq1 = 0.f, fq2 = 0.f, fq3 = 0.f, sgn = 0.f;
+        for (int jj = 0; jj < K; ++jj) {
+            const float4 tj = sT[jj], qj = sQ[jj], dt = sDt[jj], dq = sDq[jj];
+            const float ex = ti.x - tj.x, ey = ti.y - tj.y, ez = ti.z - tj.z;
+            const float kt = expf(-(ex * ex + ey * ey + ez * ez) * inv_h);
+            ft0 += kt * (dt.x + two_h * ex);
+            ft1 += kt * (dt.y + two_h * ey);
+            ft2 += kt * (dt.z + two_h * ez);
+            const float c = qj.x * qi.x + qj.y * qi.y + qj.z * qi.z + qj.w * qi.w;
+            fq0 += c * dq.x; fq1 += c * dq.y; fq2 += c * dq.z; fq3 += c * dq.w;
+            sgn += c < 0.f ? -1.f : 1.f;
+        }
+        const float invK = 1.f / (float)K;
+        float f[7] = {ft0 * invK, ft1 * invK, ft2 * invK,
+                      (fq0 + sgn * qi.x) * invK, (fq1 + sgn * qi.y) * invK,
+                      (fq2 + sgn * qi.z) * invK, (fq3 + sgn * qi.w) * invK};
+        // tangent projection at q_i (removes the radial kernel-gradient term)
+        const float d = f[3] * qi.x + f[4] * qi.y + f[5] * qi.z + f[6] * qi.w;
+        f[3] -= d * qi.x; f[4] -= d * qi.y; f[5] -= d * qi.z; f[6] -= d * qi.w;
+        float *th = a.theta + pk * 8;
+        for (int u = 0; u < 7; ++u) a.phi[pk * 8 + u] = f[u];
+        const double es = a.eta_svgd;
+        double nq[4] = {qi.x + es * f[3], qi.y + es * f[4], qi.z + es * f[5], qi.w + es * f[6]};
+        const double nn = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
+        th[0] = (float)(ti.x + es * f[0]);
+        th[1] = (float)(ti.y + es * f[1]);
+        th[2] = (float)(ti.z + es * f[2]);
+        for (int u = 0; u < 4; ++u) th[3 + u] = (float)(nq[u] / nn);
+    }
+}
+
+cudaError_t launch_update(const UpdateArgs &a, cudaStream_t st)
+{
+    const int threads = ((a.K + 31) / 32) * 32;
+    const size_t smem = sizeof(float4) * 4 * (size_t)a.K;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    update_kernel<<<a.P, threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ set-up kernels
+__global__ void pack_points_kernel(const float *xyz, int n, float4 *out, int *err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float x = xyz[3 * (size_t)i], y = xyz[3 * (size_t)i + 1], z = xyz[3 * (size_t)i + 2];
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) atomicExch(err, kDevNonFinite);
+    out[i] = make_float4(x, y, z, 0.f);
+}
+
+cudaError_t launch_pack_points(const float *xyz, int n, float4 *out, int *err, cudaStream_t st)
+{
+    pack_points_kernel<<<(n + 255) / 256, 256, 0, st>>>(xyz, n, out, err);
+    return cudaGetLastError();
+}
+
+__global__ void check_finite_kernel(const float *v, long long n, int *err)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(v[i])) atomicExch(err, kDevNonFinite);
+}
+
+cudaError_t launch_check_finite(const float *v, long long n, int *err, cudaStream_t st)
+{
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    check_finite_kernel<<<(int)blocks, 256, 0, st>>>(v, n, err);
+    return cudaGetLastError();
+}
+
+// Deterministic single-CTA float64 reductions (fixed thread striding + fixed tree).
+template <int NV, class F>
+__device__ void block_sum_f64(int n, F term, double *out)
+{
+    __shared__ double red[32][NV];
+    double acc[NV];
+    for (int c = 0; c < NV; ++c) acc[c] = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) term(i, acc);
+    warp_sum_f64(acc);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int c = 0; c < NV; ++c) red[warp][c] = acc[c];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+__global__ void centroid_kernel(const float4 *X, int n, double *out3)
+{
+    __shared__ double tmp[3];
+    block_sum_f64<3>(n, [&](int i, double *acc) {
+        const float4 x = X[i];
+        acc[0] += x.x; acc[1] += x.y; acc[2] += x.z;
+    }, tmp);
+    __syncthreads();
+    if (threadIdx.x < 3) out3[threadIdx.x] = tmp[threadIdx.x] / n;
+}
+
+cudaError_t launch_centroid(const float4 *X, int n, double *out3, cudaStream_t st)
+{
+    centroid_kernel<<<1, 1024, 0, st>>>(X, n, out3);
+    return cudaGetLastError();
+}
+
+__global__ void preshape_consts_kernel(const float4 *S, int N, double *out12)
+{
+    __shared__ double tmp[9];
+    block_sum_f64<9>(N, [&](int i, double *acc) {
+        const float4 s = S[i];
+        const double x = s.x, y = s.y, z = s.z;
+        acc[0] += x; acc[1] += y; acc[2] += z;
+        acc[3] = fma(x, x, acc[3]); acc[4] = fma(x, y, acc[4]); acc[5] = fma(x, z, acc[5]);
+        acc[6] = fma(y, y, acc[6]); acc[7] = fma(y, z, acc[7]); acc[8] = fma(z, z, acc[8]);
+    }, tmp);
+    __syncthreads();
+    if (threadIdx.x < 9) out12[threadIdx.x] = tmp[threadIdx.x];
+    if (threadIdx.x >= 9 && threadIdx.x < 12) out12[threadIdx.x] = 0.0;
+}
+
+cudaError_t launch_preshape_consts(const float4 *S, int N, double *out12, cudaStream_t st)
+{
+    preshape_consts_kernel<<<1, 1024, 0, st>>>(S, N, out12);
+    return cudaGetLastError();
+}
+
+// Fibonacci sphere of K directions around the CoM (Section V); the same set for
+// every preshape.  u_j: z = 1 - (2j+1)/K, azimuth j * pi * (3 - sqrt 5);
+// t_j = CoM + radius u_j; q_j the smallest rotation taking +z (the approach
+// axis) to -u_j, pi about x when -u_j = -z.
+__global__ void fibonacci_kernel(int P, int K, const double *com, float radius, float *theta)
+{
+    const int pk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pk >= P * K) return;
+    const int j = pk % K;
+    const double ga = 3.14159265358979323846 * (3.0 - sqrt(5.0));
+    const double z = 1.0 - (2.0 * j + 1.0) / K;
+    const double rho = sqrt(fmax(0.0, 1.0 - z * z));
+    double sa, ca;
+    sincos(j * ga, &sa, &ca);
+    const double u[3] = {rho * ca, rho * sa, z};
+    float *th = theta + (size_t)pk * 8;
+    for (int a = 0; a < 3; ++a) th[a] = (float)(com[a] + (double)radius * u[a]);
+    const double w = 1.0 - u[2];
+    if (w < 1e-12) {
+        th[3] = 0.f; th[4] = 1.f; th[5] = 0.f; th[6] = 0.f;
+    } else {
+        const double qv[4] = {w, u[1], -u[0], 0.0};
+        const double n = sqrt(qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2]);
+        for (int a = 0; a < 4; ++a) th[3 + a] = (float)(qv[a] / n);
+    }
+    th[7] = 0.f;
+}
+
+cudaError_t launch_fibonacci(int P, int K, const double *com, float radius, float *theta, cudaStream_t st)
+{
+    const int n = P * K;
+    fibonacci_kernel<<<(n + 255) / 256, 256, 0, st>>>(P, K, com, radius, theta);
+    return cudaGetLastError();
+}
+
+__global__ void set_theta_kernel(const float *theta7, int PK, float *theta8, int *err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= PK) return;
+    const float *s = theta7 + (size_t)i * 7;
+    float *d = theta8 + (size_t)i * 8;
+    bool ok = true;
+    for (int a = 0; a < 7; ++a) ok = ok && isfinite(s[a]);
+    const double n = sqrt((double)s[3] * s[3] + (double)s[4] * s[4] + (double)s[5] * s[5] + (double)s[6] * s[6]);
+    if (!ok || !(n > 0.0)) {
+        atomicExch(err, kDevNonFinite);
+        return;
+    }
+    for (int a = 0; a < 3; ++a) d[a] = s[a];
+    for (int a = 0; a < 4; ++a) d[3 + a] = (float)((double)s[3 + a] / n);
+    d[7] = 0.f;
+}
+
+cudaError_t launch_set_theta(const float *theta7, int PK, float *theta8, int *err, cudaStream_t st)
+{
+    set_theta_kernel<<<(PK + 255) / 256, 256, 0, st>>>(theta7, PK, theta8, err);
+    return cudaGetLastError();
+}
+
+// Ranking for Algorithm 1's argmin: non-colliding first, ascending cost (NaN
+// last), ties to the lower flat index.  Each particle counts the particles that
+// precede it, which gives a dense, deterministic order.
+__global__ void select_kernel(const double *cost, const int *ncol, int total, int *order)
+{
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int ci = ncol[i] > 0;
+        double vi = cost[i];
+        if (isnan(vi)) vi = __longlong_as_double(0x7ff0000000000000LL);
+        int rank = 0;
+        for (int k = 0; k < total; ++k) {
+            const int ck = ncol[k] > 0;
+            double vk = cost[k];
+            if (isnan(vk)) vk = __longlong_as_double(0x7ff0000000000000LL);
+            rank += (ck < ci) || (ck == ci && (vk < vi || (vk == vi && k < i)));
+        }
+        order[rank] = i;
+    }
+}
+
+cudaError_t launch_select(const double *cost, const int *ncol, int total, int *order, cudaStream_t st)
+{
+    select_kernel<<<1, 1024, 0, st>>>(cost, ncol, total, order);
+    return cudaGetLastError();
+}
+
+}  // namespace asicp

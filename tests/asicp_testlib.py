@@ -1,0 +1,191 @@
+"""Helpers shared by the parity tests: set a workload up on both sides and
+compare the CUDA path (through the C-ABI binding) with the FP64 oracle.
+
+Tolerances (derived in the design doc's parity section):
+* correspondences: bit-exact, except near-ties where the FP64 squared distance
+  of the GPU's choice exceeds the minimum by at most NEAR_TIE_REL relative;
+* collision flags: equal, except points whose FP64 SDF value lies within
+  PHI_TOL of zero (float32 transform and interpolation error is ~1e-7 m);
+* cost and gradient: relative error <= COST_GRAD_REL per particle and per block
+  (translation, quaternion) when both are evaluated on the same pairs.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from paper_2412_08346_gb300 import asicp, synth
+
+NEAR_TIE_REL = 1e-6
+PHI_TOL = 1e-6
+COST_GRAD_REL = 1e-4
+
+
+def make_config(w: synth.Workload, stream=None, debug=True, profile=False, **over):
+    cfg = asicp.asicp_config_default(P=len(w.preshapes), K=w.K, k_max=w.k_max, k_stein=w.k_stein,
+                                     schedule=w.schedule, g0=w.g0, g1=w.g1, C_cycles=w.C_cycles, p_exp=w.p_exp,
+                                     conv_tol=-1.0, debug=int(debug), profile=int(profile))
+    if stream is not None:
+        cfg.cuda_stream = stream
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def upload(ctx, w: synth.Workload, obj_index=0, device=True):
+    """Set object and preshapes; device=True passes CUDA tensors, else host numpy arrays."""
+    import torch
+    obj = w.objects[obj_index].points
+
+    def arr(x):
+        x = np.ascontiguousarray(x)
+        return torch.from_numpy(x).cuda() if device else x
+    keep = []
+    R = arr(obj)
+    keep.append(R)
+    asicp.asicp_set_object(ctx, R)
+    for p, pre in enumerate(w.preshapes):
+        S, g = arr(pre.S), arr(pre.sdf)
+        keep += [S, g]
+        asicp.asicp_set_gripper_sdf(ctx, p, S, g, pre.origin, pre.voxel)
+    if device:
+        torch.cuda.synchronize()
+    return keep
+
+
+def make_oracle(w: synth.Workload, obj_index=0):
+    import oracle
+    return oracle.Oracle(np.stack([pre.S for pre in w.preshapes]),
+                         [(pre.sdf, pre.origin, pre.voxel) for pre in w.preshapes],
+                         w.objects[obj_index].points, K=w.K)
+
+
+def read_state(ctx, P, K, N, Mc, debug=True):
+    PK = P * K
+    st = {"theta": np.zeros((PK, 7), np.float32), "cost": np.zeros(PK), "grad": np.zeros((PK, 7)),
+          "phi": np.zeros((PK, 7), np.float32), "ncol": np.zeros(PK, np.int32), "frozen": np.zeros(PK, np.int32),
+          "h": np.zeros(P, np.float32)}
+    if debug:
+        st.update({"nn_idx": np.zeros((PK, N), np.int32), "nn_d2": np.zeros((PK, N), np.float32),
+                   "s_prime": np.zeros((PK, N, 3), np.float32), "col_list": np.zeros((PK, Mc), np.int32),
+                   "col_nn": np.zeros((PK, Mc), np.int32)})
+    asicp.asicp_get_state(ctx, **st)
+    return st
+
+
+def read_theta(ctx, PK):
+    th = np.zeros((PK, 7), np.float32)
+    asicp.asicp_get_state(ctx, theta=th)
+    return th
+
+
+def check_nn(queries32, refs32, idx_gpu, report, kind="nn"):
+    """Correspondences against the FP64 argmin over the GPU's own float32 queries."""
+    import oracle
+    q = np.asarray(queries32, np.float64).reshape(-1, 3)
+    r = np.asarray(refs32, np.float64).reshape(-1, 3)
+    idx_o, d2_o = oracle.nn(q, r)
+    g = np.asarray(idx_gpu).reshape(-1)
+    mism = np.nonzero(g != idx_o)[0]
+    report[f"{kind}_total"] = report.get(f"{kind}_total", 0) + len(g)
+    if len(mism):
+        d2_g = ((q[mism] - r[g[mism]]) ** 2).sum(1)
+        ok = d2_g - d2_o[mism] <= NEAR_TIE_REL * d2_o[mism]
+        report[f"{kind}_near_ties"] = report.get(f"{kind}_near_ties", 0) + int(ok.sum())
+        bad = mism[~ok]
+        assert len(bad) == 0, (f"{len(bad)} correspondences differ beyond a near-tie, e.g. query {bad[0]}: gpu "
+                               f"{g[bad[0]]} d2={((q[bad[0]] - r[g[bad[0]]]) ** 2).sum():.9e} vs oracle "
+                               f"{idx_o[bad[0]]} d2={d2_o[bad[0]]:.9e}")
+    return idx_o
+
+
+def rel_err(a, b, floor=0.0):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), floor)
+
+
+def check_step(orc, w, before_theta, st, k, report, check_update=True, sample=None):
+    """Teacher-forced comparison of one GPU step against the oracle, particle by particle."""
+    import oracle
+    P, K, N = orc.P, orc.K, orc.N
+    Mc = len(orc.Cc)
+    pks = range(P * K) if sample is None else sample
+    flips = set()
+    for pk in pks:
+        p = pk // K
+        th = before_theta[pk].astype(np.float64)
+        # forward pairs: exact or near-tie against FP64 argmin over the GPU's s'
+        check_nn(st["s_prime"][pk], orc.R, st["nn_idx"][pk], report)
+        # collision flags
+        lst_o, vals = orc.collision_points(p, th)
+        n_g = int(st["ncol"][pk])
+        lst_g = st["col_list"][pk, :n_g]
+        if not np.array_equal(lst_g, lst_o):
+            diff = np.setxor1d(lst_g, lst_o)
+            assert np.all(np.abs(vals[diff]) <= PHI_TOL), f"particle {pk}: collision flags differ beyond |phi| <= {PHI_TOL}"
+            flips.add(pk)
+            report["col_flips"] = report.get("col_flips", 0) + len(diff)
+            continue
+        report["col_points"] = report.get("col_points", 0) + n_g
+        if n_g > 0:
+            Cc = orc.Cc
+            check_nn(Cc[lst_g], st["s_prime"][pk], st["col_nn"][pk, :n_g], report, kind="col_nn")
+            cost_o, g_o = orc.collision_terms(p, th, lst_g, st["col_nn"][pk, :n_g])
+            report["colliding_particles"] = report.get("colliding_particles", 0) + 1
+        else:
+            cost_o, g_o = orc.match_terms(p, th, st["nn_idx"][pk])
+        assert abs(st["cost"][pk] - cost_o) <= COST_GRAD_REL * abs(cost_o), f"particle {pk}: cost {st['cost'][pk]} vs {cost_o}"
+        for blk in (slice(0, 3), slice(3, 7)):
+            e = rel_err(st["grad"][pk, blk], g_o[blk], floor=1e-300)
+            report["max_grad_rel"] = max(report.get("max_grad_rel", 0.0), e)
+            assert e <= COST_GRAD_REL, f"particle {pk}: gradient block {blk} relative error {e:.3e}"
+        report["max_cost_rel"] = max(report.get("max_cost_rel", 0.0), abs(st["cost"][pk] - cost_o) / abs(cost_o))
+    report["particles"] = report.get("particles", 0) + len(list(pks))
+    if not check_update or sample is not None:
+        return flips
+    # update: oracle's Stein / SGD step applied to the GPU's gradients (same pairs)
+    svgd = k < w.k_stein
+    for p in range(P):
+        sl = slice(p * K, (p + 1) * K)
+        th = before_theta[sl].astype(np.float64)
+        if svgd:
+            gam = oracle.gamma(k, w.k_max, w.schedule, w.C_cycles, w.p_exp, w.g0, w.g1)
+            h = oracle.bandwidth(th)
+            assert abs(st["h"][p] - h) <= 1e-5 * h, f"bandwidth {st['h'][p]} vs {h}"
+            phi = oracle.stein_direction(th, st["grad"][sl], N, gam, h)
+            scale = stein_term_scale(th, st["grad"][sl], N, gam, h)
+            for j in range(K):
+                for b, blk in enumerate((slice(0, 3), slice(3, 7))):
+                    e = np.linalg.norm(st["phi"][sl][j, blk] - phi[j, blk])
+                    # relative error, with a floor for sums that cancel: float32 summation of K terms
+                    # of magnitude `scale` carries an absolute error of ~sqrt(K) * 6e-8 * scale
+                    tol = COST_GRAD_REL * np.linalg.norm(phi[j, blk]) + STEIN_ABS_REL * scale[j, b]
+                    report["max_phi_err_over_tol"] = max(report.get("max_phi_err_over_tol", 0.0), e / tol)
+                    assert e <= tol, f"preshape {p} particle {j}: Stein direction error {e:.3e} > {tol:.3e}"
+            new = th + phi / N
+        else:
+            new = th - st["grad"][sl]
+        new[:, 3:] /= np.linalg.norm(new[:, 3:], axis=1, keepdims=True)
+        err = np.abs(st["theta"][sl].astype(np.float64) - new).max()
+        report["max_update_abs"] = max(report.get("max_update_abs", 0.0), err)
+        assert err <= 2e-6, f"preshape {p}: updated poses differ by {err:.3e}"
+    return flips
+
+
+STEIN_ABS_REL = 1e-5
+
+
+def stein_term_scale(theta, grad, N, gam, h):
+    """Mean magnitude of the terms the Stein direction of each particle sums (per block)."""
+    t, q = theta[:, :3], theta[:, 3:]
+    dt = t[:, None, :] - t[None, :, :]                       # [i, j]
+    kt = np.exp(-(dt ** 2).sum(-1) / h)
+    c = np.abs(q @ q.T)
+    st = (kt * (gam * N * np.linalg.norm(grad[None, :, :3], axis=-1) +
+                (2 / h) * np.linalg.norm(dt, axis=-1))).mean(1)
+    sq = (c * gam * N * np.linalg.norm(grad[None, :, 3:], axis=-1) + 1.0).mean(1)
+    return np.stack([st, sq], 1)
+
+
+def geodesic_angle(q1, q2):
+    d = np.abs((np.asarray(q1, np.float64) * np.asarray(q2, np.float64)).sum(-1))
+    return 2 * np.arccos(np.clip(d / (np.linalg.norm(q1, axis=-1) * np.linalg.norm(q2, axis=-1)), -1, 1))

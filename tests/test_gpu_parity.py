@@ -1,0 +1,214 @@
+"""CUDA path (through the C-ABI) against the FP64 oracle.
+
+Teacher-forced single steps compare every output of the step on the same poses;
+free-running runs compare final poses; the full-size workload is checked on
+sampled particles; edge cases cover ragged tiles, tiny and degenerate sizes.
+"""
+import numpy as np
+import pytest
+
+from paper_2412_08346_gb300 import asicp, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import asicp_testlib as tl  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ctx(w, stream, **over):
+    cfg = tl.make_config(w, stream=stream, **over)
+    return asicp.asicp_create(cfg)
+
+
+def _teacher_forced_run(w, stream, steps, report, device=True, theta0=None, sample=None, **over):
+    """Run `steps` GPU steps; before each, read the GPU's poses and compare the step with the oracle."""
+    orc = tl.make_oracle(w)
+    ctx = _ctx(w, stream, **over)
+    try:
+        keep = tl.upload(ctx, w, device=device)
+        P, K, N, Mc = len(w.preshapes), w.K, w.preshapes[0].S.shape[0], len(w.objects[0].points)
+        if theta0 is None:
+            com = orc.R.mean(0)
+            import oracle
+            theta0 = np.tile(oracle.fibonacci_init(K, com, 0.15), (P, 1)).astype(np.float32)
+        asicp.asicp_set_state(ctx, np.ascontiguousarray(theta0, dtype=np.float32), 0)
+        for k in steps:
+            before = tl.read_theta(ctx, P * K)
+            asicp.asicp_set_state(ctx, before, k)
+            asicp.asicp_step(ctx, k)
+            st = tl.read_state(ctx, P, K, N, Mc)
+            tl.check_step(orc, w, before, st, k, report, sample=sample)
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
+    return report
+
+
+def test_small_box_teacher_forced_steps(stream):
+    """1 preshape, K=32, N=256, M=512: every step of a 50-step trajectory, teacher-forced."""
+    w = synth.small_box_case()
+    rep = _teacher_forced_run(w, stream, range(w.k_max), {})
+    print("small box:", rep)
+    assert rep["nn_total"] == 50 * 32 * 256
+    assert rep.get("nn_near_ties", 0) <= 1e-4 * rep["nn_total"]
+
+
+def test_multi_preshape_ragged_tiles_with_collisions(stream):
+    """3 preshapes, N=1000 (ragged query block), M=5000 (two full tiles + a ragged one), poses close to
+    the object so collisions occur; SVGD and SGD phases."""
+    w = synth.custom_case(P=3, K=24, N=1000, M=5000, grid=40, k_max=12, seed=7, k_stein=6)
+    import oracle
+    com = w.objects[0].points.astype(np.float64).mean(0)
+    th = oracle.fibonacci_init(w.K, com, 0.05)          # 5 cm: fingers reach into the object
+    theta0 = np.tile(th, (3, 1)).astype(np.float32)
+    rep = _teacher_forced_run(w, stream, [0, 1, 2, 5, 6, 7, 11], {}, theta0=theta0)
+    print("ragged + collisions:", rep)
+    assert rep.get("colliding_particles", 0) > 0, "the case is meant to exercise the collision path"
+
+
+def test_host_pointer_inputs_match_device_pointer_inputs(stream):
+    w = synth.custom_case(P=2, K=16, N=300, M=700, grid=24, k_max=4, seed=11)
+    outs = []
+    for device in (True, False):
+        ctx = _ctx(w, stream)
+        try:
+            keep = tl.upload(ctx, w, device=device)
+            asicp.asicp_run(ctx)
+            th = np.zeros((7 * 8,), np.float32)
+            cost = np.zeros(8, np.float32)
+            pre = np.zeros(8, np.int32)
+            n = asicp.asicp_best_grasps(ctx, 8, th, cost, pre)
+            assert n == 8
+            outs.append((th.copy(), cost.copy(), pre.copy()))
+            del keep
+        finally:
+            asicp.asicp_destroy(ctx)
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+
+
+def test_free_running_small_box_final_poses(stream):
+    """50 free-running iterations on both sides: final poses within 1 mm / 1e-3 rad."""
+    import oracle
+    w = synth.small_box_case()
+    orc = tl.make_oracle(w)
+    sched = orc.schedule(k_max=w.k_max, k_stein=w.k_stein, schedule=w.schedule, g0=w.g0, g1=w.g1, N=orc.N)
+    theta0 = oracle.fibonacci_init(w.K, orc.R.mean(0), 0.15)
+    ost, order = orc.run(theta0.astype(np.float32).astype(np.float64)[None], sched, nthreads=4, topk=8)
+    ctx = _ctx(w, stream, debug=False)
+    try:
+        keep = tl.upload(ctx, w)
+        asicp.asicp_run(ctx, np.ascontiguousarray(theta0.astype(np.float32)))
+        th = tl.read_theta(ctx, w.K)
+        best = np.zeros(8 * 7, np.float32)
+        asicp.asicp_best_grasps(ctx, 8, best)
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
+    ot = ost["theta"][0]
+    dpos = np.linalg.norm(th[:, :3] - ot[:, :3], axis=1)
+    dang = tl.geodesic_angle(th[:, 3:], ot[:, 3:])
+    print(f"final pose error: max {dpos.max():.3e} m, {dang.max():.3e} rad; median {np.median(dpos):.3e} m")
+    ok = (dpos <= 1e-3) & (dang <= 1e-3)
+    assert ok.mean() >= 0.9, f"only {ok.sum()} of {len(ok)} particles within 1 mm / 1e-3 rad"
+    assert np.median(dpos) <= 1e-4
+
+
+def test_paper_scale_sampled_step(stream):
+    """3 x 256 particles, N=2048, M=8192, SDF 64^3: one SVGD and one SGD step, sampled particles,
+    in the launch configuration the benchmark uses."""
+    w = synth.paper_scale_case()
+    g = np.random.default_rng(3)
+    sample = sorted(g.choice(w.K * 3, 24, replace=False).tolist())
+    rep = _teacher_forced_run(w, stream, [0, 60], {}, sample=sample)
+    print("paper scale sampled:", rep)
+
+
+def test_single_particle_stein_equals_sgd(stream):
+    """K = 1, gamma = 1: one SVGD step equals one SGD step (Eq. 8 reduces to Eq. 3)."""
+    w = synth.custom_case(P=1, K=1, N=128, M=256, grid=16, k_max=2, seed=5)
+    import oracle
+    th0 = oracle.fibonacci_init(1, w.objects[0].points.astype(np.float64).mean(0), 0.08).astype(np.float32)
+    res = []
+    for k_stein in (2, 0):
+        ctx = _ctx(w, stream, k_stein=k_stein, schedule=1, g0=1.0, g1=1.0)
+        try:
+            keep = tl.upload(ctx, w)
+            asicp.asicp_set_state(ctx, th0, 0)
+            asicp.asicp_step(ctx, 0)
+            res.append(tl.read_theta(ctx, 1))
+            del keep
+        finally:
+            asicp.asicp_destroy(ctx)
+    assert np.abs(res[0] - res[1]).max() <= 1e-6
+
+
+def test_degenerate_sizes(stream):
+    """M = 1 (every point pairs with the one object point), N = 1, K = 2."""
+    w = synth.custom_case(P=1, K=2, N=1, M=1, grid=8, k_max=2, seed=13)
+    rep = _teacher_forced_run(w, stream, [0, 1], {})
+    assert rep["nn_total"] == 4
+
+
+def test_selection_and_determinism(stream):
+    w = synth.custom_case(P=2, K=32, N=256, M=1024, grid=24, k_max=8, seed=17)
+    runs = []
+    for _ in range(2):
+        ctx = _ctx(w, stream)
+        try:
+            keep = tl.upload(ctx, w)
+            asicp.asicp_run(ctx)
+            st = tl.read_state(ctx, 2, 32, 256, 1024, debug=False)
+            best = np.zeros(64 * 7, np.float32)
+            cost = np.zeros(64, np.float32)
+            pre = np.zeros(64, np.int32)
+            asicp.asicp_best_grasps(ctx, 64, best, cost, pre)
+            runs.append((st, best, cost, pre))
+            del keep
+        finally:
+            asicp.asicp_destroy(ctx)
+    (a, ba, ca, pa), (b, bb, cb, pb) = runs
+    for key in ("theta", "cost", "grad", "ncol"):
+        assert np.array_equal(a[key], b[key]), f"{key} differs between identical runs"
+    assert np.array_equal(ba, bb)
+    import oracle
+    order = oracle.select(a["cost"], a["ncol"], 64)
+    assert np.array_equal(pa, order // 32)
+    assert np.allclose(ca, a["cost"][order].astype(np.float32))
+    assert np.array_equal(ba.reshape(64, 7), a["theta"][order])
+
+
+def test_invalid_inputs_are_rejected(stream):
+    w = synth.custom_case(P=1, K=4, N=16, M=32, grid=8, k_max=2, seed=19)
+    ctx = _ctx(w, stream)
+    try:
+        with pytest.raises(asicp.AsicpError) as e:
+            asicp.asicp_step(ctx, 0)
+        assert e.value.status == asicp.ASICP_ERR_STATE
+        bad = w.objects[0].points.copy()
+        bad[3, 1] = np.nan
+        with pytest.raises(asicp.AsicpError) as e:
+            asicp.asicp_set_object(ctx, bad)
+        assert e.value.status == asicp.ASICP_ERR_INVALID_ARG
+        keep = tl.upload(ctx, w)
+        with pytest.raises(asicp.AsicpError) as e:
+            asicp.asicp_step(ctx, 0)            # poses not set yet
+        assert e.value.status == asicp.ASICP_ERR_STATE
+        with pytest.raises(asicp.AsicpError) as e:
+            asicp.asicp_set_gripper_sdf(ctx, 0, w.preshapes[0].S, np.zeros((1, 8, 8), np.float32),
+                                        w.preshapes[0].origin, w.preshapes[0].voxel)
+        assert e.value.status == asicp.ASICP_ERR_INVALID_ARG
+        asicp.asicp_run(ctx)                    # the context is still usable
+        n = asicp.asicp_best_grasps(ctx, 2, np.zeros(14, np.float32))
+        assert n == 2
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
