@@ -5,6 +5,7 @@
 #include "../../include/asicp.h"
 #include "asicp_internal.cuh"
 
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -68,8 +69,9 @@ struct asicp_ctx {
     std::vector<DevMem> grids;
     int k_next = 0;
 
-    DevMem stage, R, C, S, com, pconst, dmeta, theta, fsums, csums, ncol, colidx, cost, grad, prev, frozen,
-        phi, h, order, errw, out7, outc, outi, dbg_idx, dbg_d2, dbg_sp, dbg_colnn;
+    int Mpad = 0;
+    DevMem box, stage, R, Rx, rmax, C, S, com, pconst, dmeta, theta, fsums, csums, ncol, colidx, cost, grad, prev, frozen,
+        phi, h, order, errw, out7, outc, outi, nnidx, dbg_d2, dbg_sp, dbg_colnn;
 
     // profiling: events recorded around launches (kind, start, stop)
     struct Ev { int kind; cudaEvent_t a, b; };
@@ -79,7 +81,7 @@ struct asicp_ctx {
     long long acc_n[4] = {0, 0, 0, 0};
 
     int PK() const { return cfg.P * cfg.K; }
-    int nb() const { return (N + fwd_queries_per_block() - 1) / fwd_queries_per_block(); }
+    int col_chunks() const { return (Mc + kColChunk - 1) / kColChunk; }
     bool ready() const
     {
         if (!object_set || N == 0) return false;
@@ -150,8 +152,9 @@ double gamma_of(const asicp_config &c, int k)
 void ensure_work(asicp_ctx *c)
 {
     const size_t PK = c->PK();
-    c->fsums.ensure(sizeof(double) * PK * c->nb() * kFwdSums, "fsums");
-    c->csums.ensure(sizeof(double) * PK * kColSums, "csums");
+    c->fsums.ensure(sizeof(double) * PK * kFwdSums, "fsums");
+    c->csums.ensure(sizeof(double) * PK * c->col_chunks() * kColSums, "csums");
+    c->nnidx.ensure(sizeof(int) * PK * c->N, "nn_idx");
     c->ncol.ensure(sizeof(int) * PK, "ncol");
     c->colidx.ensure(sizeof(int) * PK * (size_t)c->Mc, "colidx");
     c->cost.ensure(sizeof(double) * PK, "cost");
@@ -165,7 +168,6 @@ void ensure_work(asicp_ctx *c)
     c->outc.ensure(sizeof(float) * PK, "outc");
     c->outi.ensure(sizeof(int) * PK, "outi");
     if (c->cfg.debug) {
-        c->dbg_idx.ensure(sizeof(int) * PK * c->N, "dbg_idx");
         c->dbg_d2.ensure(sizeof(float) * PK * c->N, "dbg_d2");
         c->dbg_sp.ensure(sizeof(float) * PK * c->N * 3, "dbg_sp");
         c->dbg_colnn.ensure(sizeof(int) * PK * (size_t)c->Mc, "dbg_colnn");
@@ -213,10 +215,12 @@ void iterate(asicp_ctx *c, int mode, float gamma)
     fa.S = c->S.as<float4>();
     fa.theta = c->theta.as<float>();
     fa.R = c->R.as<float4>();
-    fa.M = c->M; fa.N = c->N; fa.K = c->cfg.K; fa.PK = PK; fa.nb = c->nb();
-    fa.fsums = c->fsums.as<double>();
+    fa.Rx = c->Rx.as<ulonglong2>();
+    fa.rmax = c->rmax.as<float>();
+    fa.err = c->errw.as<int>();
+    fa.M = c->M; fa.Mpad = c->Mpad; fa.N = c->N; fa.K = c->cfg.K; fa.PK = PK;
+    fa.nn_idx = c->nnidx.as<int>();
     if (c->cfg.debug) {
-        fa.dbg_idx = c->dbg_idx.as<int>();
         fa.dbg_d2 = c->dbg_d2.as<float>();
         fa.dbg_sp = c->dbg_sp.as<float>();
     }
@@ -230,13 +234,16 @@ void iterate(asicp_ctx *c, int mode, float gamma)
     ca.ncol = c->ncol.as<int>();
     ca.colidx = c->colidx.as<int>();
     ca.S = c->S.as<float4>();
+    ca.R = c->R.as<float4>();
+    ca.nn_idx = c->nnidx.as<int>();
+    ca.fsums = c->fsums.as<double>();
     ca.csums = c->csums.as<double>();
     if (c->cfg.debug) ca.dbg_colnn = c->dbg_colnn.as<int>();
     timed(c, kTimeCollide, [&] { return launch_collide(ca, c->st); }, "collision kernel");
     timed(c, kTimeCollideNN, [&] { return launch_collide_nn(ca, c->st); }, "collision matching kernel");
 
     UpdateArgs ua{};
-    ua.P = c->cfg.P; ua.K = c->cfg.K; ua.N = c->N; ua.nb = c->nb();
+    ua.P = c->cfg.P; ua.K = c->cfg.K; ua.N = c->N; ua.Mc = c->Mc;
     ua.theta = c->theta.as<float>();
     ua.fsums = c->fsums.as<double>();
     ua.csums = c->csums.as<double>();
@@ -395,7 +402,12 @@ asicp_status asicp_set_object(asicp_ctx *ctx, const float *R_xyz, int M, const f
             ctx->C.bytes = 0;
         }
         ck(launch_centroid(ctx->R.as<float4>(), M, ctx->com.as<double>(), ctx->st), "centroid");
+        const int Mpad = (M + kRefTilePts - 1) / kRefTilePts * kRefTilePts;
+        ctx->Rx.ensure(sizeof(float4) * (size_t)Mpad, "screening layout");
+        ctx->rmax.ensure(sizeof(float), "rmax");
+        ck(launch_ref_prep(ctx->R.as<float4>(), M, Mpad, ctx->Rx.p, ctx->rmax.as<float>(), ctx->st), "ref prep");
         sync_and_check_err(ctx, "set_object");
+        ctx->Mpad = Mpad;
         ctx->M = M;
         ctx->Mc = mc;
         ctx->object_set = true;
@@ -432,15 +444,34 @@ asicp_status asicp_set_gripper_sdf(asicp_ctx *ctx, int preshape, const float *S_
         ctx->grids[preshape].ensure(sizeof(float) * nv, "sdf grid");
         ck(cudaMemcpyAsync(ctx->grids[preshape].p, sdf, sizeof(float) * nv, cudaMemcpyDefault, ctx->st), "copy sdf");
         ck(launch_check_finite(ctx->grids[preshape].as<float>(), (long long)nv, ctx->errw.as<int>(), ctx->st), "check sdf");
+        // index box of the positive nodes -> gripper-frame box holding every cell that
+        // has a positive corner (trilinear values outside it cannot be > 0)
+        ctx->box.ensure(sizeof(int) * 6, "sdf box");
+        const int box_init[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
+        ck(cudaMemcpyAsync(ctx->box.p, box_init, sizeof(box_init), cudaMemcpyHostToDevice, ctx->st), "init sdf box");
+        ck(launch_sdf_box(ctx->grids[preshape].as<float>(), nx, ny, nz, ctx->box.as<int>(), ctx->st), "sdf box");
+        int box6[6];
+        ck(cudaMemcpyAsync(box6, ctx->box.p, sizeof(box6), cudaMemcpyDeviceToHost, ctx->st), "read sdf box");
+        sync_and_check_err(ctx, "set_gripper_sdf");
         SdfMeta m{};
         m.grid = ctx->grids[preshape].as<float>();
         m.nx = nx; m.ny = ny; m.nz = nz;
         m.ox = org[0]; m.oy = org[1]; m.oz = org[2];
         m.voxel = voxel;
+        for (int a = 0; a < 3; ++a) {
+            if (box6[a] == INT_MAX) {            // no positive node: nothing can collide
+                m.lo[a] = 1.f;
+                m.hi[a] = -1.f;
+            } else {
+                const double margin = 1e-3 * voxel;
+                m.lo[a] = (float)(org[a] + (double)voxel * (box6[a] - 1) - margin);
+                m.hi[a] = (float)(org[a] + (double)voxel * (box6[3 + a] + 1) + margin);
+            }
+        }
         ctx->meta[preshape] = m;
         ck(cudaMemcpyAsync(ctx->dmeta.as<SdfMeta>() + preshape, &ctx->meta[preshape], sizeof(SdfMeta),
                            cudaMemcpyHostToDevice, ctx->st), "copy sdf meta");
-        sync_and_check_err(ctx, "set_gripper_sdf");
+        ck(cudaStreamSynchronize(ctx->st), "set_gripper_sdf");
         ctx->pre_set[preshape] = 1;
         if (ctx->object_set) ensure_work(ctx);
     });
@@ -518,7 +549,7 @@ asicp_status asicp_best_grasps(asicp_ctx *ctx, int topk, float *theta, float *co
             copy_out(cost, ctx->outc.p, sizeof(float) * n, ctx->st, "copy best cost");
             copy_out(preshape, ctx->outi.p, sizeof(int) * n, ctx->st, "copy best preshape");
         }
-        ck(cudaStreamSynchronize(ctx->st), "best_grasps");
+        sync_and_check_err(ctx, "best_grasps");
         if (n_out) *n_out = n;
     });
 }
@@ -555,7 +586,7 @@ asicp_status asicp_get_state(asicp_ctx *ctx, const asicp_state_view *v)
             copy_out(v->ncol, ctx->ncol.p, sizeof(int) * PK, ctx->st, "copy ncol");
             copy_out(v->h, ctx->h.p, sizeof(float) * ctx->cfg.P, ctx->st, "copy h");
             if (ctx->cfg.debug) {
-                copy_out(v->nn_idx, ctx->dbg_idx.p, sizeof(int) * (size_t)PK * ctx->N, ctx->st, "copy nn_idx");
+                copy_out(v->nn_idx, ctx->nnidx.p, sizeof(int) * (size_t)PK * ctx->N, ctx->st, "copy nn_idx");
                 copy_out(v->nn_d2, ctx->dbg_d2.p, sizeof(float) * (size_t)PK * ctx->N, ctx->st, "copy nn_d2");
                 copy_out(v->s_prime, ctx->dbg_sp.p, sizeof(float) * 3 * (size_t)PK * ctx->N, ctx->st, "copy s_prime");
                 copy_out(v->col_list, ctx->colidx.p, sizeof(int) * (size_t)PK * ctx->Mc, ctx->st, "copy col_list");
@@ -565,7 +596,7 @@ asicp_status asicp_get_state(asicp_ctx *ctx, const asicp_state_view *v)
             fail(ASICP_ERR_STATE, "get_state: no step has run since the poses were set");
         }
         copy_out(v->frozen, ctx->frozen.p, sizeof(int) * PK, ctx->st, "copy frozen");
-        ck(cudaStreamSynchronize(ctx->st), "get_state");
+        sync_and_check_err(ctx, "get_state");
     });
 }
 

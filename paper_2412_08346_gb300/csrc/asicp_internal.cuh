@@ -5,8 +5,7 @@
 
 namespace asicp {
 
-constexpr int kFwdThreads = 256;       // threads of the matching kernel
-constexpr int kRefTile = 2048;         // object points staged in shared memory per tile
+constexpr int kRefTilePts = 2048;      // object points per shared-memory tile of the matching kernel
 constexpr int kFwdSums = 13;           // per-particle matching sums (see match kernel)
 constexpr int kColSums = 22;           // per-particle collision sums (see collision kernel)
 constexpr int kMaxK = 1024;            // particles per preshape (one update CTA per preshape)
@@ -19,6 +18,7 @@ struct SdfMeta {           // one preshape's grid
     int nx, ny, nz;
     float ox, oy, oz;      // position of node (0,0,0)
     float voxel;
+    float lo[3], hi[3];    // box (gripper frame) holding every cell with a positive corner
 };
 
 // Rotation of a (unit) quaternion in the homogeneous form
@@ -82,14 +82,18 @@ struct FwdArgs {
     const float4 *S;         // [P][N] gripper points (gripper frame)
     const float *theta;      // [P*K][8]
     const float4 *R;         // [M] object points
-    int M, N, K, PK, nb;     // nb = query blocks per particle
-    double *fsums;           // [PK][nb][kFwdSums]
-    int *dbg_idx;            // [PK][N] or null
+    const ulonglong2 *Rx;    // [Mpad] screening layout (pairs of (-2r, |r|^2)), Mpad = whole tiles
+    const float *rmax;       // max |r| (rounded up)
+    int *err;                // error word
+    int M, Mpad, N, K, PK;
+    int *nn_idx;             // [PK][N] nearest object point per query
     float *dbg_d2;           // [PK][N] or null
     float *dbg_sp;           // [PK][N][3] or null
 };
-int fwd_queries_per_block();
 cudaError_t launch_fwd_match(const FwdArgs &a, cudaStream_t st);
+cudaError_t launch_ref_prep(const float4 *R, int M, int Mpad, void *Rx, float *rmax, cudaStream_t st);
+
+constexpr int kColChunk = 256;         // colliding points per reverse-matching CTA
 
 struct CollideArgs {
     const float4 *C;          // [Mc]
@@ -99,17 +103,20 @@ struct CollideArgs {
     int *ncol;                // [PK]
     int *colidx;              // [PK][Mc]
     const float4 *S;          // [P][N]
-    double *csums;            // [PK][kColSums]
+    const float4 *R;          // [M] object points
+    const int *nn_idx;        // [PK][N] forward correspondences
+    double *fsums;            // [PK][kFwdSums]
+    double *csums;            // [PK][ceil(Mc / kColChunk)][kColSums]
     int *dbg_colnn;           // [PK][Mc] or null
 };
 cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st);
 cudaError_t launch_collide_nn(const CollideArgs &a, cudaStream_t st);
 
 struct UpdateArgs {
-    int P, K, N, nb;
+    int P, K, N, Mc;
     float *theta;             // [PK][8] in/out
-    const double *fsums;      // [PK][nb][kFwdSums]
-    const double *csums;      // [PK][kColSums]
+    const double *fsums;      // [PK][kFwdSums]
+    const double *csums;      // [PK][ceil(Mc / kColChunk)][kColSums]
     const int *ncol;          // [PK]
     const double *pconst;     // [P][12]: sum s (3), sum s s^T (xx,xy,xz,yy,yz,zz), pad
     const double *com;        // [3]
@@ -134,6 +141,7 @@ cudaError_t launch_centroid(const float4 *X, int n, double *out3, cudaStream_t s
 cudaError_t launch_preshape_consts(const float4 *S, int N, double *out12, cudaStream_t st);
 cudaError_t launch_fibonacci(int P, int K, const double *com, float radius, float *theta, cudaStream_t st);
 cudaError_t launch_set_theta(const float *theta7, int PK, float *theta8, int *err, cudaStream_t st);
+cudaError_t launch_sdf_box(const float *grid, int nx, int ny, int nz, int *box6, cudaStream_t st);
 cudaError_t launch_select(const double *cost, const int *ncol, int total, int *order, cudaStream_t st);
 
 }  // namespace asicp

@@ -2,115 +2,360 @@
 //
 // For particle (p, j) and gripper point i the kernel forms s'_i = R_j s_i + t_j
 // (Algorithm 1, "transform the source cloud") and finds the object point with
-// the smallest squared distance, ties to the lowest index (Eq. 1).  The object
-// cloud is streamed through shared memory in tiles; every thread keeps QPT
-// queries in registers, so one broadcast shared-memory read of a reference point
-// feeds QPT distance evaluations.
+// the smallest squared distance, ties to the lowest index (Eq. 1).
 //
-// Instead of per-point residuals the epilogue accumulates, in float64, the
-// sums that the cost and gradient of Eqs. 13-17 are linear in:
-//   sum r_i (3), sum r_i s_i^T (9), sum |r_i|^2 (1)
-// where r_i is the matched object point and s_i the untransformed gripper point.
-// Both are float32, so every product is exact in float64; the update kernel
-// rebuilds sum e_i, sum e_i s_i^T and sum |e_i|^2 (e_i = R s_i + t - r_i) from
-// them in float64 without the rounding of float32 residuals.
+// Search in two stages, exact in the end:
+//  1. Screening.  For every object point r the kernel evaluates
+//     d~(r) = |r|^2 - 2 s'.r  (= |s' - r|^2 - |s'|^2, the same ranking) as three
+//     fused multiply-adds on precomputed (-2r, |r|^2), two object points per
+//     packed f32x2 instruction, and keeps per chunk of kChunk points the chunk
+//     minimum with a 3-input min.  Per query it tracks the best two chunk
+//     minima b1 <= b2 with their chunk ids, and the third-best b3.
+//  2. Exact choice.  |d~ - (|r|^2 - 2 s'.r)| <= delta with
+//     delta = u (4.01 Rmax^2 + 6.02 |s'| Rmax), u = 2^-24, Rmax = max |r|
+//     (float32 rounding of |r|^2 plus three roundings of the FMA chain, with
+//     sum |s_k r_k| <= |s'| |r|).  The true nearest point r* therefore has
+//     d~(r*) <= b1 + 2 delta, so every chunk whose minimum exceeds that bound is
+//     excluded.  If only chunk c1 (and c2 when b2 <= b1 + 2 delta) can hold r*,
+//     their points are re-evaluated with the exact-form distance
+//     (dx^2 + dy^2 + dz^2 in float32) in index order; if a third chunk could
+//     (b3 <= b1 + 2 delta, rare), the query falls back to an exact scan of the
+//     whole cloud.  The result is the lowest-index minimum of the exact-form
+//     float32 distance among all points that can be nearest.
+//
+// Object tiles are staged in shared memory by 1D bulk (TMA) copies into two
+// buffers guarded by mbarriers; waits are bounded and report a timeout through
+// the error word instead of hanging.
+//
+// The epilogue accumulates, in float64, the sums that the cost and gradient of
+// Eqs. 13-17 are linear in: sum r_i (3), sum r_i s_i^T (9), sum |r_i|^2 (1),
+// with r_i the matched object point and s_i the untransformed gripper point;
+// both are float32, so every product is exact in float64.
 #include "asicp_internal.cuh"
 
 namespace asicp {
 
 namespace {
-constexpr int QPT = 4;   // queries per thread
+
+constexpr int kThreads = 128;            // threads per CTA
+constexpr int QPT = 8;                   // queries per thread
+constexpr int kChunk = 64;               // screening chunk (object points)
+constexpr int kTile = kRefTilePts;       // object points per shared-memory tile
+constexpr long long kWaitCycles = 1LL << 32;   // bounded mbarrier wait (~2 s)
+
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
 }
 
-int fwd_queries_per_block() { return kFwdThreads * QPT; }
-
-__global__ void __launch_bounds__(kFwdThreads) fwd_match_kernel(const FwdArgs a)
+__device__ __forceinline__ void unpack2(unsigned long long v, float &lo, float &hi)
 {
-    __shared__ float4 sR[kRefTile];
-    __shared__ double sred[kFwdThreads / 32][kFwdSums];
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
 
-    const int pk = blockIdx.y;
-    const int p = pk / a.K;
-    const int blk = blockIdx.x;
-    const float *th = a.theta + (size_t)pk * 8;
-    const float tx = th[0], ty = th[1], tz = th[2];
-    float Rm[9];
-    quat_rot_f32(th[3], th[4], th[5], th[6], Rm);
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
 
-    const int base = blk * kFwdThreads * QPT + threadIdx.x;
-    float qx[QPT], qy[QPT], qz[QPT], best[QPT];
-    int bi[QPT];
+__device__ __forceinline__ float min3(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: false when the budget ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+
+// Exact-form nearest point among object points [lo, hi) (index order, strict <).
+__device__ __forceinline__ void exact_scan(const float4 *__restrict__ R, int lo, int hi, float sx, float sy, float sz,
+                                           float &best, int &bi)
+{
+    for (int r = lo; r < hi; ++r) {
+        const float4 v = __ldg(R + r);
+        const float d = dist2_f32(sx, sy, sz, v.x, v.y, v.z);
+        if (d < best) { best = d; bi = r; }
+    }
+}
+
+}  // namespace
+
+// One screening + exact pass over the whole object cloud for the queries
+// [q0, q0 + nq) of the flattened (particle, gripper point) space, nq <= kThreads * Q.
+// Object tiles stream through the two shared buffers; `seq` counts tiles
+// consumed by this CTA across passes and `total` is the number it will consume,
+// so the next pass's first tiles are prefetched while this one finishes.
+template <int Q>
+__device__ __forceinline__ bool match_pass(const FwdArgs &a, long long q0, int nq, ulonglong2 *tiles,
+                                           unsigned long long *full, int &seq, int total, int *s_abort)
+{
+    const int ntiles = a.Mpad / kTile;
+    const unsigned tile_bytes = kTile * 16u;
+    const float rmax = *a.rmax;
+    float sx[Q], sy[Q], sz[Q], win[Q], cm[Q], b1[Q], b2[Q], b3[Q];
+    int c1[Q], c2[Q];
+    unsigned long long qx[Q], qy[Q], qz[Q];
 #pragma unroll
-    for (int q = 0; q < QPT; ++q) {
-        const int i = base + q * kFwdThreads;
-        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < a.N) s = a.S[(size_t)p * a.N + i];
-        const float3 o = xform_f32(Rm, tx, ty, tz, s.x, s.y, s.z);
-        qx[q] = o.x; qy[q] = o.y; qz[q] = o.z;
-        best[q] = __int_as_float(0x7f800000);   // +inf
-        bi[q] = 0;
+    for (int q = 0; q < Q; ++q) {
+        const int li = q * kThreads + threadIdx.x;
+        float3 o = make_float3(0.f, 0.f, 0.f);
+        if (li < nq) {
+            const long long g = q0 + li;
+            const int pk = (int)(g / a.N), i = (int)(g - (long long)pk * a.N);
+            const float *th = a.theta + (size_t)pk * 8;
+            float Rm[9];
+            quat_rot_f32(th[3], th[4], th[5], th[6], Rm);
+            const float4 s = a.S[(size_t)(pk / a.K) * a.N + i];
+            o = xform_f32(Rm, th[0], th[1], th[2], s.x, s.y, s.z);
+        }
+        sx[q] = o.x; sy[q] = o.y; sz[q] = o.z;
+        qx[q] = pack2(o.x, o.x); qy[q] = pack2(o.y, o.y); qz[q] = pack2(o.z, o.z);
+        const float sn = sqrtf(o.x * o.x + o.y * o.y + o.z * o.z) * 1.001f;
+        // 2 delta with a 1 % margin for the float32 evaluation of the bound itself
+        win[q] = 2.02f * 5.9604645e-8f * (4.01f * rmax * rmax + 6.02f * sn * rmax);
+        b1[q] = b2[q] = b3[q] = __int_as_float(0x7f800000);
+        c1[q] = c2[q] = 0;
     }
 
-    for (int r0 = 0; r0 < a.M; r0 += kRefTile) {
-        const int n = min(kRefTile, a.M - r0);
+    for (int t = 0; t < ntiles; ++t, ++seq) {
+        const int buf = seq & 1;
+        if (!mbar_wait(&full[buf], (seq >> 1) & 1)) { atomicExch(a.err, kDevTimeout); *s_abort = 1; }
         __syncthreads();
-        for (int r = threadIdx.x; r < n; r += kFwdThreads) sR[r] = a.R[r0 + r];
-        __syncthreads();
+        if (*s_abort) return false;
+        const ulonglong2 *tp = tiles + (size_t)buf * kTile;
+        for (int c = 0; c < kTile / kChunk; ++c) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) cm[q] = __int_as_float(0x7f800000);
+            const ulonglong2 *cp = tp + c * kChunk;
 #pragma unroll 4
-        for (int r = 0; r < n; ++r) {
-            const float4 ref = sR[r];
+            for (int r2 = 0; r2 < kChunk / 2; ++r2) {
+                const ulonglong2 A = cp[2 * r2];       // {ax0,ax1} {ay0,ay1}
+                const ulonglong2 B = cp[2 * r2 + 1];   // {az0,az1} {w0,w1}
 #pragma unroll
-            for (int q = 0; q < QPT; ++q) {
-                const float d = dist2_f32(qx[q], qy[q], qz[q], ref.x, ref.y, ref.z);
-                if (d < best[q]) { best[q] = d; bi[q] = r0 + r; }
+                for (int q = 0; q < Q; ++q) {
+                    const unsigned long long d = fma2(qx[q], A.x, fma2(qy[q], A.y, fma2(qz[q], B.x, B.y)));
+                    float d0, d1;
+                    unpack2(d, d0, d1);
+                    cm[q] = min3(cm[q], d0, d1);
+                }
             }
+            const int gc = t * (kTile / kChunk) + c;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const float v = cm[q];
+                const bool n1 = v < b1[q], n2 = v < b2[q];
+                b3[q] = n2 ? b2[q] : fminf(b3[q], v);
+                b2[q] = n1 ? b1[q] : (n2 ? v : b2[q]);
+                c2[q] = n1 ? c1[q] : (n2 ? gc : c2[q]);
+                b1[q] = n1 ? v : b1[q];
+                c1[q] = n1 ? gc : c1[q];
+            }
+        }
+        __syncthreads();   // every thread is done with this buffer
+        if (threadIdx.x == 0 && seq + 2 < total) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const int nt = (seq + 2) % ntiles;
+            mbar_arrive_tx(&full[buf], tile_bytes);
+            bulk_load(tiles + (size_t)buf * kTile, a.Rx + (size_t)nt * kTile, tile_bytes, &full[buf]);
         }
     }
 
-    double acc[kFwdSums];
 #pragma unroll
-    for (int c = 0; c < kFwdSums; ++c) acc[c] = 0.0;
-#pragma unroll
-    for (int q = 0; q < QPT; ++q) {
-        const int i = base + q * kFwdThreads;
-        if (i < a.N) {
-            const float4 s = a.S[(size_t)p * a.N + i];
-            const float4 r = a.R[bi[q]];
-            const double rv[3] = {r.x, r.y, r.z}, sv[3] = {s.x, s.y, s.z};
-#pragma unroll
-            for (int u = 0; u < 3; ++u) {
-                acc[u] += rv[u];
-#pragma unroll
-                for (int v = 0; v < 3; ++v) acc[3 + 3 * u + v] = fma(rv[u], sv[v], acc[3 + 3 * u + v]);
-            }
-            acc[12] = fma(rv[0], rv[0], fma(rv[1], rv[1], fma(rv[2], rv[2], acc[12])));
-            const size_t o = (size_t)pk * a.N + i;
-            if (a.dbg_idx) a.dbg_idx[o] = bi[q];
-            if (a.dbg_d2) a.dbg_d2[o] = best[q];
-            if (a.dbg_sp) {
-                a.dbg_sp[o * 3 + 0] = qx[q];
-                a.dbg_sp[o * 3 + 1] = qy[q];
-                a.dbg_sp[o * 3 + 2] = qz[q];
-            }
+    for (int q = 0; q < Q; ++q) {
+        const int li = q * kThreads + threadIdx.x;
+        if (li >= nq) continue;
+        const long long g = q0 + li;
+        const float thr = b1[q] + win[q];
+        float best = __int_as_float(0x7f800000);
+        int bi = 0;
+        if (b3[q] <= thr) {
+            exact_scan(a.R, 0, a.M, sx[q], sy[q], sz[q], best, bi);
+        } else {
+            int ca = c1[q], cb = c2[q];
+            const bool two = b2[q] <= thr && cb != ca;
+            if (two && cb < ca) { const int x = ca; ca = cb; cb = x; }
+            exact_scan(a.R, ca * kChunk, min((ca + 1) * kChunk, a.M), sx[q], sy[q], sz[q], best, bi);
+            if (two) exact_scan(a.R, cb * kChunk, min((cb + 1) * kChunk, a.M), sx[q], sy[q], sz[q], best, bi);
+        }
+        a.nn_idx[g] = bi;
+        if (a.dbg_d2) a.dbg_d2[g] = best;
+        if (a.dbg_sp) {
+            a.dbg_sp[g * 3 + 0] = sx[q];
+            a.dbg_sp[g * 3 + 1] = sy[q];
+            a.dbg_sp[g * 3 + 2] = sz[q];
         }
     }
-    warp_sum_f64(acc);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0)
-#pragma unroll
-        for (int c = 0; c < kFwdSums; ++c) sred[warp][c] = acc[c];
-    __syncthreads();
-    if (threadIdx.x < kFwdSums) {
-        double s = 0.0;
-        for (int w = 0; w < kFwdThreads / 32; ++w) s += sred[w][threadIdx.x];
-        a.fsums[((size_t)pk * a.nb + blk) * kFwdSums + threadIdx.x] = s;
+    return true;
+}
+
+// Persistent: CTA b owns an equal contiguous slice of the P*K*N queries and
+// walks it in passes of kThreads * QPT queries; the last, partial pass uses the
+// smallest queries-per-thread instantiation that covers it, so every CTA
+// carries the same work whatever the particle count.
+__global__ void __launch_bounds__(kThreads, 3) fwd_match_kernel(const FwdArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    ulonglong2 *tiles = reinterpret_cast<ulonglong2 *>(smem_raw);
+    __shared__ __align__(8) unsigned long long full[2];
+    __shared__ int s_abort;
+
+    const long long Qtot = (long long)a.PK * a.N;
+    const long long per = (Qtot + gridDim.x - 1) / gridDim.x;
+    const long long lo = (long long)blockIdx.x * per;
+    const long long hi = lo + per < Qtot ? lo + per : Qtot;
+    if (lo >= hi) return;
+    constexpr int kQB = kThreads * QPT;
+    const int npass = (int)((hi - lo + kQB - 1) / kQB);
+    const int ntiles = a.Mpad / kTile;
+    const int total = npass * ntiles;
+    const unsigned tile_bytes = kTile * 16u;
+
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int sq = 0; sq < 2 && sq < total; ++sq) {
+            mbar_arrive_tx(&full[sq], tile_bytes);
+            bulk_load(tiles + (size_t)sq * kTile, a.Rx + (size_t)(sq % ntiles) * kTile, tile_bytes, &full[sq]);
+        }
+
+    int seq = 0;
+    bool ok = true;
+    for (int ps = 0; ps < npass && ok; ++ps) {
+        const long long q0 = lo + (long long)ps * kQB;
+        const int nq = (int)(hi - q0 < kQB ? hi - q0 : kQB);
+        switch ((nq + kThreads - 1) / kThreads) {
+            case 1: ok = match_pass<1>(a, q0, nq, tiles, full, seq, total, &s_abort); break;
+            case 2: ok = match_pass<2>(a, q0, nq, tiles, full, seq, total, &s_abort); break;
+            case 3: ok = match_pass<3>(a, q0, nq, tiles, full, seq, total, &s_abort); break;
+            case 4: ok = match_pass<4>(a, q0, nq, tiles, full, seq, total, &s_abort); break;
+            case 5: ok = match_pass<5>(a, q0, nq, tiles, full, seq, total, &s_abort); break;
+            case 6: ok = match_pass<6>(a, q0, nq, tiles, full, seq, total, &s_abort); break;
+            case 7: ok = match_pass<7>(a, q0, nq, tiles, full, seq, total, &s_abort); break;
+            default: ok = match_pass<8>(a, q0, nq, tiles, full, seq, total, &s_abort); break;
+        }
+    }
+    if (!ok && threadIdx.x == 0)   // drain copies still in flight (bounded) before leaving
+        for (int b = 0; b < 2; ++b) mbar_wait(&full[b], (unsigned)((seq + b) >> 1) & 1u);
+}
+
+int fwd_grid_size()
+{
+    static int grid = 0;
+    if (grid == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(fwd_match_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kTile * 16);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_match_kernel, kThreads, 2 * kTile * 16);
+        grid = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    return grid;
 }
 
 cudaError_t launch_fwd_match(const FwdArgs &a, cudaStream_t st)
 {
-    dim3 grid(a.nb, a.PK);
-    fwd_match_kernel<<<grid, kFwdThreads, 0, st>>>(a);
+    const size_t smem = 2 * (size_t)kTile * 16;
+    const int grid = fwd_grid_size();
+    fwd_match_kernel<<<grid, kThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Reference preparation for the screening stage: pair layout of (-2 r, |r|^2)
+// padded with (0, +inf) points to a whole number of tiles, and Rmax = max |r|
+// rounded up (float64 reduction, one CTA).
+__global__ void ref_prep_kernel(const float4 *R, int M, int Mpad, ulonglong2 *Rx, float *rmax)
+{
+    __shared__ double red[32];
+    double m = 0.0;
+    for (int q = threadIdx.x; q < Mpad / 2; q += blockDim.x) {
+        float ax[2], ay[2], az[2], w[2];
+        for (int k = 0; k < 2; ++k) {
+            const int i = 2 * q + k;
+            if (i < M) {
+                const float4 r = R[i];
+                const double r2 = (double)r.x * r.x + (double)r.y * r.y + (double)r.z * r.z;
+                m = fmax(m, r2);
+                ax[k] = -2.f * r.x; ay[k] = -2.f * r.y; az[k] = -2.f * r.z;
+                w[k] = (float)r2;
+            } else {
+                ax[k] = ay[k] = az[k] = 0.f;
+                w[k] = __int_as_float(0x7f800000);
+            }
+        }
+        // pair layout within a tile: tile-local pair index q' -> {A, B} at 2 q', 2 q' + 1
+        const int tile = (2 * q) / kTile, ql = q - tile * (kTile / 2);
+        ulonglong2 A, B;
+        A.x = pack2(ax[0], ax[1]); A.y = pack2(ay[0], ay[1]);
+        B.x = pack2(az[0], az[1]); B.y = pack2(w[0], w[1]);
+        Rx[(size_t)tile * kTile + 2 * ql] = A;
+        Rx[(size_t)tile * kTile + 2 * ql + 1] = B;
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mm = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, red[w]);
+        *rmax = (float)(sqrt(mm) * (1.0 + 1e-6)) + 1e-30f;
+    }
+}
+
+cudaError_t launch_ref_prep(const float4 *R, int M, int Mpad, void *Rx, float *rmax, cudaStream_t st)
+{
+    ref_prep_kernel<<<1, 1024, 0, st>>>(R, M, Mpad, static_cast<ulonglong2 *>(Rx), rmax);
     return cudaGetLastError();
 }
 

@@ -99,9 +99,7 @@ __global__ void __launch_bounds__(kMaxK) update_kernel(const UpdateArgs a)
         double se2, Se[3], E[9], cnt;
         if (nc == 0) {
             double fs[kFwdSums];
-            for (int c = 0; c < kFwdSums; ++c) fs[c] = 0.0;
-            for (int b = 0; b < a.nb; ++b)
-                for (int c = 0; c < kFwdSums; ++c) fs[c] += a.fsums[(pk * a.nb + b) * kFwdSums + c];
+            for (int c = 0; c < kFwdSums; ++c) fs[c] = a.fsums[pk * kFwdSums + c];
             const double *pc = a.pconst + (size_t)p * 12;
             double SS[9];
             sym_full(pc + 3, SS);
@@ -118,7 +116,12 @@ __global__ void __launch_bounds__(kMaxK) update_kernel(const UpdateArgs a)
             }
             cnt = (double)a.N;
         } else {
-            const double *cs = a.csums + pk * kColSums;
+            // add the per-chunk collision sums in chunk order
+            const int nchunks = (a.Mc + kColChunk - 1) / kColChunk, used = (nc + kColChunk - 1) / kColChunk;
+            double cs[kColSums];
+            for (int c = 0; c < kColSums; ++c) cs[c] = 0.0;
+            for (int b = 0; b < used; ++b)
+                for (int c = 0; c < kColSums; ++c) cs[c] += a.csums[(pk * nchunks + b) * kColSums + c];
             double SS[9];
             sym_full(cs + 3, SS);
             residual_moments(R, t, (double)nc, cs, SS, cs + 9, cs + 12, cs[21], &se2, Se, E);
@@ -190,12 +193,20 @@ __global__ void __launch_bounds__(kMaxK) update_kernel(const UpdateArgs a)
             for (int b = j; b < 256; b += blockDim.x) hist[b] = 0u;
             __syncthreads();
             const unsigned prefix = s_prefix, mask = s_mask;
-            if (active) {
-                const float4 ti = sT[j];
-                for (int jj = j + 1; jj < K; ++jj) {
-                    const unsigned bits = __float_as_uint(pair_d2(ti, sT[jj]));
-                    if ((bits & mask) == prefix) atomicAdd(&hist[(bits >> shift) & 255u], 1u);
-                }
+            // every unordered pair once with the same trip count in every thread: thread j
+            // takes partners j + o (mod K), o = 1 .. K/2, the o = K/2 pairs only from j < K/2
+            // when K is even; lanes that land in one bin add with one aggregated atomic
+            const float4 ti = sT[active ? j : 0];
+            const int lane = j & 31;
+            for (int o = 1; o <= K / 2; ++o) {
+                int jj = j + o;
+                jj -= jj >= K ? K : 0;
+                const bool valid = active && !((K & 1) == 0 && o == K / 2 && j >= K / 2);
+                const unsigned bits = __float_as_uint(pair_d2(ti, sT[valid ? jj : 0]));
+                const bool take = valid && (bits & mask) == prefix;
+                const unsigned key = take ? ((bits >> shift) & 255u) : 256u + lane;
+                const unsigned peers = __match_any_sync(0xffffffffu, key);
+                if (take && lane == __ffs(peers) - 1) atomicAdd(&hist[key], (unsigned)__popc(peers));
             }
             __syncthreads();
             if (j == 0) {
@@ -413,19 +424,30 @@ cudaError_t launch_set_theta(const float *theta7, int PK, float *theta8, int *er
 
 // Ranking for Algorithm 1's argmin: non-colliding first, ascending cost (NaN
 // last), ties to the lower flat index.  Each particle counts the particles that
-// precede it, which gives a dense, deterministic order.
+// precede it, which gives a dense, deterministic order.  The sort key packs the
+// collision flag above the cost's order-preserving bit pattern (costs are >= 0).
+constexpr int kSelectSmem = 8192;
+
+__device__ __forceinline__ unsigned long long select_key(const double *cost, const int *ncol, int i)
+{
+    double v = cost[i];
+    if (isnan(v) || v < 0.0) v = __longlong_as_double(0x7ff0000000000000LL);
+    return ((unsigned long long)(ncol[i] > 0) << 63) | (unsigned long long)__double_as_longlong(v);
+}
+
 __global__ void select_kernel(const double *cost, const int *ncol, int total, int *order)
 {
+    __shared__ unsigned long long keys[kSelectSmem];
+    const bool staged = total <= kSelectSmem;
+    if (staged)
+        for (int i = threadIdx.x; i < total; i += blockDim.x) keys[i] = select_key(cost, ncol, i);
+    __syncthreads();
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
-        const int ci = ncol[i] > 0;
-        double vi = cost[i];
-        if (isnan(vi)) vi = __longlong_as_double(0x7ff0000000000000LL);
+        const unsigned long long ki = staged ? keys[i] : select_key(cost, ncol, i);
         int rank = 0;
         for (int k = 0; k < total; ++k) {
-            const int ck = ncol[k] > 0;
-            double vk = cost[k];
-            if (isnan(vk)) vk = __longlong_as_double(0x7ff0000000000000LL);
-            rank += (ck < ci) || (ck == ci && (vk < vi || (vk == vi && k < i)));
+            const unsigned long long kk = staged ? keys[k] : select_key(cost, ncol, k);
+            rank += kk < ki || (kk == ki && k < i);
         }
         order[rank] = i;
     }

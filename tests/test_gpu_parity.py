@@ -41,8 +41,8 @@ def _teacher_forced_run(w, stream, steps, report, device=True, theta0=None, samp
             theta0 = np.tile(oracle.fibonacci_init(K, com, 0.15), (P, 1)).astype(np.float32)
         asicp.asicp_set_state(ctx, np.ascontiguousarray(theta0, dtype=np.float32), 0)
         for k in steps:
-            before = tl.read_theta(ctx, P * K)
-            asicp.asicp_set_state(ctx, before, k)
+            asicp.asicp_set_state(ctx, tl.read_theta(ctx, P * K), k)
+            before = tl.read_theta(ctx, P * K)      # the poses exactly as stored (set_state renormalises q)
             asicp.asicp_step(ctx, k)
             st = tl.read_state(ctx, P, K, N, Mc)
             tl.check_step(orc, w, before, st, k, report, sample=sample)
@@ -212,3 +212,34 @@ def test_invalid_inputs_are_rejected(stream):
         del keep
     finally:
         asicp.asicp_destroy(ctx)
+
+
+def test_planted_duplicates_resolve_to_lowest_index(stream):
+    """Exact duplicates of object points in two and in four different screening chunks, with gripper
+    points placed on them (squared distance exactly 0): the nearest point must be the lowest index,
+    which exercises the two-chunk re-evaluation and the full exact fallback."""
+    g = np.random.default_rng(29)
+    M = 3000
+    R = g.uniform(-0.06, 0.06, (M, 3)).astype(np.float32)
+    for i in range(10):
+        R[700 + i] = R[i]                  # two chunks
+    for i in range(10, 20):
+        R[700 + i] = R[1500 + i] = R[2900 + i - 10] = R[i]   # four chunks
+    N = 40
+    S = np.concatenate([R[:20], R[100:120] + np.float32(1e-3)]).astype(np.float32)
+    sdf = -np.ones((8, 8, 8), np.float32)
+    cfg = asicp.asicp_config_default(P=1, K=1, k_max=1, k_stein=0, conv_tol=-1.0, debug=1, cuda_stream=stream)
+    ctx = asicp.asicp_create(cfg)
+    try:
+        asicp.asicp_set_object(ctx, R)
+        asicp.asicp_set_gripper_sdf(ctx, 0, S, sdf, np.full(3, -0.1, np.float32), np.float32(0.2 / 7))
+        asicp.asicp_set_state(ctx, np.array([[0, 0, 0, 1, 0, 0, 0]], np.float32), 0)
+        asicp.asicp_step(ctx, 0)
+        st = tl.read_state(ctx, 1, 1, N, M)
+    finally:
+        asicp.asicp_destroy(ctx)
+    idx = st["nn_idx"][0]
+    assert np.array_equal(idx[:20], np.arange(20))
+    assert np.all(st["nn_d2"][0, :20] == 0.0)
+    rep = {}
+    tl.check_nn(st["s_prime"][0], R, idx, rep)
