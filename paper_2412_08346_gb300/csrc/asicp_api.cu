@@ -80,6 +80,14 @@ struct asicp_ctx {
     double acc_ms[4] = {0, 0, 0, 0};
     long long acc_n[4] = {0, 0, 0, 0};
 
+    // CUDA graph of asicp_run's iteration loop (captured once per buffer layout)
+    cudaStream_t cap_st = nullptr;
+    cudaGraphExec_t loop_exec = nullptr;
+    std::vector<const void *> loop_key;
+    std::vector<Ev> graph_events;     // event pairs inside the graph (profile = 1)
+    bool graph_pending = false;       // a replay's events have not been accumulated yet
+    bool capturing = false;
+
     int PK() const { return cfg.P * cfg.K; }
     int col_chunks() const { return (Mc + kColChunk - 1) / kColChunk; }
     bool ready() const
@@ -98,7 +106,10 @@ struct asicp_ctx {
     ~asicp_ctx()
     {
         for (auto &e : events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+        for (auto &e : graph_events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
         for (auto e : pool) cudaEventDestroy(e);
+        if (loop_exec) cudaGraphExecDestroy(loop_exec);
+        if (cap_st) cudaStreamDestroy(cap_st);
     }
 };
 
@@ -183,28 +194,53 @@ __global__ void reset_convergence_kernel(double *prev, int *frozen, float *phi, 
     for (int a = 0; a < 8; ++a) phi[(size_t)i * 8 + a] = 0.f;
 }
 
-void reset_convergence(asicp_ctx *c)
-{
-    const int PK = c->PK();
-    reset_convergence_kernel<<<(PK + 255) / 256, 256, 0, c->st>>>(c->prev.as<double>(), c->frozen.as<int>(),
-                                                                  c->phi.as<float>(), PK);
-    ck(cudaGetLastError(), "reset convergence state");
-}
+
+
+// Stream the iteration kernels go to: the capture stream while a graph is being
+// recorded, else the caller's stream.
+cudaStream_t work_stream(const asicp_ctx *c) { return c->capturing ? c->cap_st : c->st; }
 
 template <class L>
 void timed(asicp_ctx *c, int kind, L &&launch, const char *what)
 {
     cudaEvent_t a = nullptr, b = nullptr;
+    cudaStream_t st = work_stream(c);
+    // inside a capture, an external record makes the event a graph node that every
+    // replay records (a plain record would only express a capture dependency)
+    const unsigned flags = c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (c->cfg.profile) {
         a = c->take_event();
         b = c->take_event();
-        ck(cudaEventRecord(a, c->st), "cudaEventRecord");
+        ck(cudaEventRecordWithFlags(a, st, flags), "cudaEventRecord");
     }
-    ck(launch(), what);
+    ck(launch(st), what);
     if (c->cfg.profile) {
-        ck(cudaEventRecord(b, c->st), "cudaEventRecord");
-        c->events.push_back({kind, a, b});
+        ck(cudaEventRecordWithFlags(b, st, flags), "cudaEventRecord");
+        (c->capturing ? c->graph_events : c->events).push_back({kind, a, b});
     }
+}
+
+// Add the device times of the last graph replay (its events are re-recorded by
+// every replay, so they are read before the next one).
+void accumulate_graph_events(asicp_ctx *c)
+{
+    if (!c->graph_pending) return;
+    for (auto &e : c->graph_events) {
+        float t = 0.f;
+        ck(cudaEventSynchronize(e.b), "cudaEventSynchronize");
+        ck(cudaEventElapsedTime(&t, e.a, e.b), "cudaEventElapsedTime");
+        c->acc_ms[e.kind] += t;
+        c->acc_n[e.kind] += 1;
+    }
+    c->graph_pending = false;
+}
+
+void reset_convergence(asicp_ctx *c)
+{
+    const int PK = c->PK();
+    reset_convergence_kernel<<<(PK + 255) / 256, 256, 0, work_stream(c)>>>(c->prev.as<double>(), c->frozen.as<int>(),
+                                                                          c->phi.as<float>(), PK);
+    ck(cudaGetLastError(), "reset convergence state");
 }
 
 // One pass of cost/gradient evaluation (+ update for mode 1/2).
@@ -224,7 +260,7 @@ void iterate(asicp_ctx *c, int mode, float gamma)
         fa.dbg_d2 = c->dbg_d2.as<float>();
         fa.dbg_sp = c->dbg_sp.as<float>();
     }
-    timed(c, kTimeMatch, [&] { return launch_fwd_match(fa, c->st); }, "forward matching kernel");
+    timed(c, kTimeMatch, [&](cudaStream_t st) { return launch_fwd_match(fa, st); }, "forward matching kernel");
 
     CollideArgs ca{};
     ca.C = c->C.p ? c->C.as<float4>() : c->R.as<float4>();
@@ -239,8 +275,8 @@ void iterate(asicp_ctx *c, int mode, float gamma)
     ca.fsums = c->fsums.as<double>();
     ca.csums = c->csums.as<double>();
     if (c->cfg.debug) ca.dbg_colnn = c->dbg_colnn.as<int>();
-    timed(c, kTimeCollide, [&] { return launch_collide(ca, c->st); }, "collision kernel");
-    timed(c, kTimeCollideNN, [&] { return launch_collide_nn(ca, c->st); }, "collision matching kernel");
+    timed(c, kTimeCollide, [&](cudaStream_t st) { return launch_collide(ca, st); }, "collision kernel");
+    timed(c, kTimeCollideNN, [&](cudaStream_t st) { return launch_collide_nn(ca, st); }, "collision matching kernel");
 
     UpdateArgs ua{};
     ua.P = c->cfg.P; ua.K = c->cfg.K; ua.N = c->N; ua.Mc = c->Mc;
@@ -264,7 +300,7 @@ void iterate(asicp_ctx *c, int mode, float gamma)
     ua.frozen = c->frozen.as<int>();
     ua.phi = c->phi.as<float>();
     ua.h = c->h.as<float>();
-    timed(c, kTimeUpdate, [&] { return launch_update(ua, c->st); }, "update kernel");
+    timed(c, kTimeUpdate, [&](cudaStream_t st) { return launch_update(ua, st); }, "update kernel");
 }
 
 void step_impl(asicp_ctx *c, int k)
@@ -273,6 +309,64 @@ void step_impl(asicp_ctx *c, int k)
     iterate(c, mode, (float)gamma_of(c->cfg, k));
     c->k_next = k + 1;
     c->stepped = true;
+}
+
+// Everything asicp_run does after the initial poses: convergence reset, k_max
+// iterations, final evaluation and ranking.
+void run_loop(asicp_ctx *c)
+{
+    reset_convergence(c);
+    for (int k = 0; k < c->cfg.k_max; ++k) step_impl(c, k);
+    iterate(c, 0, 0.f);   // final evaluation at the last poses
+    ck(launch_select(c->cost.as<double>(), c->ncol.as<int>(), c->PK(), c->order.as<int>(), work_stream(c)), "select");
+}
+
+// Buffers and sizes the captured graph depends on.
+std::vector<const void *> loop_key(const asicp_ctx *c)
+{
+    return {c->S.p, c->R.p, c->Rx.p, c->rmax.p, c->C.p, c->com.p, c->pconst.p, c->dmeta.p, c->theta.p, c->fsums.p,
+            c->csums.p, c->ncol.p, c->colidx.p, c->cost.p, c->grad.p, c->prev.p, c->frozen.p, c->phi.p, c->h.p,
+            c->order.p, c->errw.p, c->nnidx.p, c->dbg_d2.p, c->dbg_sp.p, c->dbg_colnn.p,
+            reinterpret_cast<const void *>((size_t)c->M), reinterpret_cast<const void *>((size_t)c->Mpad),
+            reinterpret_cast<const void *>((size_t)c->Mc), reinterpret_cast<const void *>((size_t)c->N)};
+}
+
+// Replay the captured loop on the caller's stream, capturing it first when the
+// buffers changed.  Kernel arguments (buffer pointers, per-iteration gamma) are
+// fixed at capture; the buffers' contents are read at replay.
+void run_loop_graph(asicp_ctx *c)
+{
+    std::vector<const void *> key = loop_key(c);
+    if (!c->loop_exec || key != c->loop_key) {
+        if (c->loop_exec) {
+            cudaGraphExecDestroy(c->loop_exec);
+            c->loop_exec = nullptr;
+        }
+        for (auto &e : c->graph_events) { c->pool.push_back(e.a); c->pool.push_back(e.b); }
+        c->graph_events.clear();
+        c->graph_pending = false;
+        if (!c->cap_st) ck(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking), "capture stream");
+        ck(cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal), "begin capture");
+        c->capturing = true;
+        cudaGraph_t g = nullptr;
+        try {
+            run_loop(c);
+        } catch (...) {
+            c->capturing = false;
+            cudaStreamEndCapture(c->cap_st, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        c->capturing = false;
+        ck(cudaStreamEndCapture(c->cap_st, &g), "end capture");
+        cudaError_t e = cudaGraphInstantiate(&c->loop_exec, g, 0);
+        cudaGraphDestroy(g);
+        ck(e, "instantiate graph");
+        c->loop_key = key;
+    }
+    accumulate_graph_events(c);
+    ck(cudaGraphLaunch(c->loop_exec, c->st), "graph launch");
+    c->graph_pending = c->cfg.profile != 0;
 }
 
 void copy_out(void *dst, const void *src, size_t bytes, cudaStream_t st, const char *what)
@@ -354,6 +448,10 @@ asicp_status asicp_create(const asicp_config *cfg, asicp_ctx **out)
     c->meta.assign(cfg->P, SdfMeta{});
     c->grids.resize(cfg->P);
     asicp_status s = guarded(c, [&] {
+        // one-time kernel attributes, set outside any graph capture
+        fwd_grid_size();
+        ck(init_collision_attributes(), "collision kernel attributes");
+        ck(init_update_attributes(), "update kernel attributes");
         c->com.ensure(sizeof(double) * 3, "com");
         c->pconst.ensure(sizeof(double) * 12 * cfg->P, "pconst");
         c->dmeta.ensure(sizeof(SdfMeta) * cfg->P, "sdf meta");
@@ -421,7 +519,7 @@ asicp_status asicp_set_gripper_sdf(asicp_ctx *ctx, int preshape, const float *S_
     return guarded(ctx, [&] {
         if (preshape < 0 || preshape >= ctx->cfg.P) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: preshape out of range");
         if (!S_xyz || !sdf || !origin) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: NULL array");
-        if (N < 1 || N > 8192) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: N must be in [1, 8192]");
+        if (N < 1 || N > kMaxN) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: N must be in [1, 8192]");
         if (nx < 2 || ny < 2 || nz < 2) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: every grid dimension must be >= 2");
         if (!(voxel > 0.f) || !std::isfinite(voxel)) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: voxel must be > 0");
         float org[3];
@@ -523,12 +621,11 @@ asicp_status asicp_run(asicp_ctx *ctx, const float *theta0)
             ck(launch_fibonacci(ctx->cfg.P, ctx->cfg.K, ctx->com.as<double>(), ctx->cfg.init_radius,
                                 ctx->theta.as<float>(), ctx->st), "fibonacci init");
         }
-        reset_convergence(ctx);
         if (theta0) sync_and_check_err(ctx, "run");
         ctx->theta_set = true;
-        for (int k = 0; k < ctx->cfg.k_max; ++k) step_impl(ctx, k);
-        iterate(ctx, 0, 0.f);   // final evaluation at the last poses
-        ck(launch_select(ctx->cost.as<double>(), ctx->ncol.as<int>(), PK, ctx->order.as<int>(), ctx->st), "select");
+        run_loop_graph(ctx);
+        ctx->k_next = ctx->cfg.k_max;
+        ctx->stepped = true;
         ctx->run_done = true;
     });
 }
@@ -605,6 +702,7 @@ asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[4], long long launches
     return guarded(ctx, [&] {
         if (!ctx->cfg.profile) fail(ASICP_ERR_STATE, "kernel_times: config.profile is 0");
         ck(cudaStreamSynchronize(ctx->st), "kernel_times");
+        accumulate_graph_events(ctx);
         for (auto &e : ctx->events) {
             float t = 0.f;
             ck(cudaEventElapsedTime(&t, e.a, e.b), "cudaEventElapsedTime");

@@ -9,6 +9,7 @@ constexpr int kRefTilePts = 2048;      // object points per shared-memory tile o
 constexpr int kFwdSums = 13;           // per-particle matching sums (see match kernel)
 constexpr int kColSums = 22;           // per-particle collision sums (see collision kernel)
 constexpr int kMaxK = 1024;            // particles per preshape (one update CTA per preshape)
+constexpr int kMaxN = 8192;            // gripper points per preshape (reverse matching in shared memory)
 
 // error word written by device code (host reads it back after synchronising)
 enum : int { kDevOk = 0, kDevNonFinite = 1, kDevTimeout = 2 };
@@ -91,6 +92,9 @@ struct FwdArgs {
     float *dbg_sp;           // [PK][N][3] or null
 };
 cudaError_t launch_fwd_match(const FwdArgs &a, cudaStream_t st);
+int fwd_grid_size();                   // persistent grid; first call sets kernel attributes
+cudaError_t init_collision_attributes();
+cudaError_t init_update_attributes();
 cudaError_t launch_ref_prep(const float4 *R, int M, int Mpad, void *Rx, float *rmax, cudaStream_t st);
 
 constexpr int kColChunk = 256;         // colliding points per reverse-matching CTA

@@ -194,13 +194,15 @@ cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+cudaError_t init_collision_attributes()
+{
+    return cudaFuncSetAttribute(collide_nn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(float4) * kMaxN));
+}
+
 cudaError_t launch_collide_nn(const CollideArgs &a, cudaStream_t st)
 {
     const size_t smem = sizeof(float4) * (size_t)a.N;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(collide_nn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
     dim3 grid(a.PK, (a.Mc + kColChunk - 1) / kColChunk);
     collide_nn_kernel<<<grid, kColThreads, smem, st>>>(a);
     return cudaGetLastError();

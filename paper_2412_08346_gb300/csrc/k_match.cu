@@ -175,7 +175,7 @@ __device__ __forceinline__ bool match_pass(const FwdArgs &a, long long q0, int n
 #pragma unroll
             for (int q = 0; q < Q; ++q) cm[q] = __int_as_float(0x7f800000);
             const ulonglong2 *cp = tp + c * kChunk;
-#pragma unroll 4
+#pragma unroll 8
             for (int r2 = 0; r2 < kChunk / 2; ++r2) {
                 const ulonglong2 A = cp[2 * r2];       // {ax0,ax1} {ay0,ay1}
                 const ulonglong2 B = cp[2 * r2 + 1];   // {az0,az1} {w0,w1}

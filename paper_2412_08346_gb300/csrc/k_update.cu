@@ -262,14 +262,16 @@ __global__ void __launch_bounds__(kMaxK) update_kernel(const UpdateArgs a)
     }
 }
 
+cudaError_t init_update_attributes()
+{
+    return cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(float4) * 4 * kMaxK));
+}
+
 cudaError_t launch_update(const UpdateArgs &a, cudaStream_t st)
 {
     const int threads = ((a.K + 31) / 32) * 32;
     const size_t smem = sizeof(float4) * 4 * (size_t)a.K;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
     update_kernel<<<a.P, threads, smem, st>>>(a);
     return cudaGetLastError();
 }

@@ -243,3 +243,44 @@ def test_planted_duplicates_resolve_to_lowest_index(stream):
     assert np.all(st["nn_d2"][0, :20] == 0.0)
     rep = {}
     tl.check_nn(st["s_prime"][0], R, idx, rep)
+
+
+def test_graph_replay_equals_direct_steps(stream):
+    """asicp_run replays a captured CUDA graph of the loop; its poses equal those of the same
+    iterations launched one by one with asicp_step, and a second replay repeats them exactly."""
+    w = synth.custom_case(P=2, K=16, N=300, M=2500, grid=24, k_max=6, seed=37, k_stein=3)
+    import oracle
+    th0 = np.tile(oracle.fibonacci_init(w.K, w.objects[0].points.astype(np.float64).mean(0), 0.08),
+                  (2, 1)).astype(np.float32)
+    ctx = _ctx(w, stream, debug=False)
+    try:
+        keep = tl.upload(ctx, w)
+        asicp.asicp_run(ctx, th0)
+        a = tl.read_theta(ctx, 32)
+        asicp.asicp_run(ctx, th0)
+        b = tl.read_theta(ctx, 32)
+        asicp.asicp_set_state(ctx, th0, 0)
+        for k in range(w.k_max):
+            asicp.asicp_step(ctx, k)
+        c = tl.read_theta(ctx, 32)
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
+    assert np.array_equal(a, b)
+    assert np.array_equal(a, c)
+
+
+def test_kernel_times_from_graph_replays(stream):
+    """With profiling on, asicp_run's graph replays report one timed launch per kernel and pass."""
+    w = synth.custom_case(P=1, K=8, N=128, M=600, grid=16, k_max=3, seed=41)
+    ctx = _ctx(w, stream, debug=False, profile=True)
+    try:
+        keep = tl.upload(ctx, w)
+        for _ in range(2):
+            asicp.asicp_run(ctx)
+        ms, n = asicp.asicp_kernel_times(ctx, reset=True)
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
+    assert n == [2 * (w.k_max + 1)] * 4
+    assert all(t > 0 for t in ms)
