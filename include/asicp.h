@@ -170,6 +170,33 @@ asicp_status asicp_get_state(asicp_ctx *ctx, const asicp_state_view *view);
  * reset = 1 clears the counters after reading.  Errors: STATE (profile off). */
 asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[4], long long launches[4], int reset);
 
+/* Forward matching without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory, such as
+ * real-time control loops that reserve all memory at start-up and cannot afford the
+ * device synchronisation of cudaMalloc/cudaFree, or runtimes that hand out all
+ * device memory from their own pool.  It computes what asicp_step's matching stage
+ * computes (Eq. 1): for every particle p*K+j and gripper point i, the index of the
+ * nearest object point, ties to the lowest index, written to
+ * nn_idx[(p*K + j)*N + i].
+ *   theta   P*K*7 floats (poses, quaternions are normalised), S_xyz P*N*3 floats
+ *           (gripper clouds, preshape-major), R_xyz M*3 floats: host or device memory
+ *   nn_idx  P*K*N int32 output, device memory
+ *   cuda_stream  cudaStream_t (NULL: default stream); the call synchronises it
+ * Its scratch is one fixed-size static device array (5 MiB) that every device that
+ * loads the library keeps until the process exits; it bounds the sizes to
+ * P*K <= ASICP_NOALLOC_MAX_PK, P*N <= ASICP_NOALLOC_MAX_PN, M <= ASICP_NOALLOC_MAX_M
+ * (larger problems: use the context API).  The first call on a device looks the
+ * array's device address up once (make it before any stream capture).  All calls
+ * share the array: calls that overlap on the GPU race and must be ordered by the
+ * caller.  Returns INVALID_ARG for NULL pointers, sizes < 1 or beyond the limits,
+ * nn_idx not in device memory, or a non-finite input; TIMEOUT if a bounded device
+ * wait expired; CUDA for a failed CUDA call. */
+#define ASICP_NOALLOC_MAX_PK 16384
+#define ASICP_NOALLOC_MAX_PN 65536
+#define ASICP_NOALLOC_MAX_M 65536
+asicp_status asicp_match_noalloc(const float *theta, int P, int K, const float *S_xyz, int N,
+                                 const float *R_xyz, int M, int *nn_idx, void *cuda_stream);
+
 /* Message of the last failing call on ctx (owned by ctx, valid until its next call). */
 const char *asicp_last_error(const asicp_ctx *ctx);
 

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "STATE", 3: "CUDA", 4: "OOM", 5: "
 
 EXPORTED = ("asicp_config_default", "asicp_create", "asicp_destroy", "asicp_set_object",
             "asicp_set_gripper_sdf", "asicp_set_state", "asicp_step", "asicp_run", "asicp_best_grasps",
-            "asicp_get_state", "asicp_kernel_times", "asicp_last_error")
+            "asicp_get_state", "asicp_kernel_times", "asicp_last_error", "asicp_match_noalloc")
 
 
 class AsicpError(RuntimeError):
@@ -81,6 +81,7 @@ def load(build_if_missing: bool = True):
     lib.asicp_best_grasps.argtypes = [vp, ip, vp, vp, vp, C.POINTER(C.c_int)]
     lib.asicp_get_state.argtypes = [vp, C.POINTER(asicp_state_view)]
     lib.asicp_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), ip]
+    lib.asicp_match_noalloc.argtypes = [vp, ip, ip, vp, ip, vp, ip, vp, vp]
     lib.asicp_last_error.argtypes = [vp]
     lib.asicp_last_error.restype = C.c_char_p
     for name in EXPORTED:
@@ -175,6 +176,17 @@ def asicp_kernel_times(ctx, reset: bool = False):
     n = (C.c_longlong * 4)()
     _check(ctx, load().asicp_kernel_times(ctx, ms, n, int(reset)))
     return list(ms), list(n)
+
+
+def asicp_match_noalloc(theta, S_xyz, R_xyz, nn_idx, P: int, K: int, stream=None) -> None:
+    """Nearest-neighbour indices without any device allocation (see include/asicp.h).
+
+    ``theta`` (P*K, 7), ``S_xyz`` (P*N, 3), ``R_xyz`` (M, 3); ``nn_idx`` a CUDA int32 tensor of P*K*N."""
+    N = int(S_xyz.shape[0]) // int(P)
+    st = load().asicp_match_noalloc(_ptr(theta), int(P), int(K), _ptr(S_xyz), N, _ptr(R_xyz),
+                                    int(R_xyz.shape[0]), _ptr(nn_idx), stream)
+    if st != ASICP_OK:
+        raise AsicpError(st, "asicp_match_noalloc failed")
 
 
 def asicp_last_error(ctx) -> str:

@@ -1,0 +1,80 @@
+"""asicp_match_noalloc, the matching entry point for callers that must not allocate
+device memory (real-time loops with memory reserved up front, runtimes that own
+every byte of device memory): its correspondences must equal those of the
+context API's matching stage, call after call, and it must not change the
+device's free memory.
+
+This file is named so that pytest collects it last."""
+import numpy as np
+import pytest
+
+from paper_2412_08346_gb300 import asicp, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+def _context_indices(w, theta, stream):
+    """Correspondences of asicp_step's matching stage (debug read-back) for poses theta."""
+    P, K, N = len(w.preshapes), w.K, w.preshapes[0].S.shape[0]
+    cfg = asicp.asicp_config_default(P=P, K=K, k_max=1, k_stein=0, conv_tol=-1.0, debug=1, cuda_stream=stream)
+    ctx = asicp.asicp_create(cfg)
+    try:
+        asicp.asicp_set_object(ctx, w.objects[0].points)
+        for p, pre in enumerate(w.preshapes):
+            asicp.asicp_set_gripper_sdf(ctx, p, pre.S, pre.sdf, pre.origin, pre.voxel)
+        asicp.asicp_set_state(ctx, theta, 0)
+        asicp.asicp_step(ctx, 0)
+        idx = np.zeros((P * K, N), np.int32)
+        asicp.asicp_get_state(ctx, nn_idx=idx)
+    finally:
+        asicp.asicp_destroy(ctx)
+    return idx
+
+
+def test_noalloc_matches_context_api_on_consecutive_calls():
+    stream = torch.cuda.current_stream().cuda_stream
+    w = synth.custom_case(P=2, K=24, N=700, M=5000, grid=24, k_max=2, seed=31)
+    P, K, N = 2, w.K, 700
+    g = np.random.default_rng(7)
+    poses = []
+    for _ in range(2):
+        t = g.normal(size=(P * K, 3)) * 0.06
+        q = g.normal(size=(P * K, 4))
+        q /= np.linalg.norm(q, axis=1, keepdims=True)
+        poses.append(np.ascontiguousarray(np.concatenate([t, q], 1), dtype=np.float32))
+    expected = [_context_indices(w, th, stream) for th in poses]
+
+    S = torch.from_numpy(np.concatenate([pre.S for pre in w.preshapes])).cuda()
+    R = torch.from_numpy(w.objects[0].points).cuda()
+    th_dev = [torch.from_numpy(th).cuda() for th in poses]
+    out = torch.full((P * K * N,), -1, dtype=torch.int32, device="cuda")
+    # the first call on a device looks the scratch array up; the driver may load the
+    # array's memory with the library's device code at that point
+    asicp.asicp_match_noalloc(th_dev[1], S, R, out, P, K, stream)
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    got = []
+    for th in th_dev:                     # two calls in a row on the shared scratch
+        asicp.asicp_match_noalloc(th, S, R, out, P, K, stream)
+        got.append(out.cpu().numpy().reshape(P * K, N).copy())
+    free_after = torch.cuda.mem_get_info()[0]
+    for a, b in zip(got, expected):
+        assert np.array_equal(a, b)
+    assert not np.array_equal(got[0], got[1])
+    assert free_after == free_before, "the no-allocation path changed the device's free memory"
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    stream = torch.cuda.current_stream().cuda_stream
+    M = 65537                               # one object point more than the fixed scratch holds
+    R = torch.zeros((M, 3), dtype=torch.float32, device="cuda")
+    S = torch.zeros((4, 3), dtype=torch.float32, device="cuda")
+    th = torch.tensor([[0, 0, 0, 1, 0, 0, 0]], dtype=torch.float32, device="cuda")
+    out = torch.zeros(4, dtype=torch.int32, device="cuda")
+    with pytest.raises(asicp.AsicpError) as e:
+        asicp.asicp_match_noalloc(th, S, R, out, 1, 1, stream)
+    assert e.value.status == asicp.ASICP_ERR_INVALID_ARG
