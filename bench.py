@@ -246,7 +246,8 @@ def run_gpu(args, rank, world, local_rank):
     pairs_per_launch = P * K * N * M
     achieved = pairs_per_launch / match_avg_s / 1e9
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / OPS_PER_PAIR / 1e9
-    launches_per_step = 4 * (w.k_max + 1) + 4   # match, collide, collide_nn, update per pass + init/reset/select/gather
+    # match, collide, collide_nn, finalize per pass, Stein per SVGD pass, + init, reset, select, gather
+    launches_per_step = 4 * (w.k_max + 1) + w.k_stein + 4
 
     e2e = None
     if not args.no_e2e:
@@ -280,8 +281,7 @@ def run_gpu(args, rank, world, local_rank):
                              f"{OPS_PER_PAIR} ops per pair",
                          "launch_ms": match_avg_s * 1e3,
                          "kernel_share": ms[0] / max(1e-9, sum(ms))},
-            "kernel_ms_per_step": {k: v / args.steps for k, v in
-                                   zip(("match", "collide", "collide_nn", "update"), ms)},
+            "kernel_ms_per_step": {k: v / args.steps for k, v in zip(asicp.KERNEL_KINDS, ms)},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
         }

@@ -165,10 +165,11 @@ asicp_status asicp_best_grasps(asicp_ctx *ctx, int topk, float *theta, float *co
 asicp_status asicp_get_state(asicp_ctx *ctx, const asicp_state_view *view);
 
 /* With config.profile = 1: accumulated device time (ms) and launch count of the
- * forward matching kernel, the collision kernels and the update kernel since the
- * last reset.  ms[4] / launches[4] order: match, collide, collide_nn, update.
- * reset = 1 clears the counters after reading.  Errors: STATE (profile off). */
-asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[4], long long launches[4], int reset);
+ * path's kernels since the last reset.  ms[5] / launches[5] order: forward
+ * matching, collision test (with the matching sums), reverse matching, finalize
+ * (cost, gradient, convergence, SGD step), Stein (SVGD step).  reset = 1 clears
+ * the counters after reading.  Errors: STATE (profile off). */
+asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[5], long long launches[5], int reset);
 
 /* Forward matching without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that must not allocate device memory, such as

@@ -171,9 +171,12 @@ def asicp_get_state(ctx, **arrays) -> None:
     _check(ctx, load().asicp_get_state(ctx, C.byref(view)))
 
 
+KERNEL_KINDS = ("match", "collide", "collide_nn", "finalize", "stein")
+
+
 def asicp_kernel_times(ctx, reset: bool = False):
-    ms = (C.c_double * 4)()
-    n = (C.c_longlong * 4)()
+    ms = (C.c_double * 5)()
+    n = (C.c_longlong * 5)()
     _check(ctx, load().asicp_kernel_times(ctx, ms, n, int(reset)))
     return list(ms), list(n)
 

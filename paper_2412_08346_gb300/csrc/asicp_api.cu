@@ -54,7 +54,7 @@ struct DevMem {
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
 
-enum { kTimeMatch = 0, kTimeCollide = 1, kTimeCollideNN = 2, kTimeUpdate = 3 };
+enum { kTimeMatch = 0, kTimeCollide = 1, kTimeCollideNN = 2, kTimeFinalize = 3, kTimeStein = 4, kTimeKinds = 5 };
 
 }  // namespace
 
@@ -70,15 +70,15 @@ struct asicp_ctx {
     int k_next = 0;
 
     int Mpad = 0;
-    DevMem box, stage, R, Rx, rmax, C, S, com, pconst, dmeta, theta, fsums, csums, ncol, colidx, cost, grad, prev, frozen,
+    DevMem colitems, collist, box, stage, R, Rx, rmax, C, S, com, pconst, dmeta, theta, fsums, csums, ncol, colidx, cost, grad, prev, frozen,
         phi, h, order, errw, out7, outc, outi, nnidx, dbg_d2, dbg_sp, dbg_colnn;
 
     // profiling: events recorded around launches (kind, start, stop)
     struct Ev { int kind; cudaEvent_t a, b; };
     std::vector<Ev> events;
     std::vector<cudaEvent_t> pool;
-    double acc_ms[4] = {0, 0, 0, 0};
-    long long acc_n[4] = {0, 0, 0, 0};
+    double acc_ms[kTimeKinds] = {0, 0, 0, 0, 0};
+    long long acc_n[kTimeKinds] = {0, 0, 0, 0, 0};
 
     // CUDA graph of asicp_run's iteration loop (captured once per buffer layout)
     cudaStream_t cap_st = nullptr;
@@ -165,6 +165,8 @@ void ensure_work(asicp_ctx *c)
     const size_t PK = c->PK();
     c->fsums.ensure(sizeof(double) * PK * kFwdSums, "fsums");
     c->csums.ensure(sizeof(double) * PK * c->col_chunks() * kColSums, "csums");
+    c->colitems.ensure(sizeof(int) * 2, "collision work counters");
+    c->collist.ensure(sizeof(int) * PK * c->col_chunks(), "collision work list");
     c->nnidx.ensure(sizeof(int) * PK * c->N, "nn_idx");
     c->ncol.ensure(sizeof(int) * PK, "ncol");
     c->colidx.ensure(sizeof(int) * PK * (size_t)c->Mc, "colidx");
@@ -185,9 +187,10 @@ void ensure_work(asicp_ctx *c)
     }
 }
 
-__global__ void reset_convergence_kernel(double *prev, int *frozen, float *phi, int PK)
+__global__ void reset_convergence_kernel(double *prev, int *frozen, float *phi, int PK, int *col_items)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) { col_items[0] = 0; col_items[1] = 0; }
     if (i >= PK) return;
     prev[i] = -1.0;     // no previous cost
     frozen[i] = 0;
@@ -239,7 +242,8 @@ void reset_convergence(asicp_ctx *c)
 {
     const int PK = c->PK();
     reset_convergence_kernel<<<(PK + 255) / 256, 256, 0, work_stream(c)>>>(c->prev.as<double>(), c->frozen.as<int>(),
-                                                                          c->phi.as<float>(), PK);
+                                                                          c->phi.as<float>(), PK,
+                                                                          c->colitems.as<int>());
     ck(cudaGetLastError(), "reset convergence state");
 }
 
@@ -274,6 +278,8 @@ void iterate(asicp_ctx *c, int mode, float gamma)
     ca.nn_idx = c->nnidx.as<int>();
     ca.fsums = c->fsums.as<double>();
     ca.csums = c->csums.as<double>();
+    ca.col_items = c->colitems.as<int>();
+    ca.col_list = c->collist.as<int>();
     if (c->cfg.debug) ca.dbg_colnn = c->dbg_colnn.as<int>();
     timed(c, kTimeCollide, [&](cudaStream_t st) { return launch_collide(ca, st); }, "collision kernel");
     timed(c, kTimeCollideNN, [&](cudaStream_t st) { return launch_collide_nn(ca, st); }, "collision matching kernel");
@@ -300,7 +306,10 @@ void iterate(asicp_ctx *c, int mode, float gamma)
     ua.frozen = c->frozen.as<int>();
     ua.phi = c->phi.as<float>();
     ua.h = c->h.as<float>();
-    timed(c, kTimeUpdate, [&](cudaStream_t st) { return launch_update(ua, st); }, "update kernel");
+    ua.col_items = c->colitems.as<int>();
+    timed(c, kTimeFinalize, [&](cudaStream_t st) { return launch_finalize(ua, st); }, "finalize kernel");
+    if (mode == 1)
+        timed(c, kTimeStein, [&](cudaStream_t st) { return launch_stein(ua, st); }, "Stein kernel");
 }
 
 void step_impl(asicp_ctx *c, int k)
@@ -324,7 +333,7 @@ void run_loop(asicp_ctx *c)
 // Buffers and sizes the captured graph depends on.
 std::vector<const void *> loop_key(const asicp_ctx *c)
 {
-    return {c->S.p, c->R.p, c->Rx.p, c->rmax.p, c->C.p, c->com.p, c->pconst.p, c->dmeta.p, c->theta.p, c->fsums.p,
+    return {c->colitems.p, c->collist.p, c->S.p, c->R.p, c->Rx.p, c->rmax.p, c->C.p, c->com.p, c->pconst.p, c->dmeta.p, c->theta.p, c->fsums.p,
             c->csums.p, c->ncol.p, c->colidx.p, c->cost.p, c->grad.p, c->prev.p, c->frozen.p, c->phi.p, c->h.p,
             c->order.p, c->errw.p, c->nnidx.p, c->dbg_d2.p, c->dbg_sp.p, c->dbg_colnn.p,
             reinterpret_cast<const void *>((size_t)c->M), reinterpret_cast<const void *>((size_t)c->Mpad),
@@ -697,7 +706,7 @@ asicp_status asicp_get_state(asicp_ctx *ctx, const asicp_state_view *v)
     });
 }
 
-asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[4], long long launches[4], int reset)
+asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[5], long long launches[5], int reset)
 {
     return guarded(ctx, [&] {
         if (!ctx->cfg.profile) fail(ASICP_ERR_STATE, "kernel_times: config.profile is 0");
@@ -712,12 +721,12 @@ asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[4], long long launches
             ctx->pool.push_back(e.b);
         }
         ctx->events.clear();
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < kTimeKinds; ++i) {
             if (ms) ms[i] = ctx->acc_ms[i];
             if (launches) launches[i] = ctx->acc_n[i];
         }
         if (reset)
-            for (int i = 0; i < 4; ++i) { ctx->acc_ms[i] = 0; ctx->acc_n[i] = 0; }
+            for (int i = 0; i < kTimeKinds; ++i) { ctx->acc_ms[i] = 0; ctx->acc_n[i] = 0; }
     });
 }
 

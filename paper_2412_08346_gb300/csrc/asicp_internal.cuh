@@ -68,6 +68,61 @@ __device__ __forceinline__ float dist2_f32(float ax, float ay, float az, float b
     return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
+// Double-float accumulation (hi + lo, ~48-bit significand) from float32 error-free
+// transformations: products are split exactly by an FMA, sums by two-sum.  Used
+// for the per-particle sums, where float64 arithmetic would dominate the run time
+// on GB300 (float64 rate 1/64 of float32).
+struct dfloat {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+__device__ __forceinline__ void df_add(dfloat &x, float v)
+{
+    float s, e;
+    two_sum(x.hi, v, s, e);
+    x.hi = s;
+    x.lo = __fadd_rn(x.lo, e);
+}
+
+__device__ __forceinline__ void df_add_prod(dfloat &x, float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);      // a * b = p + pe exactly
+    float s, e;
+    two_sum(x.hi, p, s, e);
+    x.hi = s;
+    x.lo = __fadd_rn(x.lo, __fadd_rn(e, pe));
+}
+
+__device__ __forceinline__ void df_merge(dfloat &x, const dfloat &y)
+{
+    float s, e;
+    two_sum(x.hi, y.hi, s, e);
+    x.hi = s;
+    x.lo = __fadd_rn(x.lo, __fadd_rn(e, y.lo));
+}
+
+template <int N>
+__device__ __forceinline__ void warp_sum_df(dfloat (&v)[N])
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            dfloat y;
+            y.hi = __shfl_xor_sync(0xffffffffu, v[c].hi, o);
+            y.lo = __shfl_xor_sync(0xffffffffu, v[c].lo, o);
+            df_merge(v[c], y);
+        }
+}
+
 template <int N>
 __device__ __forceinline__ void warp_sum_f64(double (&v)[N])
 {
@@ -97,7 +152,7 @@ cudaError_t init_collision_attributes();
 cudaError_t init_update_attributes();
 cudaError_t launch_ref_prep(const float4 *R, int M, int Mpad, void *Rx, float *rmax, cudaStream_t st);
 
-constexpr int kColChunk = 256;         // colliding points per reverse-matching CTA
+constexpr int kColChunk = 64;          // colliding points per reverse-matching work item
 
 struct CollideArgs {
     const float4 *C;          // [Mc]
@@ -112,6 +167,8 @@ struct CollideArgs {
     double *fsums;            // [PK][kFwdSums]
     double *csums;            // [PK][ceil(Mc / kColChunk)][kColSums]
     int *dbg_colnn;           // [PK][Mc] or null
+    int *col_items;           // (count, next) of the reverse-matching work list
+    int *col_list;            // [PK * ceil(Mc / kColChunk)] work items pk * chunks + chunk
 };
 cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st);
 cudaError_t launch_collide_nn(const CollideArgs &a, cudaStream_t st);
@@ -136,8 +193,10 @@ struct UpdateArgs {
     int *frozen;              // [PK]
     float *phi;               // [PK][8]
     float *h;                 // [P]
+    int *col_items;           // collision work-list counters (count, next), cleared for the next pass
 };
-cudaError_t launch_update(const UpdateArgs &a, cudaStream_t st);
+cudaError_t launch_finalize(const UpdateArgs &a, cudaStream_t st);   // cost/gradient, convergence, SGD step
+cudaError_t launch_stein(const UpdateArgs &a, cudaStream_t st);      // SVGD step (mode 1)
 
 cudaError_t launch_pack_points(const float *xyz, int n, float4 *out, int *err, cudaStream_t st);
 cudaError_t launch_check_finite(const float *v, long long n, int *err, cudaStream_t st);

@@ -38,14 +38,16 @@ __device__ __forceinline__ bool sdf_lookup(const SdfMeta &m, float x, float y, f
     return true;
 }
 
+// Block sum of double-float accumulators: warp trees in double-float, then the
+// warps' partials added in float64 in warp order by NV threads.
 template <int NV>
-__device__ __forceinline__ void block_reduce_store(double (&acc)[NV], double (*sred)[NV], double *out)
+__device__ __forceinline__ void block_reduce_store(dfloat (&acc)[NV], double (*sred)[NV], double *out)
 {
-    warp_sum_f64(acc);
+    warp_sum_df(acc);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0)
 #pragma unroll
-        for (int c = 0; c < NV; ++c) sred[warp][c] = acc[c];
+        for (int c = 0; c < NV; ++c) sred[warp][c] = (double)acc[c].hi + (double)acc[c].lo;
     __syncthreads();
     if (threadIdx.x < NV) {
         double s = 0.0;
@@ -76,22 +78,22 @@ __global__ void __launch_bounds__(kColThreads) collide_kernel(const CollideArgs 
     quat_rot_f32(th[3], th[4], th[5], th[6], Rm);
 
     {
-        double acc[kFwdSums];
+        dfloat acc[kFwdSums];
 #pragma unroll
-        for (int c = 0; c < kFwdSums; ++c) acc[c] = 0.0;
+        for (int c = 0; c < kFwdSums; ++c) acc[c] = dfloat{0.f, 0.f};
         const float4 *S = a.S + (size_t)p * a.N;
         const int *idx = a.nn_idx + (size_t)pk * a.N;
         for (int i = threadIdx.x; i < a.N; i += kColThreads) {
             const float4 s = S[i];
             const float4 r = __ldg(a.R + idx[i]);
-            const double rv[3] = {r.x, r.y, r.z}, sv[3] = {s.x, s.y, s.z};
+            const float rv[3] = {r.x, r.y, r.z}, sv[3] = {s.x, s.y, s.z};
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
-                acc[u] += rv[u];
+                df_add(acc[u], rv[u]);
 #pragma unroll
-                for (int v = 0; v < 3; ++v) acc[3 + 3 * u + v] = fma(rv[u], sv[v], acc[3 + 3 * u + v]);
+                for (int v = 0; v < 3; ++v) df_add_prod(acc[3 + 3 * u + v], rv[u], sv[v]);
+                df_add_prod(acc[12], rv[u], rv[u]);
             }
-            acc[12] = fma(rv[0], rv[0], fma(rv[1], rv[1], fma(rv[2], rv[2], acc[12])));
         }
         block_reduce_store<kFwdSums>(acc, sred, a.fsums + (size_t)pk * kFwdSums);
     }
@@ -127,65 +129,105 @@ __global__ void __launch_bounds__(kColThreads) collide_kernel(const CollideArgs 
         count += tot;
         __syncthreads();
     }
-    if (threadIdx.x == 0) a.ncol[pk] = count;
+    if (threadIdx.x == 0) {
+        a.ncol[pk] = count;
+        // queue this particle's chunks of colliding points for the reverse matching
+        const int chunks = (a.Mc + kColChunk - 1) / kColChunk, used = (count + kColChunk - 1) / kColChunk;
+        if (used > 0) {
+            const int base = atomicAdd(&a.col_items[0], used);
+            for (int c = 0; c < used; ++c) a.col_list[base + c] = pk * chunks + c;
+        }
+    }
 }
 
-// Grid (particle, chunk of kColChunk colliding points); chunks past the
-// particle's colliding count exit at once.  The particle's transformed contact
-// cloud is built in shared memory with the same float32 transform as the
-// forward matching, then each colliding point finds its nearest contact point
-// (ties to the lowest index).  Per chunk, the float64 sums the collision cost
-// and gradient are linear in:
+// Persistent: CTAs take (particle, chunk of kColChunk colliding points) items
+// from the list the collision kernel filled.  For an item the particle's
+// transformed contact cloud is built in shared memory with the same float32
+// transform as the forward matching; each warp then matches kQW colliding
+// points against it (lanes stride over the contact points, a shuffle reduction
+// picks the smallest distance, ties to the lowest index).  Per item, the sums
+// the collision cost and gradient are linear in (double-float accumulation of
+// exact products):
 //   sum s (3), sum s s^T (xx,xy,xz,yy,yz,zz) (6), sum c (3), sum c s^T (9), sum |c|^2 (1)
-// with s the matched gripper point in the gripper frame; the update kernel adds
-// the chunks in order.
+// with s the matched gripper point in the gripper frame; the finalize kernel
+// adds the chunks of a particle in chunk order, so the result does not depend
+// on which CTA took which item.
 __global__ void __launch_bounds__(kColThreads) collide_nn_kernel(const CollideArgs a)
 {
+    constexpr int kQW = kColChunk / (kColThreads / 32);     // colliding points per warp
     extern __shared__ float4 sSp[];
     __shared__ double sred[kColThreads / 32][kColSums];
-    const int pk = blockIdx.x, p = pk / a.K;
-    const int n = a.ncol[pk];
-    const int l0 = blockIdx.y * kColChunk;
-    if (l0 >= n) return;
-    const float *th = a.theta + (size_t)pk * 8;
-    const float tx = th[0], ty = th[1], tz = th[2];
-    float Rm[9];
-    quat_rot_f32(th[3], th[4], th[5], th[6], Rm);
-    const float4 *S = a.S + (size_t)p * a.N;
-    for (int i = threadIdx.x; i < a.N; i += kColThreads) {
-        const float4 s = S[i];
-        const float3 o = xform_f32(Rm, tx, ty, tz, s.x, s.y, s.z);
-        sSp[i] = make_float4(o.x, o.y, o.z, 0.f);
-    }
-    __syncthreads();
-    double acc[kColSums];
-#pragma unroll
-    for (int c = 0; c < kColSums; ++c) acc[c] = 0.0;
-    const int l = l0 + threadIdx.x;
-    if (l < n) {
-        const float4 c = a.C[a.colidx[(size_t)pk * a.Mc + l]];
-        float best = __int_as_float(0x7f800000);
-        int bi = 0;
-        for (int i = 0; i < a.N; ++i) {
-            const float4 s = sSp[i];
-            const float d = dist2_f32(s.x, s.y, s.z, c.x, c.y, c.z);
-            if (d < best) { best = d; bi = i; }
+    __shared__ int s_item;
+    const int chunks = (a.Mc + kColChunk - 1) / kColChunk;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&a.col_items[1], 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= a.col_items[0]) break;
+        const int code = a.col_list[item];
+        const int pk = code / chunks, chunk = code - pk * chunks, p = pk / a.K;
+        const int n = a.ncol[pk];
+        const float *th = a.theta + (size_t)pk * 8;
+        const float tx = th[0], ty = th[1], tz = th[2];
+        float Rm[9];
+        quat_rot_f32(th[3], th[4], th[5], th[6], Rm);
+        const float4 *S = a.S + (size_t)p * a.N;
+        for (int i = threadIdx.x; i < a.N; i += kColThreads) {
+            const float4 s = S[i];
+            const float3 o = xform_f32(Rm, tx, ty, tz, s.x, s.y, s.z);
+            sSp[i] = make_float4(o.x, o.y, o.z, 0.f);
         }
-        if (a.dbg_colnn) a.dbg_colnn[(size_t)pk * a.Mc + l] = bi;
-        const float4 s = S[bi];
-        const double sv[3] = {s.x, s.y, s.z}, cv[3] = {c.x, c.y, c.z};
-        acc[0] = sv[0]; acc[1] = sv[1]; acc[2] = sv[2];
-        acc[3] = sv[0] * sv[0]; acc[4] = sv[0] * sv[1]; acc[5] = sv[0] * sv[2];
-        acc[6] = sv[1] * sv[1]; acc[7] = sv[1] * sv[2]; acc[8] = sv[2] * sv[2];
-        acc[9] = cv[0]; acc[10] = cv[1]; acc[11] = cv[2];
+        __syncthreads();
+        const int l0 = chunk * kColChunk + warp * kQW;
+        float cx[kQW], cy[kQW], cz[kQW], best[kQW];
+        int bi[kQW];
 #pragma unroll
-        for (int u = 0; u < 3; ++u)
+        for (int q = 0; q < kQW; ++q) {
+            float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (l0 + q < n) c = a.C[a.colidx[(size_t)pk * a.Mc + l0 + q]];
+            cx[q] = c.x; cy[q] = c.y; cz[q] = c.z;
+            best[q] = __int_as_float(0x7f800000);
+            bi[q] = 0;
+        }
+        for (int i = lane; i < a.N; i += 32) {
+            const float4 s = sSp[i];
 #pragma unroll
-            for (int v = 0; v < 3; ++v) acc[12 + 3 * u + v] = cv[u] * sv[v];
-        acc[21] = fma(cv[0], cv[0], fma(cv[1], cv[1], cv[2] * cv[2]));
+            for (int q = 0; q < kQW; ++q) {
+                const float d = dist2_f32(s.x, s.y, s.z, cx[q], cy[q], cz[q]);
+                if (d < best[q]) { best[q] = d; bi[q] = i; }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kQW; ++q)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best[q], o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi[q], o);
+                if (ob < best[q] || (ob == best[q] && oi < bi[q])) { best[q] = ob; bi[q] = oi; }
+            }
+        dfloat acc[kColSums];
+#pragma unroll
+        for (int c = 0; c < kColSums; ++c) acc[c] = dfloat{0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < kQW; ++q) {
+            if (lane != q || l0 + q >= n) continue;       // lane q records colliding point q
+            if (a.dbg_colnn) a.dbg_colnn[(size_t)pk * a.Mc + l0 + q] = bi[q];
+            const float4 s = S[bi[q]];
+            const float sv[3] = {s.x, s.y, s.z}, cv[3] = {cx[q], cy[q], cz[q]};
+            acc[0] = dfloat{sv[0], 0.f}; acc[1] = dfloat{sv[1], 0.f}; acc[2] = dfloat{sv[2], 0.f};
+            df_add_prod(acc[3], sv[0], sv[0]); df_add_prod(acc[4], sv[0], sv[1]); df_add_prod(acc[5], sv[0], sv[2]);
+            df_add_prod(acc[6], sv[1], sv[1]); df_add_prod(acc[7], sv[1], sv[2]); df_add_prod(acc[8], sv[2], sv[2]);
+            acc[9] = dfloat{cv[0], 0.f}; acc[10] = dfloat{cv[1], 0.f}; acc[11] = dfloat{cv[2], 0.f};
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+#pragma unroll
+                for (int v = 0; v < 3; ++v) df_add_prod(acc[12 + 3 * u + v], cv[u], sv[v]);
+            df_add_prod(acc[21], cv[0], cv[0]); df_add_prod(acc[21], cv[1], cv[1]); df_add_prod(acc[21], cv[2], cv[2]);
+        }
+        block_reduce_store<kColSums>(acc, sred, a.csums + ((size_t)pk * chunks + chunk) * kColSums);
+        __syncthreads();   // sSp, sred and s_item are reused by the next item
     }
-    const int nchunks = (a.Mc + kColChunk - 1) / kColChunk;
-    block_reduce_store<kColSums>(acc, sred, a.csums + ((size_t)pk * nchunks + blockIdx.y) * kColSums);
 }
 
 cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st)
@@ -202,8 +244,14 @@ cudaError_t init_collision_attributes()
 
 cudaError_t launch_collide_nn(const CollideArgs &a, cudaStream_t st)
 {
+    static int grid = 0;
+    if (grid == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid = 4 * sms;
+    }
     const size_t smem = sizeof(float4) * (size_t)a.N;
-    dim3 grid(a.PK, (a.Mc + kColChunk - 1) / kColChunk);
     collide_nn_kernel<<<grid, kColThreads, smem, st>>>(a);
     return cudaGetLastError();
 }

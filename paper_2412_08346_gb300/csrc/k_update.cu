@@ -65,16 +65,99 @@ __device__ __forceinline__ float pair_d2(float4 a, float4 b)
 
 }  // namespace
 
-// One CTA per preshape, one thread per particle.
+// Per particle (one thread each, small CTAs so the float64 work spreads over
+// many SMs):
 //  1. cost and gradient from the matching sums (Eqs. 13-17) or, for a particle
 //     with colliding points, from the collision sums (Eq. 18 with Eqs. 4-5),
 //     quaternion block projected onto the tangent space at q;
 //  2. convergence bookkeeping (SGD phase);
-//  3. mode 1: median-heuristic bandwidth (exact radix select of the lower
-//     median of |t_i - t_j|^2, i < j), Stein direction of Eq. 8 read as the mean
-//     of Eq. 6 with the kernels of Eqs. 9-10 per block, update of Eq. 7;
-//     mode 2: SGD-ICP update of Eq. 3 (A = I); mode 0: no update.
-__global__ void __launch_bounds__(kMaxK) update_kernel(const UpdateArgs a)
+//  3. mode 2: the SGD-ICP update of Eq. 3 (A = I); modes 0 (evaluate only) and 1
+//     (SVGD, done by stein_kernel) leave the poses alone.
+//  Thread 0 of CTA 0 also clears the collision work-list counters for the next pass.
+constexpr int kFinalizeThreads = 32;
+
+__global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(const UpdateArgs a)
+{
+    const int PK = a.P * a.K;
+    const int pk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pk == 0 && a.col_items) { a.col_items[0] = 0; a.col_items[1] = 0; }
+    if (pk >= PK) return;
+    const int p = pk / a.K;
+    double t[3], q[4], g[7];
+    const float *th = a.theta + (size_t)pk * 8;
+    for (int c = 0; c < 3; ++c) t[c] = th[c];
+    for (int c = 0; c < 4; ++c) q[c] = th[3 + c];
+    double R[9];
+    quat_rot_f64(q[0], q[1], q[2], q[3], R);
+    const int nc = a.ncol[pk];
+    double se2, Se[3], E[9], cnt;
+    if (nc == 0) {
+        double fs[kFwdSums];
+        for (int c = 0; c < kFwdSums; ++c) fs[c] = a.fsums[(size_t)pk * kFwdSums + c];
+        const double *pc = a.pconst + (size_t)p * 12;
+        double SS[9];
+        sym_full(pc + 3, SS);
+        residual_moments(R, t, (double)a.N, pc, SS, fs, fs + 3, fs[12], &se2, Se, E);
+        // TCP-CoM term (Eq. 15) inside the 1/N, weight w_com (Eqs. 16-17)
+        const double tcp[3] = {pc[0] / a.N, pc[1] / a.N, pc[2] / a.N};
+        double ec[3];
+        for (int u = 0; u < 3; ++u)
+            ec[u] = R[u * 3 + 0] * tcp[0] + R[u * 3 + 1] * tcp[1] + R[u * 3 + 2] * tcp[2] + t[u] - a.com[u];
+        se2 += a.w_com * (ec[0] * ec[0] + ec[1] * ec[1] + ec[2] * ec[2]);
+        for (int u = 0; u < 3; ++u) {
+            Se[u] += a.w_com * ec[u];
+            for (int v = 0; v < 3; ++v) E[u * 3 + v] += a.w_com * ec[u] * tcp[v];
+        }
+        cnt = (double)a.N;
+    } else {
+        // add the per-chunk collision sums in chunk order
+        const int nchunks = (a.Mc + kColChunk - 1) / kColChunk, used = (nc + kColChunk - 1) / kColChunk;
+        double cs[kColSums];
+        for (int c = 0; c < kColSums; ++c) cs[c] = 0.0;
+        for (int b = 0; b < used; ++b)
+            for (int c = 0; c < kColSums; ++c) cs[c] += a.csums[((size_t)pk * nchunks + b) * kColSums + c];
+        double SS[9];
+        sym_full(cs + 3, SS);
+        residual_moments(R, t, (double)nc, cs, SS, cs + 9, cs + 12, cs[21], &se2, Se, E);
+        cnt = (double)nc;
+    }
+    double gq[4];
+    quat_grad_from_E(q, E, gq);
+    const double inv = 1.0 / cnt;
+    for (int u = 0; u < 3; ++u) g[u] = Se[u] * inv;
+    for (int u = 0; u < 4; ++u) gq[u] *= inv;
+    const double dq = gq[0] * q[0] + gq[1] * q[1] + gq[2] * q[2] + gq[3] * q[3];
+    for (int u = 0; u < 4; ++u) g[3 + u] = gq[u] - dq * q[u];
+    const double cost = se2 * inv;
+    a.cost[pk] = cost;
+    for (int u = 0; u < 7; ++u) a.grad[(size_t)pk * 8 + u] = g[u];
+    int frozen = a.frozen[pk];
+    if (a.mode == 2 && a.conv_tol >= 0.f) {
+        const double prev = a.prev_cost[pk];
+        if (nc > 0) frozen = 0;
+        else if (prev >= 0.0 && fabs(cost - prev) <= (double)a.conv_tol * prev) frozen = 1;
+        a.frozen[pk] = frozen;
+    }
+    if (a.mode != 0) a.prev_cost[pk] = cost;
+    if (a.mode == 2) {
+        float *tw = a.theta + (size_t)pk * 8;
+        for (int u = 0; u < 7; ++u) a.phi[(size_t)pk * 8 + u] = 0.f;
+        if (pk < a.P) a.h[pk] = 0.f;
+        if (!frozen) {
+            double nq[4];
+            for (int u = 0; u < 4; ++u) nq[u] = q[u] - (double)a.eta_sgd * g[3 + u];
+            const double nn = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
+            for (int u = 0; u < 3; ++u) tw[u] = (float)(t[u] - (double)a.eta_sgd * g[u]);
+            for (int u = 0; u < 4; ++u) tw[3 + u] = (float)(nq[u] / nn);
+        }
+    }
+}
+
+// SVGD phase, one CTA per preshape, one thread per particle: median-heuristic
+// bandwidth (exact radix select of the lower median of |t_i - t_j|^2, i < j),
+// Stein direction of Eq. 8 read as the mean of Eq. 6 with the kernels of
+// Eqs. 9-10 per block, and the update of Eq. 7.
+__global__ void __launch_bounds__(kMaxK) stein_kernel(const UpdateArgs a)
 {
     extern __shared__ float4 sm[];
     float4 *sT = sm;                  // [K] t (xyz)
@@ -87,87 +170,10 @@ __global__ void __launch_bounds__(kMaxK) update_kernel(const UpdateArgs a)
     const int p = blockIdx.x, j = threadIdx.x, K = a.K;
     const bool active = j < K;
     const size_t pk = (size_t)p * K + j;
-    double t[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, g[7] = {0, 0, 0, 0, 0, 0, 0};
-    int frozen = 0;
-    if (active) {
-        const float *th = a.theta + pk * 8;
-        for (int c = 0; c < 3; ++c) t[c] = th[c];
-        for (int c = 0; c < 4; ++c) q[c] = th[3 + c];
-        double R[9];
-        quat_rot_f64(q[0], q[1], q[2], q[3], R);
-        const int nc = a.ncol[pk];
-        double se2, Se[3], E[9], cnt;
-        if (nc == 0) {
-            double fs[kFwdSums];
-            for (int c = 0; c < kFwdSums; ++c) fs[c] = a.fsums[pk * kFwdSums + c];
-            const double *pc = a.pconst + (size_t)p * 12;
-            double SS[9];
-            sym_full(pc + 3, SS);
-            residual_moments(R, t, (double)a.N, pc, SS, fs, fs + 3, fs[12], &se2, Se, E);
-            // TCP-CoM term (Eq. 15) inside the 1/N, weight w_com (Eqs. 16-17)
-            const double tcp[3] = {pc[0] / a.N, pc[1] / a.N, pc[2] / a.N};
-            double ec[3];
-            for (int u = 0; u < 3; ++u)
-                ec[u] = R[u * 3 + 0] * tcp[0] + R[u * 3 + 1] * tcp[1] + R[u * 3 + 2] * tcp[2] + t[u] - a.com[u];
-            se2 += a.w_com * (ec[0] * ec[0] + ec[1] * ec[1] + ec[2] * ec[2]);
-            for (int u = 0; u < 3; ++u) {
-                Se[u] += a.w_com * ec[u];
-                for (int v = 0; v < 3; ++v) E[u * 3 + v] += a.w_com * ec[u] * tcp[v];
-            }
-            cnt = (double)a.N;
-        } else {
-            // add the per-chunk collision sums in chunk order
-            const int nchunks = (a.Mc + kColChunk - 1) / kColChunk, used = (nc + kColChunk - 1) / kColChunk;
-            double cs[kColSums];
-            for (int c = 0; c < kColSums; ++c) cs[c] = 0.0;
-            for (int b = 0; b < used; ++b)
-                for (int c = 0; c < kColSums; ++c) cs[c] += a.csums[(pk * nchunks + b) * kColSums + c];
-            double SS[9];
-            sym_full(cs + 3, SS);
-            residual_moments(R, t, (double)nc, cs, SS, cs + 9, cs + 12, cs[21], &se2, Se, E);
-            cnt = (double)nc;
-        }
-        double gq[4];
-        quat_grad_from_E(q, E, gq);
-        for (int u = 0; u < 3; ++u) g[u] = Se[u] / cnt;
-        for (int u = 0; u < 4; ++u) gq[u] /= cnt;
-        const double dq = gq[0] * q[0] + gq[1] * q[1] + gq[2] * q[2] + gq[3] * q[3];
-        for (int u = 0; u < 4; ++u) g[3 + u] = gq[u] - dq * q[u];
-        const double cost = se2 / cnt;
-        a.cost[pk] = cost;
-        for (int u = 0; u < 7; ++u) a.grad[pk * 8 + u] = g[u];
-        frozen = a.frozen[pk];
-        if (a.mode == 2 && a.conv_tol >= 0.f) {
-            const double prev = a.prev_cost[pk];
-            if (nc > 0) frozen = 0;
-            else if (prev >= 0.0 && fabs(cost - prev) <= (double)a.conv_tol * prev) frozen = 1;
-            a.frozen[pk] = frozen;
-        }
-        if (a.mode != 0) a.prev_cost[pk] = cost;
-    }
-    if (a.mode == 0) return;
-
-    if (a.mode == 2) {
-        if (active) {
-            float *th = a.theta + pk * 8;
-            for (int u = 0; u < 7; ++u) a.phi[pk * 8 + u] = 0.f;
-            if (!frozen) {
-                double nt[3], nq[4];
-                for (int u = 0; u < 3; ++u) nt[u] = t[u] - (double)a.eta_sgd * g[u];
-                for (int u = 0; u < 4; ++u) nq[u] = q[u] - (double)a.eta_sgd * g[3 + u];
-                const double nn = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
-                for (int u = 0; u < 3; ++u) th[u] = (float)nt[u];
-                for (int u = 0; u < 4; ++u) th[3 + u] = (float)(nq[u] / nn);
-            }
-        }
-        if (j == 0) a.h[p] = 0.f;
-        return;
-    }
-
-    // ---------------------------------------------------------- SVGD phase
     const float gN = -a.gamma * (float)a.N;
     if (active) {
         const float *th = a.theta + pk * 8;
+        const double *g = a.grad + pk * 8;
         sT[j] = make_float4(th[0], th[1], th[2], 0.f);
         sQ[j] = make_float4(th[3], th[4], th[5], th[6]);
         sDt[j] = make_float4(gN * (float)g[0], gN * (float)g[1], gN * (float)g[2], 0.f);
@@ -264,15 +270,22 @@ __global__ void __launch_bounds__(kMaxK) update_kernel(const UpdateArgs a)
 
 cudaError_t init_update_attributes()
 {
-    return cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(stein_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(float4) * 4 * kMaxK));
 }
 
-cudaError_t launch_update(const UpdateArgs &a, cudaStream_t st)
+cudaError_t launch_finalize(const UpdateArgs &a, cudaStream_t st)
+{
+    const int PK = a.P * a.K;
+    finalize_kernel<<<(PK + kFinalizeThreads - 1) / kFinalizeThreads, kFinalizeThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stein(const UpdateArgs &a, cudaStream_t st)
 {
     const int threads = ((a.K + 31) / 32) * 32;
     const size_t smem = sizeof(float4) * 4 * (size_t)a.K;
-    update_kernel<<<a.P, threads, smem, st>>>(a);
+    stein_kernel<<<a.P, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -282,5 +282,5 @@ def test_kernel_times_from_graph_replays(stream):
         del keep
     finally:
         asicp.asicp_destroy(ctx)
-    assert n == [2 * (w.k_max + 1)] * 4
+    assert n == [2 * (w.k_max + 1)] * 4 + [2 * w.k_stein]
     assert all(t > 0 for t in ms)
