@@ -61,7 +61,15 @@ typedef enum {
  *   debug         1: keep per-query correspondences, transformed points and collision
  *                  lists so asicp_get_state can return them (costs memory and bandwidth)
  *   profile       1: time the main kernels with CUDA events (asicp_kernel_times)
- *   cuda_stream   cudaStream_t for all work, NULL for the default stream            */
+ *   cuda_stream   cudaStream_t for all work, NULL for the default stream
+ *   n_objects     objects optimised together in one pass (one grasp set each, default 1);
+ *                  every kernel covers all of them, each particle matched against its
+ *                  own object (Section IV-D's "combine into multidimensional tensors",
+ *                  extended across objects)
+ * Particles are numbered object by object, preshape by preshape: the group
+ * g = object * P + preshape holds K_g particles (K_g = K unless set with
+ * asicp_set_particle_counts); T = sum of K_g is the particle count of every
+ * per-particle array below. */
 typedef struct {
     int P, K;
     int k_max, k_stein;
@@ -76,24 +84,28 @@ typedef struct {
     int debug;
     int profile;
     void *cuda_stream;
+    int n_objects;
 } asicp_config;
 
 /* Host pointers (or device pointers) the library fills in asicp_get_state; any
- * may be NULL.  Flat particle index = p * K + j.
- *   theta     P*K*7 float   poses (after the last step's update)
- *   cost      P*K   double  cost at the poses the last step started from: the match
+ * may be NULL.  T = total particle count; with one object and uniform K the flat
+ * particle index is p * K + j.
+ *   theta     T*7 float     poses (after the last step's update)
+ *   cost      T   double    cost at the poses the last step started from: the match
  *                           cost L (Eqs. 13-15) or, for a colliding particle, L_col (Eq. 18)
- *   grad      P*K*7 double  gradient used by the last step (Eqs. 16-17, or Eq. 18 via 4-5)
- *   phi       P*K*7 float   Stein direction of the last step (Eq. 8; zero in the SGD phase)
- *   ncol      P*K   int     colliding points of C at those poses (Eq. 12)
- *   frozen    P*K   int     convergence flag
- *   h         P     float   RBF bandwidth of the last SVGD step (Eq. 9)
+ *   grad      T*7 double    gradient used by the last step (Eqs. 16-17, or Eq. 18 via 4-5)
+ *   phi       T*7 float     Stein direction of the last step (Eq. 8; zero in the SGD phase)
+ *   ncol      T   int       colliding points of C at those poses (Eq. 12)
+ *   frozen    T   int       convergence flag
+ *   h         G   float     RBF bandwidth of every group in the last SVGD step (Eq. 9)
  * needing config.debug = 1:
- *   nn_idx    P*K*N int     forward correspondence index into R per gripper point (Eq. 1)
- *   nn_d2     P*K*N float   its squared distance
- *   s_prime   P*K*N*3 float transformed gripper points exactly as matched
- *   col_list  P*K*Mc int    colliding C indices, ascending, first ncol entries valid
- *   col_nn    P*K*Mc int    nearest gripper point per colliding point (Eq. 18)     */
+ *   nn_idx    T*N int       forward correspondence index into R per gripper point (Eq. 1)
+ *   nn_d2     T*N float     its squared distance
+ *   s_prime   T*N*3 float   transformed gripper points exactly as matched
+ *   col_list  sum over particles of their object's Mc, int: for every particle, Mc
+ *                           entries (object by object, particle by particle); the first
+ *                           ncol hold the colliding C indices, ascending
+ *   col_nn    same layout   nearest gripper point per colliding point (Eq. 18)     */
 typedef struct {
     float *theta;
     double *cost;
@@ -109,7 +121,7 @@ typedef struct {
     int *col_nn;
 } asicp_state_view;
 
-/* Fill *cfg with the defaults described above for P = 1, K = 32, k_max = 40. */
+/* Fill *cfg with the defaults described above for P = 1, K = 32, k_max = 40, one object. */
 void asicp_config_default(asicp_config *cfg);
 
 /* Create a context for one GPU (the current device).  *out receives the handle.
@@ -125,18 +137,27 @@ asicp_status asicp_destroy(asicp_ctx *ctx);
  * Errors: INVALID_ARG (NULL R, M < 1, Mc < 1 when C is given, non-finite value). */
 asicp_status asicp_set_object(asicp_ctx *ctx, const float *R_xyz, int M, const float *C_xyz, int Mc);
 
+/* The same for object `object` (0 <= object < n_objects); objects may have
+ * different M and Mc.  Errors: as asicp_set_object, INVALID_ARG for the index. */
+asicp_status asicp_set_object_at(asicp_ctx *ctx, int object, const float *R_xyz, int M, const float *C_xyz, int Mc);
+
+/* Particles per group: K[object * P + preshape], n = n_objects * P values in
+ * [1, 1024].  Clears the poses.  Errors: INVALID_ARG. */
+asicp_status asicp_set_particle_counts(asicp_ctx *ctx, const int *K, int n);
+
 /* Preshape `preshape` (0 <= preshape < P): contact-surface cloud S (N x 3, gripper
  * frame; the source cloud of Section IV-A) and the gripper's signed distance field
  * sampled on a node-centred grid of nx*ny*nz float32 values, x fastest, positive
  * inside the gripper (Eq. 12), node (0,0,0) at origin, spacing voxel.  Computes
- * TCP = centroid of S (Section IV-B).  Every preshape must have the same N.
- * Errors: INVALID_ARG (index, N < 1, a grid dimension < 2, voxel <= 0, N differing
+ * TCP = centroid of S (Section IV-B).  Every preshape must have the same N
+ * (1 <= N <= 6144).
+ * Errors: INVALID_ARG (index, N out of range, a grid dimension < 2, voxel <= 0, N differing
  * from an earlier preshape, non-finite value). */
 asicp_status asicp_set_gripper_sdf(asicp_ctx *ctx, int preshape, const float *S_xyz, int N,
                                    const float *sdf, int nx, int ny, int nz,
                                    const float origin[3], float voxel);
 
-/* Set all P*K poses (P*K*7 floats; quaternions are normalised) and the iteration
+/* Set all T poses (T*7 floats; quaternions are normalised) and the iteration
  * counter, clearing the convergence state.  Used for warm starts and to
  * teacher-force a single step.  Errors: INVALID_ARG, STATE (inputs not set). */
 asicp_status asicp_set_state(asicp_ctx *ctx, const float *theta, int k);
@@ -147,18 +168,24 @@ asicp_status asicp_set_state(asicp_ctx *ctx, const float *theta, int k);
  * (Eq. 3).  Errors: STATE (inputs or poses not set), INVALID_ARG (k), CUDA. */
 asicp_status asicp_step(asicp_ctx *ctx, int k);
 
-/* Full optimisation of one grasp set: initial poses theta0 (P*K*7, normalised
- * here) or, for theta0 = NULL, the Fibonacci sphere of radius init_radius around
- * the CoM (Section V); k_max steps; a final evaluation of cost and collisions at
- * the last poses; and the ranking used by asicp_best_grasps (Algorithm 1's
- * argmin).  Errors: STATE, INVALID_ARG, CUDA. */
+/* Full optimisation of every object's grasp set: initial poses theta0 (T*7,
+ * normalised here) or, for theta0 = NULL, for every group the Fibonacci sphere of
+ * K_g poses of radius init_radius around its object's CoM (Section V); k_max steps;
+ * a final evaluation of cost and collisions at the last poses; and the per-object
+ * ranking used by asicp_best_grasps (Algorithm 1's argmin).  The loop is replayed
+ * from a captured CUDA graph.  Errors: STATE, INVALID_ARG, CUDA. */
 asicp_status asicp_run(asicp_ctx *ctx, const float *theta0);
 
-/* The topk best particles of the last asicp_run: non-colliding first, then by
- * ascending final cost, ties to the lower flat index.  theta: topk*7 floats,
- * cost: topk floats, preshape: topk ints (any may be NULL); *n_out = entries
- * written (min(topk, P*K)).  Errors: STATE (no completed run), INVALID_ARG. */
+/* The topk best particles of object 0 in the last asicp_run: non-colliding first,
+ * then by ascending final cost, ties to the lower flat index.  theta: topk*7
+ * floats, cost: topk floats, preshape: topk ints (any may be NULL); *n_out =
+ * entries written (min(topk, particles of the object)).
+ * Errors: STATE (no completed run), INVALID_ARG. */
 asicp_status asicp_best_grasps(asicp_ctx *ctx, int topk, float *theta, float *cost, int *preshape, int *n_out);
+
+/* The same for object `object`.  Errors: as asicp_best_grasps, INVALID_ARG for the index. */
+asicp_status asicp_best_grasps_at(asicp_ctx *ctx, int object, int topk, float *theta, float *cost, int *preshape,
+                                  int *n_out);
 
 /* Copy the current particle state into the arrays of *view (see above).
  * Errors: STATE (debug arrays requested without config.debug, or no step yet). */

@@ -26,7 +26,8 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "STATE", 3: "CUDA", 4: "OOM", 5: "
 
 EXPORTED = ("asicp_config_default", "asicp_create", "asicp_destroy", "asicp_set_object",
             "asicp_set_gripper_sdf", "asicp_set_state", "asicp_step", "asicp_run", "asicp_best_grasps",
-            "asicp_get_state", "asicp_kernel_times", "asicp_last_error", "asicp_match_noalloc")
+            "asicp_get_state", "asicp_kernel_times", "asicp_last_error", "asicp_match_noalloc",
+            "asicp_set_object_at", "asicp_set_particle_counts", "asicp_best_grasps_at")
 
 
 class AsicpError(RuntimeError):
@@ -41,7 +42,7 @@ class asicp_config(C.Structure):
                 ("g1", C.c_float), ("eta_sgd", C.c_float), ("eta_svgd", C.c_float), ("w_com", C.c_float),
                 ("bandwidth_mode", C.c_int), ("h_fixed", C.c_float), ("conv_tol", C.c_float),
                 ("init_radius", C.c_float), ("debug", C.c_int), ("profile", C.c_int),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("n_objects", C.c_int)]
 
 
 class asicp_state_view(C.Structure):
@@ -82,6 +83,9 @@ def load(build_if_missing: bool = True):
     lib.asicp_get_state.argtypes = [vp, C.POINTER(asicp_state_view)]
     lib.asicp_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), ip]
     lib.asicp_match_noalloc.argtypes = [vp, ip, ip, vp, ip, vp, ip, vp, vp]
+    lib.asicp_set_object_at.argtypes = [vp, ip, vp, ip, vp, ip]
+    lib.asicp_set_particle_counts.argtypes = [vp, vp, ip]
+    lib.asicp_best_grasps_at.argtypes = [vp, ip, ip, vp, vp, vp, C.POINTER(C.c_int)]
     lib.asicp_last_error.argtypes = [vp]
     lib.asicp_last_error.restype = C.c_char_p
     for name in EXPORTED:
@@ -139,6 +143,18 @@ def asicp_set_object(ctx, R_xyz, C_xyz=None) -> None:
     _check(ctx, load().asicp_set_object(ctx, _ptr(R_xyz), M, _ptr(C_xyz), Mc))
 
 
+def asicp_set_object_at(ctx, obj: int, R_xyz, C_xyz=None) -> None:
+    M = int(R_xyz.shape[0])
+    Mc = int(C_xyz.shape[0]) if C_xyz is not None else 0
+    _check(ctx, load().asicp_set_object_at(ctx, int(obj), _ptr(R_xyz), M, _ptr(C_xyz), Mc))
+
+
+def asicp_set_particle_counts(ctx, K) -> None:
+    """``K`` int32 array of n_objects * P particle counts (object-major)."""
+    K = np.ascontiguousarray(np.asarray(K, dtype=np.int32))
+    _check(ctx, load().asicp_set_particle_counts(ctx, _ptr(K), int(K.size)))
+
+
 def asicp_set_gripper_sdf(ctx, preshape, S_xyz, sdf_zyx, origin, voxel) -> None:
     """``sdf_zyx`` has shape (nz, ny, nx) (x fastest in memory)."""
     nz, ny, nx = (int(d) for d in sdf_zyx.shape)
@@ -162,6 +178,13 @@ def asicp_run(ctx, theta0=None) -> None:
 def asicp_best_grasps(ctx, topk: int, theta=None, cost=None, preshape=None) -> int:
     n = C.c_int(0)
     _check(ctx, load().asicp_best_grasps(ctx, int(topk), _ptr(theta), _ptr(cost), _ptr(preshape), C.byref(n)))
+    return n.value
+
+
+def asicp_best_grasps_at(ctx, obj: int, topk: int, theta=None, cost=None, preshape=None) -> int:
+    n = C.c_int(0)
+    _check(ctx, load().asicp_best_grasps_at(ctx, int(obj), int(topk), _ptr(theta), _ptr(cost), _ptr(preshape),
+                                            C.byref(n)))
     return n.value
 
 

@@ -2,9 +2,15 @@
 // iteration loop of Algorithm 1 and result read-back.  Host code only; every
 // arithmetic step of the method runs in the kernels of k_match.cu,
 // k_collision.cu and k_update.cu.
+//
+// A context holds n_objects objects (one grasp set each) that are optimised
+// together: every kernel covers the particles of all objects, each particle
+// matched against its own object's cloud.  Particles are numbered object by
+// object, preshape by preshape (groups g = o * P + p of K_g particles).
 #include "../../include/asicp.h"
 #include "asicp_internal.cuh"
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -51,7 +57,19 @@ struct DevMem {
         ck(cudaMalloc(&p, want), what);
         bytes = want;
     }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
     template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+struct ObjBufs {
+    DevMem R, Rx, C;          // C stays empty when the collision cloud is R itself
+    int M = 0, Mpad = 0, Mc = 0;
+    bool set = false;
 };
 
 enum { kTimeMatch = 0, kTimeCollide = 1, kTimeCollideNN = 2, kTimeFinalize = 3, kTimeStein = 4, kTimeKinds = 5 };
@@ -62,16 +80,26 @@ struct asicp_ctx {
     asicp_config cfg{};
     cudaStream_t st = nullptr;
     std::string err;
-    int M = 0, Mc = 0, N = 0;
-    bool object_set = false, theta_set = false, stepped = false, run_done = false;
+    int N = 0;
+    int nobj = 1;
+    std::vector<int> Kg;              // particles per group, [nobj * P]
+    std::vector<ObjBufs> objs;
+    bool theta_set = false, stepped = false, run_done = false;
     std::vector<char> pre_set;
     std::vector<SdfMeta> meta;
     std::vector<DevMem> grids;
     int k_next = 0;
 
-    int Mpad = 0;
-    DevMem colitems, collist, box, stage, R, Rx, rmax, C, S, com, pconst, dmeta, theta, fsums, csums, ncol, colidx, cost, grad, prev, frozen,
-        phi, h, order, errw, out7, outc, outi, nnidx, dbg_d2, dbg_sp, dbg_colnn;
+    // layout (rebuilt when objects, particle counts or N change)
+    bool layout_dirty = true;
+    int T = 0, G = 0, n_items = 0;
+    long long colidx_total = 0, csum_total = 0;
+    std::vector<int> grp_off_h;
+    std::vector<ObjMeta> objmeta_h;
+
+    DevMem partgrp, grpoff, objmeta, items, com, rmax, colitems, collist, box, stage, S, pconst, dmeta, theta, fsums,
+        csums, ncol, colidx, cost, grad, prev, frozen, phi, h, order, errw, out7, outc, outi, nnidx, dbg_d2, dbg_sp,
+        dbg_colnn;
 
     // profiling: events recorded around launches (kind, start, stop)
     struct Ev { int kind; cudaEvent_t a, b; };
@@ -88,13 +116,27 @@ struct asicp_ctx {
     bool graph_pending = false;       // a replay's events have not been accumulated yet
     bool capturing = false;
 
-    int PK() const { return cfg.P * cfg.K; }
-    int col_chunks() const { return (Mc + kColChunk - 1) / kColChunk; }
-    bool ready() const
+    bool inputs_ready() const
     {
-        if (!object_set || N == 0) return false;
+        if (N == 0) return false;
+        for (const auto &o : objs) if (!o.set) return false;
         for (char c : pre_set) if (!c) return false;
         return true;
+    }
+    Layout layout() const
+    {
+        Layout L;
+        L.P = cfg.P;
+        L.N = N;
+        L.G = G;
+        L.nobj = nobj;
+        L.T = T;
+        L.part_grp = partgrp.as<int>();
+        L.grp_off = grpoff.as<int>();
+        L.obj = objmeta.as<ObjMeta>();
+        L.com = com.as<double>();
+        L.rmax = rmax.as<float>();
+        return L;
     }
     cudaEvent_t take_event()
     {
@@ -160,48 +202,122 @@ double gamma_of(const asicp_config &c, int k)
     return std::pow(std::fmod((double)k, period) / period, (double)c.p_exp);
 }
 
-void ensure_work(asicp_ctx *c)
+// Offsets, work items and buffers for the current objects, particle counts and N.
+void build_layout(asicp_ctx *c)
 {
-    const size_t PK = c->PK();
-    c->fsums.ensure(sizeof(double) * PK * kFwdSums, "fsums");
-    c->csums.ensure(sizeof(double) * PK * c->col_chunks() * kColSums, "csums");
-    c->colitems.ensure(sizeof(int) * 2, "collision work counters");
-    c->collist.ensure(sizeof(int) * PK * c->col_chunks(), "collision work list");
-    c->nnidx.ensure(sizeof(int) * PK * c->N, "nn_idx");
-    c->ncol.ensure(sizeof(int) * PK, "ncol");
-    c->colidx.ensure(sizeof(int) * PK * (size_t)c->Mc, "colidx");
-    c->cost.ensure(sizeof(double) * PK, "cost");
-    c->grad.ensure(sizeof(double) * PK * 8, "grad");
-    c->prev.ensure(sizeof(double) * PK, "prev_cost");
-    c->frozen.ensure(sizeof(int) * PK, "frozen");
-    c->phi.ensure(sizeof(float) * PK * 8, "phi");
-    c->h.ensure(sizeof(float) * c->cfg.P, "h");
-    c->order.ensure(sizeof(int) * PK, "order");
-    c->out7.ensure(sizeof(float) * PK * 8, "out7");
-    c->outc.ensure(sizeof(float) * PK, "outc");
-    c->outi.ensure(sizeof(int) * PK, "outi");
-    if (c->cfg.debug) {
-        c->dbg_d2.ensure(sizeof(float) * PK * c->N, "dbg_d2");
-        c->dbg_sp.ensure(sizeof(float) * PK * c->N * 3, "dbg_sp");
-        c->dbg_colnn.ensure(sizeof(int) * PK * (size_t)c->Mc, "dbg_colnn");
+    if (!c->layout_dirty) return;
+    if (!c->inputs_ready()) fail(ASICP_ERR_STATE, "objects and every preshape must be set first");
+    const int P = c->cfg.P, G = c->nobj * P, N = c->N;
+    std::vector<int> off(G + 1, 0);
+    for (int g = 0; g < G; ++g) off[g + 1] = off[g] + c->Kg[g];
+    const int T = off[G];
+    std::vector<int> part_grp(T);
+    for (int g = 0; g < G; ++g)
+        for (int i = off[g]; i < off[g + 1]; ++i) part_grp[i] = g;
+    std::vector<ObjMeta> om(c->nobj);
+    std::vector<FwdItem> items;
+    long long colidx_total = 0, csum_total = 0;
+    for (int o = 0; o < c->nobj; ++o) {
+        const ObjBufs &b = c->objs[o];
+        ObjMeta &m = om[o];
+        m.R = b.R.as<float4>();
+        m.Rx = b.Rx.as<ulonglong2>();
+        m.C = b.C.p ? b.C.as<float4>() : b.R.as<float4>();
+        m.M = b.M;
+        m.Mpad = b.Mpad;
+        m.Mc = b.Mc;
+        m.chunks = (b.Mc + kColChunk - 1) / kColChunk;
+        m.pfirst = off[o * P];
+        m.np = off[(o + 1) * P] - off[o * P];
+        m.colidx_base = colidx_total;
+        m.csum_base = csum_total;
+        colidx_total += (long long)m.np * m.Mc;
+        csum_total += (long long)m.np * m.chunks;
+        const long long q0 = (long long)m.pfirst * N, q1 = (long long)(m.pfirst + m.np) * N;
+        for (long long q = q0; q < q1; q += kFwdItemQueries) {
+            FwdItem it;
+            it.q0 = q;
+            it.nq = (int)std::min<long long>(kFwdItemQueries, q1 - q);
+            it.obj = o;
+            items.push_back(it);
+        }
     }
+    // longest items first: the persistent matching kernel deals them out round-robin
+    std::stable_sort(items.begin(), items.end(), [&](const FwdItem &x, const FwdItem &y) {
+        return (long long)x.nq * om[x.obj].Mpad > (long long)y.nq * om[y.obj].Mpad;
+    });
+
+    if (T != c->T) {
+        c->theta_set = false;
+        c->run_done = false;
+    }
+    c->T = T;
+    c->G = G;
+    c->n_items = (int)items.size();
+    c->colidx_total = colidx_total;
+    c->csum_total = csum_total;
+    c->grp_off_h = off;
+    c->objmeta_h = om;
+
+    c->partgrp.ensure(sizeof(int) * T, "particle groups");
+    c->grpoff.ensure(sizeof(int) * (G + 1), "group offsets");
+    c->objmeta.ensure(sizeof(ObjMeta) * c->nobj, "object table");
+    c->items.ensure(sizeof(FwdItem) * std::max<size_t>(1, items.size()), "matching work items");
+    c->theta.ensure(sizeof(float) * 8 * (size_t)T, "poses");
+    c->fsums.ensure(sizeof(double) * T * kFwdSums, "fsums");
+    c->csums.ensure(sizeof(double) * std::max<long long>(1, csum_total) * kColSums, "csums");
+    c->colitems.ensure(sizeof(int) * 2, "collision work counters");
+    c->collist.ensure(sizeof(int) * 2 * std::max<long long>(1, csum_total), "collision work list");
+    c->nnidx.ensure(sizeof(int) * (size_t)T * N, "nn_idx");
+    c->ncol.ensure(sizeof(int) * T, "ncol");
+    c->colidx.ensure(sizeof(int) * std::max<long long>(1, colidx_total), "colidx");
+    c->cost.ensure(sizeof(double) * T, "cost");
+    c->grad.ensure(sizeof(double) * T * 8, "grad");
+    c->prev.ensure(sizeof(double) * T, "prev_cost");
+    c->frozen.ensure(sizeof(int) * T, "frozen");
+    c->phi.ensure(sizeof(float) * T * 8, "phi");
+    c->h.ensure(sizeof(float) * G, "h");
+    c->order.ensure(sizeof(int) * T, "order");
+    c->out7.ensure(sizeof(float) * T * 8, "out7");
+    c->outc.ensure(sizeof(float) * T, "outc");
+    c->outi.ensure(sizeof(int) * T, "outi");
+    if (c->cfg.debug) {
+        c->dbg_d2.ensure(sizeof(float) * (size_t)T * N, "dbg_d2");
+        c->dbg_sp.ensure(sizeof(float) * (size_t)T * N * 3, "dbg_sp");
+        c->dbg_colnn.ensure(sizeof(int) * std::max<long long>(1, colidx_total), "dbg_colnn");
+    }
+    // device tables (pageable sources: the copies complete before returning)
+    ck(cudaMemcpyAsync(c->partgrp.p, part_grp.data(), sizeof(int) * T, cudaMemcpyHostToDevice, c->st), "particle groups");
+    ck(cudaMemcpyAsync(c->grpoff.p, off.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, c->st), "group offsets");
+    ck(cudaMemcpyAsync(c->objmeta.p, om.data(), sizeof(ObjMeta) * c->nobj, cudaMemcpyHostToDevice, c->st),
+       "object table");
+    if (!items.empty())
+        ck(cudaMemcpyAsync(c->items.p, items.data(), sizeof(FwdItem) * items.size(), cudaMemcpyHostToDevice, c->st),
+           "work items");
+    ck(cudaStreamSynchronize(c->st), "layout");
+    c->layout_dirty = false;
 }
 
-__global__ void reset_convergence_kernel(double *prev, int *frozen, float *phi, int PK, int *col_items)
+__global__ void reset_convergence_kernel(double *prev, int *frozen, float *phi, int T, int *col_items)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) { col_items[0] = 0; col_items[1] = 0; }
-    if (i >= PK) return;
+    if (i >= T) return;
     prev[i] = -1.0;     // no previous cost
     frozen[i] = 0;
     for (int a = 0; a < 8; ++a) phi[(size_t)i * 8 + a] = 0.f;
 }
 
-
-
 // Stream the iteration kernels go to: the capture stream while a graph is being
 // recorded, else the caller's stream.
 cudaStream_t work_stream(const asicp_ctx *c) { return c->capturing ? c->cap_st : c->st; }
+
+void reset_convergence(asicp_ctx *c)
+{
+    reset_convergence_kernel<<<(c->T + 255) / 256, 256, 0, work_stream(c)>>>(
+        c->prev.as<double>(), c->frozen.as<int>(), c->phi.as<float>(), c->T, c->colitems.as<int>());
+    ck(cudaGetLastError(), "reset convergence state");
+}
 
 template <class L>
 void timed(asicp_ctx *c, int kind, L &&launch, const char *what)
@@ -238,27 +354,17 @@ void accumulate_graph_events(asicp_ctx *c)
     c->graph_pending = false;
 }
 
-void reset_convergence(asicp_ctx *c)
-{
-    const int PK = c->PK();
-    reset_convergence_kernel<<<(PK + 255) / 256, 256, 0, work_stream(c)>>>(c->prev.as<double>(), c->frozen.as<int>(),
-                                                                          c->phi.as<float>(), PK,
-                                                                          c->colitems.as<int>());
-    ck(cudaGetLastError(), "reset convergence state");
-}
-
 // One pass of cost/gradient evaluation (+ update for mode 1/2).
 void iterate(asicp_ctx *c, int mode, float gamma)
 {
-    const int PK = c->PK();
+    const Layout L = c->layout();
     FwdArgs fa{};
+    fa.L = L;
     fa.S = c->S.as<float4>();
     fa.theta = c->theta.as<float>();
-    fa.R = c->R.as<float4>();
-    fa.Rx = c->Rx.as<ulonglong2>();
-    fa.rmax = c->rmax.as<float>();
+    fa.items = c->items.as<FwdItem>();
+    fa.n_items = c->n_items;
     fa.err = c->errw.as<int>();
-    fa.M = c->M; fa.Mpad = c->Mpad; fa.N = c->N; fa.K = c->cfg.K; fa.PK = PK;
     fa.nn_idx = c->nnidx.as<int>();
     if (c->cfg.debug) {
         fa.dbg_d2 = c->dbg_d2.as<float>();
@@ -267,15 +373,13 @@ void iterate(asicp_ctx *c, int mode, float gamma)
     timed(c, kTimeMatch, [&](cudaStream_t st) { return launch_fwd_match(fa, st); }, "forward matching kernel");
 
     CollideArgs ca{};
-    ca.C = c->C.p ? c->C.as<float4>() : c->R.as<float4>();
-    ca.Mc = c->Mc; ca.K = c->cfg.K; ca.PK = PK; ca.N = c->N;
+    ca.L = L;
     ca.theta = c->theta.as<float>();
     ca.meta = c->dmeta.as<SdfMeta>();
+    ca.S = c->S.as<float4>();
+    ca.nn_idx = c->nnidx.as<int>();
     ca.ncol = c->ncol.as<int>();
     ca.colidx = c->colidx.as<int>();
-    ca.S = c->S.as<float4>();
-    ca.R = c->R.as<float4>();
-    ca.nn_idx = c->nnidx.as<int>();
     ca.fsums = c->fsums.as<double>();
     ca.csums = c->csums.as<double>();
     ca.col_items = c->colitems.as<int>();
@@ -285,13 +389,12 @@ void iterate(asicp_ctx *c, int mode, float gamma)
     timed(c, kTimeCollideNN, [&](cudaStream_t st) { return launch_collide_nn(ca, st); }, "collision matching kernel");
 
     UpdateArgs ua{};
-    ua.P = c->cfg.P; ua.K = c->cfg.K; ua.N = c->N; ua.Mc = c->Mc;
+    ua.L = L;
     ua.theta = c->theta.as<float>();
     ua.fsums = c->fsums.as<double>();
     ua.csums = c->csums.as<double>();
     ua.ncol = c->ncol.as<int>();
     ua.pconst = c->pconst.as<double>();
-    ua.com = c->com.as<double>();
     ua.w_com = c->cfg.w_com;
     ua.mode = mode;
     ua.gamma = gamma;
@@ -327,17 +430,20 @@ void run_loop(asicp_ctx *c)
     reset_convergence(c);
     for (int k = 0; k < c->cfg.k_max; ++k) step_impl(c, k);
     iterate(c, 0, 0.f);   // final evaluation at the last poses
-    ck(launch_select(c->cost.as<double>(), c->ncol.as<int>(), c->PK(), c->order.as<int>(), work_stream(c)), "select");
+    ck(launch_select(c->layout(), c->cost.as<double>(), c->ncol.as<int>(), c->order.as<int>(), work_stream(c)),
+       "select");
 }
 
-// Buffers and sizes the captured graph depends on.
+// Buffers and sizes the captured graph depends on (the tables they hold are
+// read at replay, so new objects of the same sizes reuse the graph).
 std::vector<const void *> loop_key(const asicp_ctx *c)
 {
-    return {c->colitems.p, c->collist.p, c->S.p, c->R.p, c->Rx.p, c->rmax.p, c->C.p, c->com.p, c->pconst.p, c->dmeta.p, c->theta.p, c->fsums.p,
-            c->csums.p, c->ncol.p, c->colidx.p, c->cost.p, c->grad.p, c->prev.p, c->frozen.p, c->phi.p, c->h.p,
-            c->order.p, c->errw.p, c->nnidx.p, c->dbg_d2.p, c->dbg_sp.p, c->dbg_colnn.p,
-            reinterpret_cast<const void *>((size_t)c->M), reinterpret_cast<const void *>((size_t)c->Mpad),
-            reinterpret_cast<const void *>((size_t)c->Mc), reinterpret_cast<const void *>((size_t)c->N)};
+    return {c->partgrp.p, c->grpoff.p, c->objmeta.p, c->items.p, c->com.p, c->rmax.p, c->colitems.p, c->collist.p,
+            c->S.p, c->pconst.p, c->dmeta.p, c->theta.p, c->fsums.p, c->csums.p, c->ncol.p, c->colidx.p, c->cost.p,
+            c->grad.p, c->prev.p, c->frozen.p, c->phi.p, c->h.p, c->order.p, c->errw.p, c->nnidx.p, c->dbg_d2.p,
+            c->dbg_sp.p, c->dbg_colnn.p, reinterpret_cast<const void *>((size_t)c->T),
+            reinterpret_cast<const void *>((size_t)c->G), reinterpret_cast<const void *>((size_t)c->n_items),
+            reinterpret_cast<const void *>((size_t)c->N)};
 }
 
 // Replay the captured loop on the caller's stream, capturing it first when the
@@ -398,15 +504,47 @@ __global__ void repack_f64_kernel(const double *src8, int n, double *dst7)
     for (int a = 0; a < 7; ++a) dst7[(size_t)i * 7 + a] = src8[(size_t)i * 8 + a];
 }
 
-__global__ void gather_best_kernel(const int *order, int n, int K, const float *theta8, const double *cost,
-                                   float *o7, float *oc, int *oi)
+__global__ void gather_best_kernel(const int *order, int first, int n, const int *part_grp, int P, const float *theta8,
+                                   const double *cost, float *o7, float *oc, int *oi)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    const int i = order[r];
+    const int i = order[first + r];
     for (int a = 0; a < 7; ++a) o7[(size_t)r * 7 + a] = theta8[(size_t)i * 8 + a];
     oc[r] = (float)cost[i];
-    oi[r] = i / K;
+    oi[r] = part_grp[i] % P;
+}
+
+void set_object_impl(asicp_ctx *ctx, int o, const float *R_xyz, int M, const float *C_xyz, int Mc)
+{
+    if (o < 0 || o >= ctx->nobj) fail(ASICP_ERR_INVALID_ARG, "set_object: object index out of range");
+    if (!R_xyz || M < 1) fail(ASICP_ERR_INVALID_ARG, "set_object: R must be non-NULL with M >= 1");
+    if (C_xyz && Mc < 1) fail(ASICP_ERR_INVALID_ARG, "set_object: Mc must be >= 1 when C is given");
+    ObjBufs &b = ctx->objs[o];
+    const int mc = C_xyz ? Mc : M;
+    b.set = false;
+    ctx->run_done = false;
+    ctx->stage.ensure(sizeof(float) * 3 * (size_t)(M > mc ? M : mc), "staging");
+    b.R.ensure(sizeof(float4) * M, "object cloud");
+    ck(cudaMemcpyAsync(ctx->stage.p, R_xyz, sizeof(float) * 3 * (size_t)M, cudaMemcpyDefault, ctx->st), "copy R");
+    ck(launch_pack_points(ctx->stage.as<float>(), M, b.R.as<float4>(), ctx->errw.as<int>(), ctx->st), "pack R");
+    if (C_xyz) {
+        b.C.ensure(sizeof(float4) * mc, "collision cloud");
+        ck(cudaMemcpyAsync(ctx->stage.p, C_xyz, sizeof(float) * 3 * (size_t)mc, cudaMemcpyDefault, ctx->st), "copy C");
+        ck(launch_pack_points(ctx->stage.as<float>(), mc, b.C.as<float4>(), ctx->errw.as<int>(), ctx->st), "pack C");
+    } else {
+        b.C.release();
+    }
+    ck(launch_centroid(b.R.as<float4>(), M, ctx->com.as<double>() + 3 * o, ctx->st), "centroid");
+    const int Mpad = (M + kRefTilePts - 1) / kRefTilePts * kRefTilePts;
+    b.Rx.ensure(sizeof(float4) * (size_t)Mpad, "screening layout");
+    ck(launch_ref_prep(b.R.as<float4>(), M, Mpad, b.Rx.p, ctx->rmax.as<float>() + o, ctx->st), "ref prep");
+    sync_and_check_err(ctx, "set_object");
+    b.M = M;
+    b.Mpad = Mpad;
+    b.Mc = mc;
+    b.set = true;
+    ctx->layout_dirty = true;
 }
 
 }  // namespace
@@ -437,6 +575,7 @@ void asicp_config_default(asicp_config *cfg)
     cfg->debug = 0;
     cfg->profile = 0;
     cfg->cuda_stream = nullptr;
+    cfg->n_objects = 1;
 }
 
 asicp_status asicp_create(const asicp_config *cfg, asicp_ctx **out)
@@ -447,24 +586,27 @@ asicp_status asicp_create(const asicp_config *cfg, asicp_ctx **out)
         cfg->k_stein > cfg->k_max || (cfg->schedule != 0 && cfg->schedule != 1) ||
         (cfg->schedule == 0 && !(cfg->C_cycles > 0.f)) || !(cfg->eta_sgd >= 0.f) ||
         (cfg->bandwidth_mode == 1 && !(cfg->h_fixed > 0.f)) || !std::isfinite(cfg->w_com) ||
-        !(cfg->init_radius >= 0.f))
+        !(cfg->init_radius >= 0.f) || cfg->n_objects < 1 || cfg->n_objects > 4096)
         return ASICP_ERR_INVALID_ARG;
     asicp_ctx *c = new (std::nothrow) asicp_ctx();
     if (!c) return ASICP_ERR_OOM;
     c->cfg = *cfg;
     c->st = static_cast<cudaStream_t>(cfg->cuda_stream);
+    c->nobj = cfg->n_objects;
     c->pre_set.assign(cfg->P, 0);
     c->meta.assign(cfg->P, SdfMeta{});
     c->grids.resize(cfg->P);
+    c->objs.resize(c->nobj);
+    c->Kg.assign((size_t)c->nobj * cfg->P, cfg->K);
     asicp_status s = guarded(c, [&] {
         // one-time kernel attributes, set outside any graph capture
         fwd_grid_size();
         ck(init_collision_attributes(), "collision kernel attributes");
         ck(init_update_attributes(), "update kernel attributes");
-        c->com.ensure(sizeof(double) * 3, "com");
+        c->com.ensure(sizeof(double) * 3 * c->nobj, "com");
+        c->rmax.ensure(sizeof(float) * c->nobj, "rmax");
         c->pconst.ensure(sizeof(double) * 12 * cfg->P, "pconst");
         c->dmeta.ensure(sizeof(SdfMeta) * cfg->P, "sdf meta");
-        c->theta.ensure(sizeof(float) * 8 * (size_t)c->PK(), "theta");
         c->errw.ensure(sizeof(int), "error word");
         ck(cudaMemsetAsync(c->errw.p, 0, sizeof(int), c->st), "clear error word");
         ck(cudaStreamSynchronize(c->st), "create");
@@ -487,38 +629,27 @@ asicp_status asicp_destroy(asicp_ctx *ctx)
 
 asicp_status asicp_set_object(asicp_ctx *ctx, const float *R_xyz, int M, const float *C_xyz, int Mc)
 {
+    return guarded(ctx, [&] { set_object_impl(ctx, 0, R_xyz, M, C_xyz, Mc); });
+}
+
+asicp_status asicp_set_object_at(asicp_ctx *ctx, int object, const float *R_xyz, int M, const float *C_xyz, int Mc)
+{
+    return guarded(ctx, [&] { set_object_impl(ctx, object, R_xyz, M, C_xyz, Mc); });
+}
+
+asicp_status asicp_set_particle_counts(asicp_ctx *ctx, const int *K, int n)
+{
     return guarded(ctx, [&] {
-        if (!R_xyz || M < 1) fail(ASICP_ERR_INVALID_ARG, "set_object: R must be non-NULL with M >= 1");
-        if (C_xyz && Mc < 1) fail(ASICP_ERR_INVALID_ARG, "set_object: Mc must be >= 1 when C is given");
-        const int mc = C_xyz ? Mc : M;
-        ctx->object_set = false;
+        if (!K || n != ctx->nobj * ctx->cfg.P)
+            fail(ASICP_ERR_INVALID_ARG, "set_particle_counts: need n_objects * P counts");
+        std::vector<int> k(n);
+        ck(cudaMemcpy(k.data(), K, sizeof(int) * n, cudaMemcpyDefault), "copy particle counts");
+        for (int v : k)
+            if (v < 1 || v > kMaxK) fail(ASICP_ERR_INVALID_ARG, "set_particle_counts: every count must be in [1, 1024]");
+        ctx->Kg = k;
+        ctx->layout_dirty = true;
+        ctx->theta_set = false;
         ctx->run_done = false;
-        ctx->stage.ensure(sizeof(float) * 3 * (size_t)(M > mc ? M : mc), "staging");
-        ctx->R.ensure(sizeof(float4) * M, "object cloud");
-        ck(cudaMemcpyAsync(ctx->stage.p, R_xyz, sizeof(float) * 3 * (size_t)M, cudaMemcpyDefault, ctx->st), "copy R");
-        ck(launch_pack_points(ctx->stage.as<float>(), M, ctx->R.as<float4>(), ctx->errw.as<int>(), ctx->st), "pack R");
-        if (C_xyz) {
-            ctx->C.ensure(sizeof(float4) * mc, "collision cloud");
-            ck(cudaMemcpyAsync(ctx->stage.p, C_xyz, sizeof(float) * 3 * (size_t)mc, cudaMemcpyDefault, ctx->st),
-               "copy C");
-            ck(launch_pack_points(ctx->stage.as<float>(), mc, ctx->C.as<float4>(), ctx->errw.as<int>(), ctx->st),
-               "pack C");
-        } else if (ctx->C.p) {
-            cudaFree(ctx->C.p);
-            ctx->C.p = nullptr;
-            ctx->C.bytes = 0;
-        }
-        ck(launch_centroid(ctx->R.as<float4>(), M, ctx->com.as<double>(), ctx->st), "centroid");
-        const int Mpad = (M + kRefTilePts - 1) / kRefTilePts * kRefTilePts;
-        ctx->Rx.ensure(sizeof(float4) * (size_t)Mpad, "screening layout");
-        ctx->rmax.ensure(sizeof(float), "rmax");
-        ck(launch_ref_prep(ctx->R.as<float4>(), M, Mpad, ctx->Rx.p, ctx->rmax.as<float>(), ctx->st), "ref prep");
-        sync_and_check_err(ctx, "set_object");
-        ctx->Mpad = Mpad;
-        ctx->M = M;
-        ctx->Mc = mc;
-        ctx->object_set = true;
-        if (ctx->N > 0) ensure_work(ctx);
     });
 }
 
@@ -528,7 +659,7 @@ asicp_status asicp_set_gripper_sdf(asicp_ctx *ctx, int preshape, const float *S_
     return guarded(ctx, [&] {
         if (preshape < 0 || preshape >= ctx->cfg.P) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: preshape out of range");
         if (!S_xyz || !sdf || !origin) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: NULL array");
-        if (N < 1 || N > kMaxN) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: N must be in [1, 8192]");
+        if (N < 1 || N > kMaxN) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: N must be in [1, 6144]");
         if (nx < 2 || ny < 2 || nz < 2) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: every grid dimension must be >= 2");
         if (!(voxel > 0.f) || !std::isfinite(voxel)) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: voxel must be > 0");
         float org[3];
@@ -538,7 +669,10 @@ asicp_status asicp_set_gripper_sdf(asicp_ctx *ctx, int preshape, const float *S_
         bool any_set = false;
         for (char s : ctx->pre_set) any_set = any_set || s;
         if (any_set && N != ctx->N) fail(ASICP_ERR_INVALID_ARG, "set_gripper_sdf: every preshape must have the same N");
-        if (!any_set && N != ctx->N) ctx->N = N;
+        if (N != ctx->N) {
+            ctx->N = N;
+            ctx->layout_dirty = true;
+        }
         ctx->pre_set[preshape] = 0;
         ctx->run_done = false;
         ctx->S.ensure(sizeof(float4) * (size_t)ctx->cfg.P * N, "gripper clouds");
@@ -580,20 +714,19 @@ asicp_status asicp_set_gripper_sdf(asicp_ctx *ctx, int preshape, const float *S_
                            cudaMemcpyHostToDevice, ctx->st), "copy sdf meta");
         ck(cudaStreamSynchronize(ctx->st), "set_gripper_sdf");
         ctx->pre_set[preshape] = 1;
-        if (ctx->object_set) ensure_work(ctx);
     });
 }
 
 asicp_status asicp_set_state(asicp_ctx *ctx, const float *theta, int k)
 {
     return guarded(ctx, [&] {
-        if (!ctx->ready()) fail(ASICP_ERR_STATE, "set_state: object and every preshape must be set first");
+        if (!ctx->inputs_ready()) fail(ASICP_ERR_STATE, "set_state: objects and every preshape must be set first");
         if (!theta || k < 0 || k > ctx->cfg.k_max) fail(ASICP_ERR_INVALID_ARG, "set_state: bad theta or k");
-        ensure_work(ctx);
-        const size_t PK = ctx->PK();
-        ctx->stage.ensure(sizeof(float) * 7 * PK, "staging");
-        ck(cudaMemcpyAsync(ctx->stage.p, theta, sizeof(float) * 7 * PK, cudaMemcpyDefault, ctx->st), "copy theta");
-        ck(launch_set_theta(ctx->stage.as<float>(), (int)PK, ctx->theta.as<float>(), ctx->errw.as<int>(), ctx->st),
+        build_layout(ctx);
+        const size_t T = ctx->T;
+        ctx->stage.ensure(sizeof(float) * 7 * T, "staging");
+        ck(cudaMemcpyAsync(ctx->stage.p, theta, sizeof(float) * 7 * T, cudaMemcpyDefault, ctx->st), "copy theta");
+        ck(launch_set_theta(ctx->stage.as<float>(), (int)T, ctx->theta.as<float>(), ctx->errw.as<int>(), ctx->st),
            "set theta");
         reset_convergence(ctx);
         sync_and_check_err(ctx, "set_state");
@@ -607,7 +740,8 @@ asicp_status asicp_set_state(asicp_ctx *ctx, const float *theta, int k)
 asicp_status asicp_step(asicp_ctx *ctx, int k)
 {
     return guarded(ctx, [&] {
-        if (!ctx->ready() || !ctx->theta_set) fail(ASICP_ERR_STATE, "step: inputs and poses must be set first");
+        if (!ctx->inputs_ready() || !ctx->theta_set) fail(ASICP_ERR_STATE, "step: inputs and poses must be set first");
+        if (ctx->layout_dirty) fail(ASICP_ERR_STATE, "step: inputs changed since the poses were set");
         if (k < 0 || k >= ctx->cfg.k_max) fail(ASICP_ERR_INVALID_ARG, "step: k out of [0, k_max)");
         step_impl(ctx, k);
         ctx->run_done = false;
@@ -617,20 +751,19 @@ asicp_status asicp_step(asicp_ctx *ctx, int k)
 asicp_status asicp_run(asicp_ctx *ctx, const float *theta0)
 {
     return guarded(ctx, [&] {
-        if (!ctx->ready()) fail(ASICP_ERR_STATE, "run: object and every preshape must be set first");
-        ensure_work(ctx);
-        const int PK = ctx->PK();
+        if (!ctx->inputs_ready()) fail(ASICP_ERR_STATE, "run: objects and every preshape must be set first");
+        build_layout(ctx);
+        const int T = ctx->T;
         if (theta0) {
-            ctx->stage.ensure(sizeof(float) * 7 * PK, "staging");
-            ck(cudaMemcpyAsync(ctx->stage.p, theta0, sizeof(float) * 7 * (size_t)PK, cudaMemcpyDefault, ctx->st),
+            ctx->stage.ensure(sizeof(float) * 7 * T, "staging");
+            ck(cudaMemcpyAsync(ctx->stage.p, theta0, sizeof(float) * 7 * (size_t)T, cudaMemcpyDefault, ctx->st),
                "copy theta0");
-            ck(launch_set_theta(ctx->stage.as<float>(), PK, ctx->theta.as<float>(), ctx->errw.as<int>(), ctx->st),
+            ck(launch_set_theta(ctx->stage.as<float>(), T, ctx->theta.as<float>(), ctx->errw.as<int>(), ctx->st),
                "set theta0");
+            sync_and_check_err(ctx, "run");
         } else {
-            ck(launch_fibonacci(ctx->cfg.P, ctx->cfg.K, ctx->com.as<double>(), ctx->cfg.init_radius,
-                                ctx->theta.as<float>(), ctx->st), "fibonacci init");
+            ck(launch_fibonacci(ctx->layout(), ctx->cfg.init_radius, ctx->theta.as<float>(), ctx->st), "fibonacci init");
         }
-        if (theta0) sync_and_check_err(ctx, "run");
         ctx->theta_set = true;
         run_loop_graph(ctx);
         ctx->k_next = ctx->cfg.k_max;
@@ -639,14 +772,18 @@ asicp_status asicp_run(asicp_ctx *ctx, const float *theta0)
     });
 }
 
-asicp_status asicp_best_grasps(asicp_ctx *ctx, int topk, float *theta, float *cost, int *preshape, int *n_out)
+asicp_status asicp_best_grasps_at(asicp_ctx *ctx, int object, int topk, float *theta, float *cost, int *preshape,
+                                  int *n_out)
 {
     return guarded(ctx, [&] {
         if (!ctx->run_done) fail(ASICP_ERR_STATE, "best_grasps: no completed run");
         if (topk < 0) fail(ASICP_ERR_INVALID_ARG, "best_grasps: topk < 0");
-        const int n = topk < ctx->PK() ? topk : ctx->PK();
+        if (object < 0 || object >= ctx->nobj) fail(ASICP_ERR_INVALID_ARG, "best_grasps: object index out of range");
+        const ObjMeta &om = ctx->objmeta_h[object];
+        const int n = topk < om.np ? topk : om.np;
         if (n > 0) {
-            gather_best_kernel<<<(n + 127) / 128, 128, 0, ctx->st>>>(ctx->order.as<int>(), n, ctx->cfg.K,
+            gather_best_kernel<<<(n + 127) / 128, 128, 0, ctx->st>>>(ctx->order.as<int>(), om.pfirst, n,
+                                                                     ctx->partgrp.as<int>(), ctx->cfg.P,
                                                                      ctx->theta.as<float>(), ctx->cost.as<double>(),
                                                                      ctx->out7.as<float>(), ctx->outc.as<float>(),
                                                                      ctx->outi.as<int>());
@@ -660,6 +797,11 @@ asicp_status asicp_best_grasps(asicp_ctx *ctx, int topk, float *theta, float *co
     });
 }
 
+asicp_status asicp_best_grasps(asicp_ctx *ctx, int topk, float *theta, float *cost, int *preshape, int *n_out)
+{
+    return asicp_best_grasps_at(ctx, 0, topk, theta, cost, preshape, n_out);
+}
+
 asicp_status asicp_get_state(asicp_ctx *ctx, const asicp_state_view *v)
 {
     return guarded(ctx, [&] {
@@ -667,41 +809,41 @@ asicp_status asicp_get_state(asicp_ctx *ctx, const asicp_state_view *v)
         if (!ctx->theta_set) fail(ASICP_ERR_STATE, "get_state: no poses yet");
         const bool dbg = v->nn_idx || v->nn_d2 || v->s_prime || v->col_list || v->col_nn;
         if (dbg && !ctx->cfg.debug) fail(ASICP_ERR_STATE, "get_state: debug arrays need config.debug = 1");
-        const int PK = ctx->PK();
+        const int T = ctx->T;
         if (v->theta) {
-            repack_kernel<<<(PK + 127) / 128, 128, 0, ctx->st>>>(ctx->theta.as<float>(), PK, ctx->out7.as<float>());
+            repack_kernel<<<(T + 127) / 128, 128, 0, ctx->st>>>(ctx->theta.as<float>(), T, ctx->out7.as<float>());
             ck(cudaGetLastError(), "repack theta");
-            copy_out(v->theta, ctx->out7.p, sizeof(float) * 7 * PK, ctx->st, "copy theta");
+            copy_out(v->theta, ctx->out7.p, sizeof(float) * 7 * T, ctx->st, "copy theta");
             ck(cudaStreamSynchronize(ctx->st), "get_state");
         }
         if (v->phi) {
-            repack_kernel<<<(PK + 127) / 128, 128, 0, ctx->st>>>(ctx->phi.as<float>(), PK, ctx->out7.as<float>());
+            repack_kernel<<<(T + 127) / 128, 128, 0, ctx->st>>>(ctx->phi.as<float>(), T, ctx->out7.as<float>());
             ck(cudaGetLastError(), "repack phi");
-            copy_out(v->phi, ctx->out7.p, sizeof(float) * 7 * PK, ctx->st, "copy phi");
+            copy_out(v->phi, ctx->out7.p, sizeof(float) * 7 * T, ctx->st, "copy phi");
             ck(cudaStreamSynchronize(ctx->st), "get_state");
         }
         if (v->grad) {
-            ctx->stage.ensure(sizeof(double) * 7 * PK, "staging");
-            repack_f64_kernel<<<(PK + 127) / 128, 128, 0, ctx->st>>>(ctx->grad.as<double>(), PK, ctx->stage.as<double>());
+            ctx->stage.ensure(sizeof(double) * 7 * T, "staging");
+            repack_f64_kernel<<<(T + 127) / 128, 128, 0, ctx->st>>>(ctx->grad.as<double>(), T, ctx->stage.as<double>());
             ck(cudaGetLastError(), "repack grad");
-            copy_out(v->grad, ctx->stage.p, sizeof(double) * 7 * PK, ctx->st, "copy grad");
+            copy_out(v->grad, ctx->stage.p, sizeof(double) * 7 * T, ctx->st, "copy grad");
             ck(cudaStreamSynchronize(ctx->st), "get_state");
         }
         if (ctx->stepped || ctx->run_done) {
-            copy_out(v->cost, ctx->cost.p, sizeof(double) * PK, ctx->st, "copy cost");
-            copy_out(v->ncol, ctx->ncol.p, sizeof(int) * PK, ctx->st, "copy ncol");
-            copy_out(v->h, ctx->h.p, sizeof(float) * ctx->cfg.P, ctx->st, "copy h");
+            copy_out(v->cost, ctx->cost.p, sizeof(double) * T, ctx->st, "copy cost");
+            copy_out(v->ncol, ctx->ncol.p, sizeof(int) * T, ctx->st, "copy ncol");
+            copy_out(v->h, ctx->h.p, sizeof(float) * ctx->G, ctx->st, "copy h");
             if (ctx->cfg.debug) {
-                copy_out(v->nn_idx, ctx->nnidx.p, sizeof(int) * (size_t)PK * ctx->N, ctx->st, "copy nn_idx");
-                copy_out(v->nn_d2, ctx->dbg_d2.p, sizeof(float) * (size_t)PK * ctx->N, ctx->st, "copy nn_d2");
-                copy_out(v->s_prime, ctx->dbg_sp.p, sizeof(float) * 3 * (size_t)PK * ctx->N, ctx->st, "copy s_prime");
-                copy_out(v->col_list, ctx->colidx.p, sizeof(int) * (size_t)PK * ctx->Mc, ctx->st, "copy col_list");
-                copy_out(v->col_nn, ctx->dbg_colnn.p, sizeof(int) * (size_t)PK * ctx->Mc, ctx->st, "copy col_nn");
+                copy_out(v->nn_idx, ctx->nnidx.p, sizeof(int) * (size_t)T * ctx->N, ctx->st, "copy nn_idx");
+                copy_out(v->nn_d2, ctx->dbg_d2.p, sizeof(float) * (size_t)T * ctx->N, ctx->st, "copy nn_d2");
+                copy_out(v->s_prime, ctx->dbg_sp.p, sizeof(float) * 3 * (size_t)T * ctx->N, ctx->st, "copy s_prime");
+                copy_out(v->col_list, ctx->colidx.p, sizeof(int) * (size_t)ctx->colidx_total, ctx->st, "copy col_list");
+                copy_out(v->col_nn, ctx->dbg_colnn.p, sizeof(int) * (size_t)ctx->colidx_total, ctx->st, "copy col_nn");
             }
         } else if (v->cost || v->ncol || v->h || dbg) {
             fail(ASICP_ERR_STATE, "get_state: no step has run since the poses were set");
         }
-        copy_out(v->frozen, ctx->frozen.p, sizeof(int) * PK, ctx->st, "copy frozen");
+        copy_out(v->frozen, ctx->frozen.p, sizeof(int) * T, ctx->st, "copy frozen");
         sync_and_check_err(ctx, "get_state");
     });
 }

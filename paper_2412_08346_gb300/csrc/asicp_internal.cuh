@@ -9,7 +9,7 @@ constexpr int kRefTilePts = 2048;      // object points per shared-memory tile o
 constexpr int kFwdSums = 13;           // per-particle matching sums (see match kernel)
 constexpr int kColSums = 22;           // per-particle collision sums (see collision kernel)
 constexpr int kMaxK = 1024;            // particles per preshape (one update CTA per preshape)
-constexpr int kMaxN = 8192;            // gripper points per preshape (reverse matching in shared memory)
+constexpr int kMaxN = 6144;            // gripper points per preshape (reverse matching keeps 32 B per point in shared memory)
 
 // error word written by device code (host reads it back after synchronising)
 enum : int { kDevOk = 0, kDevNonFinite = 1, kDevTimeout = 2 };
@@ -134,20 +134,50 @@ __device__ __forceinline__ void warp_sum_f64(double (&v)[N])
 
 // ---------------------------------------------------------------- launchers
 // Every launcher enqueues on `st` and returns the launch status.
+// ---------------------------------------------------------------- layout
+// Several objects can be optimised in one pass.  Particles are numbered object
+// by object, preshape by preshape: group g = o * P + p holds the K_g particles
+// grp_off[g] .. grp_off[g + 1] - 1 of preshape p on object o.
+struct ObjMeta {
+    const float4 *R;          // [M] object points
+    const ulonglong2 *Rx;     // [Mpad] screening layout (pairs of (-2r, |r|^2)), Mpad = whole tiles
+    const float4 *C;          // [Mc] collision points (may alias R)
+    int M, Mpad, Mc, chunks;  // chunks = ceil(Mc / kColChunk)
+    int pfirst, np;           // first particle and number of particles of this object
+    long long colidx_base;    // this object's collision lists start here ([np][Mc] ints)
+    long long csum_base;      // this object's chunk sums start here ([np][chunks] slots)
+};
+
+struct Layout {
+    int P, N, G, nobj, T;     // preshapes, gripper points, groups, objects, particles
+    const int *part_grp;      // [T] group of every particle
+    const int *grp_off;       // [G + 1] first particle of every group
+    const ObjMeta *obj;       // [nobj]
+    const double *com;        // [nobj][3] object centroids (CoM)
+    const float *rmax;        // [nobj] max |r| per object (rounded up)
+};
+
+// A unit of forward-matching work: queries [q0, q0 + nq) of the flattened
+// (particle, gripper point) space, all on object `obj` (nq <= 1024).
+struct FwdItem {
+    long long q0;
+    int nq, obj;
+};
+
 struct FwdArgs {
+    Layout L;
     const float4 *S;         // [P][N] gripper points (gripper frame)
-    const float *theta;      // [P*K][8]
-    const float4 *R;         // [M] object points
-    const ulonglong2 *Rx;    // [Mpad] screening layout (pairs of (-2r, |r|^2)), Mpad = whole tiles
-    const float *rmax;       // max |r| (rounded up)
+    const float *theta;      // [T][8]
+    const FwdItem *items;    // [n_items] work items (null: object 0, consecutive 1024-query items)
+    int n_items;
     int *err;                // error word
-    int M, Mpad, N, K, PK;
-    int *nn_idx;             // [PK][N] nearest object point per query
-    float *dbg_d2;           // [PK][N] or null
-    float *dbg_sp;           // [PK][N][3] or null
+    int *nn_idx;             // [T][N] nearest object point per query
+    float *dbg_d2;           // [T][N] or null
+    float *dbg_sp;           // [T][N][3] or null
 };
 cudaError_t launch_fwd_match(const FwdArgs &a, cudaStream_t st);
 int fwd_grid_size();                   // persistent grid; first call sets kernel attributes
+constexpr int kFwdItemQueries = 1024;  // queries per forward-matching work item
 cudaError_t init_collision_attributes();
 cudaError_t init_update_attributes();
 cudaError_t launch_ref_prep(const float4 *R, int M, int Mpad, void *Rx, float *rmax, cudaStream_t st);
@@ -155,44 +185,41 @@ cudaError_t launch_ref_prep(const float4 *R, int M, int Mpad, void *Rx, float *r
 constexpr int kColChunk = 64;          // colliding points per reverse-matching work item
 
 struct CollideArgs {
-    const float4 *C;          // [Mc]
-    int Mc, K, PK, N;
-    const float *theta;       // [PK][8]
+    Layout L;
+    const float *theta;       // [T][8]
     const SdfMeta *meta;      // [P]
-    int *ncol;                // [PK]
-    int *colidx;              // [PK][Mc]
     const float4 *S;          // [P][N]
-    const float4 *R;          // [M] object points
-    const int *nn_idx;        // [PK][N] forward correspondences
-    double *fsums;            // [PK][kFwdSums]
-    double *csums;            // [PK][ceil(Mc / kColChunk)][kColSums]
-    int *dbg_colnn;           // [PK][Mc] or null
+    const int *nn_idx;        // [T][N] forward correspondences
+    int *ncol;                // [T]
+    int *colidx;              // collision lists (see ObjMeta::colidx_base)
+    double *fsums;            // [T][kFwdSums]
+    double *csums;            // chunk sums (see ObjMeta::csum_base) [.][kColSums]
+    int *dbg_colnn;           // like colidx, or null
     int *col_items;           // (count, next) of the reverse-matching work list
-    int *col_list;            // [PK * ceil(Mc / kColChunk)] work items pk * chunks + chunk
+    int *col_list;            // [2 * items] (particle, chunk) pairs
 };
 cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st);
 cudaError_t launch_collide_nn(const CollideArgs &a, cudaStream_t st);
 
 struct UpdateArgs {
-    int P, K, N, Mc;
-    float *theta;             // [PK][8] in/out
-    const double *fsums;      // [PK][kFwdSums]
-    const double *csums;      // [PK][ceil(Mc / kColChunk)][kColSums]
-    const int *ncol;          // [PK]
+    Layout L;
+    float *theta;             // [T][8] in/out
+    const double *fsums;      // [T][kFwdSums]
+    const double *csums;      // chunk sums
+    const int *ncol;          // [T]
     const double *pconst;     // [P][12]: sum s (3), sum s s^T (xx,xy,xz,yy,yz,zz), pad
-    const double *com;        // [3]
     double w_com;
     int mode;                 // 0: evaluate only, 1: SVGD step, 2: SGD step
     float gamma, eta_svgd, eta_sgd;
     int bandwidth_mode;
     float h_fixed;
     float conv_tol;           // < 0 disables
-    double *cost;             // [PK]
-    double *grad;             // [PK][8]
-    double *prev_cost;        // [PK]
-    int *frozen;              // [PK]
-    float *phi;               // [PK][8]
-    float *h;                 // [P]
+    double *cost;             // [T]
+    double *grad;             // [T][8]
+    double *prev_cost;        // [T]
+    int *frozen;              // [T]
+    float *phi;               // [T][8]
+    float *h;                 // [G]
     int *col_items;           // collision work-list counters (count, next), cleared for the next pass
 };
 cudaError_t launch_finalize(const UpdateArgs &a, cudaStream_t st);   // cost/gradient, convergence, SGD step
@@ -202,9 +229,10 @@ cudaError_t launch_pack_points(const float *xyz, int n, float4 *out, int *err, c
 cudaError_t launch_check_finite(const float *v, long long n, int *err, cudaStream_t st);
 cudaError_t launch_centroid(const float4 *X, int n, double *out3, cudaStream_t st);
 cudaError_t launch_preshape_consts(const float4 *S, int N, double *out12, cudaStream_t st);
-cudaError_t launch_fibonacci(int P, int K, const double *com, float radius, float *theta, cudaStream_t st);
-cudaError_t launch_set_theta(const float *theta7, int PK, float *theta8, int *err, cudaStream_t st);
+cudaError_t launch_fibonacci(const Layout &L, float radius, float *theta, cudaStream_t st);
+cudaError_t launch_set_theta(const float *theta7, int T, float *theta8, int *err, cudaStream_t st);
 cudaError_t launch_sdf_box(const float *grid, int nx, int ny, int nz, int *box6, cudaStream_t st);
-cudaError_t launch_select(const double *cost, const int *ncol, int total, int *order, cudaStream_t st);
+cudaError_t launch_select(const Layout &L, const double *cost, const int *ncol, int *order, cudaStream_t st);
+cudaError_t launch_uniform_groups(int *part_grp, int *grp_off, int P, int K, cudaStream_t st);
 
 }  // namespace asicp

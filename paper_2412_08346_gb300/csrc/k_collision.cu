@@ -71,7 +71,10 @@ __global__ void __launch_bounds__(kColThreads) collide_kernel(const CollideArgs 
 {
     __shared__ int swarp[kColThreads / 32];
     __shared__ double sred[kColThreads / 32][kFwdSums];
-    const int pk = blockIdx.x, p = pk / a.K;
+    const int pk = blockIdx.x;
+    const int grp = a.L.part_grp[pk], p = grp % a.L.P;
+    const ObjMeta om = a.L.obj[grp / a.L.P];
+    const int N = a.L.N, Mc = om.Mc;
     const float *th = a.theta + (size_t)pk * 8;
     const float tx = th[0], ty = th[1], tz = th[2];
     float Rm[9];
@@ -81,11 +84,11 @@ __global__ void __launch_bounds__(kColThreads) collide_kernel(const CollideArgs 
         dfloat acc[kFwdSums];
 #pragma unroll
         for (int c = 0; c < kFwdSums; ++c) acc[c] = dfloat{0.f, 0.f};
-        const float4 *S = a.S + (size_t)p * a.N;
-        const int *idx = a.nn_idx + (size_t)pk * a.N;
-        for (int i = threadIdx.x; i < a.N; i += kColThreads) {
+        const float4 *S = a.S + (size_t)p * N;
+        const int *idx = a.nn_idx + (size_t)pk * N;
+        for (int i = threadIdx.x; i < N; i += kColThreads) {
             const float4 s = S[i];
-            const float4 r = __ldg(a.R + idx[i]);
+            const float4 r = __ldg(om.R + idx[i]);
             const float rv[3] = {r.x, r.y, r.z}, sv[3] = {s.x, s.y, s.z};
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
@@ -100,12 +103,13 @@ __global__ void __launch_bounds__(kColThreads) collide_kernel(const CollideArgs 
 
     const SdfMeta m = a.meta[p];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *colidx = a.colidx + om.colidx_base + (long long)(pk - om.pfirst) * Mc;
     int count = 0;
-    for (int c0 = 0; c0 < a.Mc; c0 += kColThreads) {
+    for (int c0 = 0; c0 < Mc; c0 += kColThreads) {
         const int c = c0 + threadIdx.x;
         bool hit = false;
-        if (c < a.Mc) {
-            const float4 v = a.C[c];
+        if (c < Mc) {
+            const float4 v = om.C[c];
             const float dx = __fsub_rn(v.x, tx), dy = __fsub_rn(v.y, ty), dz = __fsub_rn(v.z, tz);
             const float lx = __fmaf_rn(Rm[0], dx, __fmaf_rn(Rm[3], dy, __fmul_rn(Rm[6], dz)));
             const float ly = __fmaf_rn(Rm[1], dx, __fmaf_rn(Rm[4], dy, __fmul_rn(Rm[7], dz)));
@@ -125,95 +129,205 @@ __global__ void __launch_bounds__(kColThreads) collide_kernel(const CollideArgs 
             off += w < warp ? n : 0;
             tot += n;
         }
-        if (hit) a.colidx[(size_t)pk * a.Mc + count + off + __popc(bal & ((1u << lane) - 1u))] = c;
+        if (hit) colidx[count + off + __popc(bal & ((1u << lane) - 1u))] = c;
         count += tot;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         a.ncol[pk] = count;
         // queue this particle's chunks of colliding points for the reverse matching
-        const int chunks = (a.Mc + kColChunk - 1) / kColChunk, used = (count + kColChunk - 1) / kColChunk;
+        const int used = (count + kColChunk - 1) / kColChunk;
         if (used > 0) {
             const int base = atomicAdd(&a.col_items[0], used);
-            for (int c = 0; c < used; ++c) a.col_list[base + c] = pk * chunks + c;
+            for (int c = 0; c < used; ++c) {
+                a.col_list[2 * (base + c)] = pk;
+                a.col_list[2 * (base + c) + 1] = c;
+            }
         }
     }
 }
 
+namespace {
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void upk2(unsigned long long v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// Warp-wide exact nearest point (exact-form float32 distance, ties to the lowest
+// index) of query (x, y, z) among the points ref0 + stride k, k < nk (lanes take
+// k = lane, lane + 32, ...).
+__device__ __forceinline__ void warp_exact_argmin(const float4 *sS, int N, int ref0, int stride, int nk, float x,
+                                                  float y, float z, int lane, float &best, int &bi)
+{
+    best = __int_as_float(0x7f800000);
+    bi = 0x7fffffff;
+    for (int k = lane; k < nk; k += 32) {
+        const int r = ref0 + stride * k;
+        if (r >= N) continue;
+        const float4 s = sS[r];
+        const float d = dist2_f32(s.x, s.y, s.z, x, y, z);
+        if (d < best || (d == best && r < bi)) { best = d; bi = r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob < best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+}
+}  // namespace
+
 // Persistent: CTAs take (particle, chunk of kColChunk colliding points) items
-// from the list the collision kernel filled.  For an item the particle's
-// transformed contact cloud is built in shared memory with the same float32
-// transform as the forward matching; each warp then matches kQW colliding
-// points against it (lanes stride over the contact points, a shuffle reduction
-// picks the smallest distance, ties to the lowest index).  Per item, the sums
-// the collision cost and gradient are linear in (double-float accumulation of
-// exact products):
+// from the list the collision kernel filled.  Per item the particle's
+// transformed contact cloud S' is built in shared memory twice: exact (float4)
+// and in the screening layout (-2 s', |s'|^2), pairs of points interleaved so
+// that lane l owns the chunk of points l + 32 k.  Each warp matches kQW
+// colliding points c:
+//  1. screening: every lane evaluates d~ = |s'|^2 - 2 c.s' over its chunk
+//     (packed f32x2 FMAs, 3-input min); shuffles give the best chunk minimum b1
+//     (lane l1) and the best of the other chunks b2;
+//  2. exact choice: with delta = u (7 Smax^2 + 6.1 |c| Smax) bounding the error of
+//     d~ (Smax = max |s'|), the nearest point lies in chunk l1 unless b2 <= b1 +
+//     2 delta; the warp re-evaluates chunk l1 (or, in that rare case, the whole
+//     cloud) with the exact-form distance, ties to the lowest index.
+// The sums the collision cost and gradient are linear in are accumulated per item
+// (double-float, exact products):
 //   sum s (3), sum s s^T (xx,xy,xz,yy,yz,zz) (6), sum c (3), sum c s^T (9), sum |c|^2 (1)
-// with s the matched gripper point in the gripper frame; the finalize kernel
-// adds the chunks of a particle in chunk order, so the result does not depend
-// on which CTA took which item.
+// with s the matched gripper point in the gripper frame; the finalize kernel adds
+// the chunks of a particle in chunk order, so the result does not depend on
+// which CTA took which item.
 __global__ void __launch_bounds__(kColThreads) collide_nn_kernel(const CollideArgs a)
 {
     constexpr int kQW = kColChunk / (kColThreads / 32);     // colliding points per warp
-    extern __shared__ float4 sSp[];
+    extern __shared__ __align__(16) unsigned char smem_nn[];
+    const int N = a.L.N;
+    const int Npad = (N + 63) / 64 * 64;
+    float4 *sS = reinterpret_cast<float4 *>(smem_nn);                          // [N] exact S'
+    ulonglong2 *sX = reinterpret_cast<ulonglong2 *>(smem_nn + sizeof(float4) * Npad);   // [Npad] screening
     __shared__ double sred[kColThreads / 32][kColSums];
     __shared__ int s_item;
-    const int chunks = (a.Mc + kColChunk - 1) / kColChunk;
+    __shared__ float s_smax[kColThreads / 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slots = Npad / 64;                 // point pairs per lane
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(&a.col_items[1], 1);
         __syncthreads();
         const int item = s_item;
         if (item >= a.col_items[0]) break;
-        const int code = a.col_list[item];
-        const int pk = code / chunks, chunk = code - pk * chunks, p = pk / a.K;
+        const int pk = a.col_list[2 * item], chunk = a.col_list[2 * item + 1];
+        const int grp = a.L.part_grp[pk], p = grp % a.L.P;
+        const ObjMeta om = a.L.obj[grp / a.L.P];
         const int n = a.ncol[pk];
+        const int *colidx = a.colidx + om.colidx_base + (long long)(pk - om.pfirst) * om.Mc;
         const float *th = a.theta + (size_t)pk * 8;
         const float tx = th[0], ty = th[1], tz = th[2];
         float Rm[9];
         quat_rot_f32(th[3], th[4], th[5], th[6], Rm);
-        const float4 *S = a.S + (size_t)p * a.N;
-        for (int i = threadIdx.x; i < a.N; i += kColThreads) {
-            const float4 s = S[i];
-            const float3 o = xform_f32(Rm, tx, ty, tz, s.x, s.y, s.z);
-            sSp[i] = make_float4(o.x, o.y, o.z, 0.f);
+        const float4 *S = a.S + (size_t)p * N;
+        float smax2 = 0.f;
+        // pair (l + 64 m, l + 32 + 64 m) of lane l at screening slot m * 32 + l
+        for (int q = threadIdx.x; q < Npad / 2; q += kColThreads) {
+            const int l = q & 31, m = q >> 5;
+            float ax[2], ay[2], az[2], w[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = l + 32 * h + 64 * m;
+                if (r < N) {
+                    const float4 sv = S[r];
+                    const float3 o = xform_f32(Rm, tx, ty, tz, sv.x, sv.y, sv.z);
+                    sS[r] = make_float4(o.x, o.y, o.z, 0.f);
+                    ax[h] = -2.f * o.x; ay[h] = -2.f * o.y; az[h] = -2.f * o.z;
+                    w[h] = __fmaf_rn(o.x, o.x, __fmaf_rn(o.y, o.y, __fmul_rn(o.z, o.z)));
+                    smax2 = fmaxf(smax2, w[h]);
+                } else {
+                    ax[h] = ay[h] = az[h] = 0.f;
+                    w[h] = __int_as_float(0x7f800000);
+                }
+            }
+            ulonglong2 A, B;
+            A.x = pk2(ax[0], ax[1]); A.y = pk2(ay[0], ay[1]);
+            B.x = pk2(az[0], az[1]); B.y = pk2(w[0], w[1]);
+            sX[2 * q] = A;
+            sX[2 * q + 1] = B;
         }
+        for (int o = 16; o > 0; o >>= 1) smax2 = fmaxf(smax2, __shfl_xor_sync(0xffffffffu, smax2, o));
+        if (lane == 0) s_smax[warp] = smax2;
         __syncthreads();
+        float sm2 = 0.f;
+        for (int w8 = 0; w8 < kColThreads / 32; ++w8) sm2 = fmaxf(sm2, s_smax[w8]);
+        const float smax = sqrtf(sm2) * 1.0001f;
+
         const int l0 = chunk * kColChunk + warp * kQW;
-        float cx[kQW], cy[kQW], cz[kQW], best[kQW];
-        int bi[kQW];
+        float cx[kQW], cy[kQW], cz[kQW], cm[kQW];
+        unsigned long long qx[kQW], qy[kQW], qz[kQW];
 #pragma unroll
         for (int q = 0; q < kQW; ++q) {
             float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (l0 + q < n) c = a.C[a.colidx[(size_t)pk * a.Mc + l0 + q]];
+            if (l0 + q < n) c = om.C[colidx[l0 + q]];
             cx[q] = c.x; cy[q] = c.y; cz[q] = c.z;
-            best[q] = __int_as_float(0x7f800000);
-            bi[q] = 0;
+            qx[q] = pk2(c.x, c.x); qy[q] = pk2(c.y, c.y); qz[q] = pk2(c.z, c.z);
+            cm[q] = __int_as_float(0x7f800000);
         }
-        for (int i = lane; i < a.N; i += 32) {
-            const float4 s = sSp[i];
+        for (int m = 0; m < slots; ++m) {
+            const ulonglong2 A = sX[2 * (m * 32 + lane)];
+            const ulonglong2 B = sX[2 * (m * 32 + lane) + 1];
 #pragma unroll
             for (int q = 0; q < kQW; ++q) {
-                const float d = dist2_f32(s.x, s.y, s.z, cx[q], cy[q], cz[q]);
-                if (d < best[q]) { best[q] = d; bi[q] = i; }
+                const unsigned long long d = ffma2(qx[q], A.x, ffma2(qy[q], A.y, ffma2(qz[q], B.x, B.y)));
+                float d0, d1;
+                upk2(d, d0, d1);
+                cm[q] = fmin3(cm[q], d0, d1);
             }
         }
-#pragma unroll
-        for (int q = 0; q < kQW; ++q)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best[q], o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi[q], o);
-                if (ob < best[q] || (ob == best[q] && oi < bi[q])) { best[q] = ob; bi[q] = oi; }
-            }
         dfloat acc[kColSums];
 #pragma unroll
         for (int c = 0; c < kColSums; ++c) acc[c] = dfloat{0.f, 0.f};
 #pragma unroll
         for (int q = 0; q < kQW; ++q) {
+            // best chunk (ties to the lower lane) and the best of the other chunks
+            float b1 = cm[q];
+            int l1 = lane;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, b1, o);
+                const int ol = __shfl_xor_sync(0xffffffffu, l1, o);
+                if (ob < b1 || (ob == b1 && ol < l1)) { b1 = ob; l1 = ol; }
+            }
+            float b2 = lane == l1 ? __int_as_float(0x7f800000) : cm[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) b2 = fminf(b2, __shfl_xor_sync(0xffffffffu, b2, o));
+            const float cn = sqrtf(cx[q] * cx[q] + cy[q] * cy[q] + cz[q] * cz[q]) * 1.001f;
+            const float win = 2.02f * 5.9604645e-8f * (7.f * smax * smax + 6.1f * cn * smax);
+            float best;
+            int bi;
+            if (b2 <= b1 + win)      // another chunk may hold the nearest point: whole cloud
+                warp_exact_argmin(sS, N, 0, 1, N, cx[q], cy[q], cz[q], lane, best, bi);
+            else                     // chunk l1: points l1 + 32 k
+                warp_exact_argmin(sS, N, l1, 32, Npad / 32, cx[q], cy[q], cz[q], lane, best, bi);
             if (lane != q || l0 + q >= n) continue;       // lane q records colliding point q
-            if (a.dbg_colnn) a.dbg_colnn[(size_t)pk * a.Mc + l0 + q] = bi[q];
-            const float4 s = S[bi[q]];
+            if (a.dbg_colnn) a.dbg_colnn[om.colidx_base + (long long)(pk - om.pfirst) * om.Mc + l0 + q] = bi;
+            const float4 s = S[bi];
             const float sv[3] = {s.x, s.y, s.z}, cv[3] = {cx[q], cy[q], cz[q]};
             acc[0] = dfloat{sv[0], 0.f}; acc[1] = dfloat{sv[1], 0.f}; acc[2] = dfloat{sv[2], 0.f};
             df_add_prod(acc[3], sv[0], sv[0]); df_add_prod(acc[4], sv[0], sv[1]); df_add_prod(acc[5], sv[0], sv[2]);
@@ -225,21 +339,22 @@ __global__ void __launch_bounds__(kColThreads) collide_nn_kernel(const CollideAr
                 for (int v = 0; v < 3; ++v) df_add_prod(acc[12 + 3 * u + v], cv[u], sv[v]);
             df_add_prod(acc[21], cv[0], cv[0]); df_add_prod(acc[21], cv[1], cv[1]); df_add_prod(acc[21], cv[2], cv[2]);
         }
-        block_reduce_store<kColSums>(acc, sred, a.csums + ((size_t)pk * chunks + chunk) * kColSums);
-        __syncthreads();   // sSp, sred and s_item are reused by the next item
+        block_reduce_store<kColSums>(
+            acc, sred, a.csums + (om.csum_base + (long long)(pk - om.pfirst) * om.chunks + chunk) * kColSums);
+        __syncthreads();   // shared buffers and s_item are reused by the next item
     }
 }
 
 cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st)
 {
-    collide_kernel<<<a.PK, kColThreads, 0, st>>>(a);
+    collide_kernel<<<a.L.T, kColThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t init_collision_attributes()
 {
     return cudaFuncSetAttribute(collide_nn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(float4) * kMaxN));
+                                (int)(2 * sizeof(float4) * kMaxN));
 }
 
 cudaError_t launch_collide_nn(const CollideArgs &a, cudaStream_t st)
@@ -251,7 +366,7 @@ cudaError_t launch_collide_nn(const CollideArgs &a, cudaStream_t st)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         grid = 4 * sms;
     }
-    const size_t smem = sizeof(float4) * (size_t)a.N;
+    const size_t smem = 2 * sizeof(float4) * (size_t)((a.L.N + 63) / 64 * 64);
     collide_nn_kernel<<<grid, kColThreads, smem, st>>>(a);
     return cudaGetLastError();
 }

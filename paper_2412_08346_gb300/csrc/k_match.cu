@@ -128,18 +128,24 @@ __device__ __forceinline__ void exact_scan(const float4 *__restrict__ R, int lo,
 
 }  // namespace
 
-// One screening + exact pass over the whole object cloud for the queries
-// [q0, q0 + nq) of the flattened (particle, gripper point) space, nq <= kThreads * Q.
-// Object tiles stream through the two shared buffers; `seq` counts tiles
-// consumed by this CTA across passes and `total` is the number it will consume,
-// so the next pass's first tiles are prefetched while this one finishes.
+// One screening + exact pass of the queries [q0, q0 + nq) (nq <= kThreads * Q,
+// all on one object) over that object's whole cloud.  Object tiles stream
+// through the two shared buffers; `seq` counts the tiles this CTA has consumed,
+// which gives each buffer's mbarrier phase.
 template <int Q>
-__device__ __forceinline__ bool match_pass(const FwdArgs &a, long long q0, int nq, ulonglong2 *tiles,
-                                           unsigned long long *full, int &seq, int total, int *s_abort)
+__device__ __forceinline__ bool match_pass(const FwdArgs &a, const ObjMeta &om, float rmax, long long q0, int nq,
+                                           ulonglong2 *tiles, unsigned long long *full, int &seq, int *s_abort)
 {
-    const int ntiles = a.Mpad / kTile;
+    const int ntiles = om.Mpad / kTile;
     const unsigned tile_bytes = kTile * 16u;
-    const float rmax = *a.rmax;
+    if (threadIdx.x == 0) {    // both buffers are free: the previous pass ended with a barrier
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int t = 0; t < 2 && t < ntiles; ++t) {
+            const int b = (seq + t) & 1;
+            mbar_arrive_tx(&full[b], tile_bytes);
+            bulk_load(tiles + (size_t)b * kTile, om.Rx + (size_t)t * kTile, tile_bytes, &full[b]);
+        }
+    }
     float sx[Q], sy[Q], sz[Q], win[Q], cm[Q], b1[Q], b2[Q], b3[Q];
     int c1[Q], c2[Q];
     unsigned long long qx[Q], qy[Q], qz[Q];
@@ -149,11 +155,12 @@ __device__ __forceinline__ bool match_pass(const FwdArgs &a, long long q0, int n
         float3 o = make_float3(0.f, 0.f, 0.f);
         if (li < nq) {
             const long long g = q0 + li;
-            const int pk = (int)(g / a.N), i = (int)(g - (long long)pk * a.N);
+            const int pk = (int)(g / a.L.N), i = (int)(g - (long long)pk * a.L.N);
+            const int pre = a.L.part_grp[pk] % a.L.P;
             const float *th = a.theta + (size_t)pk * 8;
             float Rm[9];
             quat_rot_f32(th[3], th[4], th[5], th[6], Rm);
-            const float4 s = a.S[(size_t)(pk / a.K) * a.N + i];
+            const float4 s = a.S[(size_t)pre * a.L.N + i];
             o = xform_f32(Rm, th[0], th[1], th[2], s.x, s.y, s.z);
         }
         sx[q] = o.x; sy[q] = o.y; sz[q] = o.z;
@@ -200,11 +207,10 @@ __device__ __forceinline__ bool match_pass(const FwdArgs &a, long long q0, int n
             }
         }
         __syncthreads();   // every thread is done with this buffer
-        if (threadIdx.x == 0 && seq + 2 < total) {
+        if (threadIdx.x == 0 && t + 2 < ntiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            const int nt = (seq + 2) % ntiles;
             mbar_arrive_tx(&full[buf], tile_bytes);
-            bulk_load(tiles + (size_t)buf * kTile, a.Rx + (size_t)nt * kTile, tile_bytes, &full[buf]);
+            bulk_load(tiles + (size_t)buf * kTile, om.Rx + (size_t)(t + 2) * kTile, tile_bytes, &full[buf]);
         }
     }
 
@@ -217,13 +223,13 @@ __device__ __forceinline__ bool match_pass(const FwdArgs &a, long long q0, int n
         float best = __int_as_float(0x7f800000);
         int bi = 0;
         if (b3[q] <= thr) {
-            exact_scan(a.R, 0, a.M, sx[q], sy[q], sz[q], best, bi);
+            exact_scan(om.R, 0, om.M, sx[q], sy[q], sz[q], best, bi);
         } else {
             int ca = c1[q], cb = c2[q];
             const bool two = b2[q] <= thr && cb != ca;
             if (two && cb < ca) { const int x = ca; ca = cb; cb = x; }
-            exact_scan(a.R, ca * kChunk, min((ca + 1) * kChunk, a.M), sx[q], sy[q], sz[q], best, bi);
-            if (two) exact_scan(a.R, cb * kChunk, min((cb + 1) * kChunk, a.M), sx[q], sy[q], sz[q], best, bi);
+            exact_scan(om.R, ca * kChunk, min((ca + 1) * kChunk, om.M), sx[q], sy[q], sz[q], best, bi);
+            if (two) exact_scan(om.R, cb * kChunk, min((cb + 1) * kChunk, om.M), sx[q], sy[q], sz[q], best, bi);
         }
         a.nn_idx[g] = bi;
         if (a.dbg_d2) a.dbg_d2[g] = best;
@@ -236,28 +242,17 @@ __device__ __forceinline__ bool match_pass(const FwdArgs &a, long long q0, int n
     return true;
 }
 
-// Persistent: CTA b owns an equal contiguous slice of the P*K*N queries and
-// walks it in passes of kThreads * QPT queries; the last, partial pass uses the
-// smallest queries-per-thread instantiation that covers it, so every CTA
-// carries the same work whatever the particle count.
+// Persistent: CTA b takes work items b, b + gridDim.x, ... (listed longest
+// first when objects differ, so the tail is short); an item is at most
+// kThreads * QPT queries of one object, and a partial item uses the smallest
+// queries-per-thread instantiation that covers it.
 __global__ void __launch_bounds__(kThreads, 3) fwd_match_kernel(const FwdArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     ulonglong2 *tiles = reinterpret_cast<ulonglong2 *>(smem_raw);
     __shared__ __align__(8) unsigned long long full[2];
     __shared__ int s_abort;
-
-    const long long Qtot = (long long)a.PK * a.N;
-    const long long per = (Qtot + gridDim.x - 1) / gridDim.x;
-    const long long lo = (long long)blockIdx.x * per;
-    const long long hi = lo + per < Qtot ? lo + per : Qtot;
-    if (lo >= hi) return;
-    constexpr int kQB = kThreads * QPT;
-    const int npass = (int)((hi - lo + kQB - 1) / kQB);
-    const int ntiles = a.Mpad / kTile;
-    const int total = npass * ntiles;
-    const unsigned tile_bytes = kTile * 16u;
-
+    if (blockIdx.x >= a.n_items) return;
     if (threadIdx.x == 0) {
         s_abort = 0;
         mbar_init(&full[0], 1);
@@ -265,30 +260,33 @@ __global__ void __launch_bounds__(kThreads, 3) fwd_match_kernel(const FwdArgs a)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (threadIdx.x == 0)
-        for (int sq = 0; sq < 2 && sq < total; ++sq) {
-            mbar_arrive_tx(&full[sq], tile_bytes);
-            bulk_load(tiles + (size_t)sq * kTile, a.Rx + (size_t)(sq % ntiles) * kTile, tile_bytes, &full[sq]);
-        }
-
+    const long long Qtot = (long long)a.L.T * a.L.N;
     int seq = 0;
     bool ok = true;
-    for (int ps = 0; ps < npass && ok; ++ps) {
-        const long long q0 = lo + (long long)ps * kQB;
-        const int nq = (int)(hi - q0 < kQB ? hi - q0 : kQB);
-        switch ((nq + kThreads - 1) / kThreads) {
-            case 1: ok = match_pass<1>(a, q0, nq, tiles, full, seq, total, &s_abort); break;
-            case 2: ok = match_pass<2>(a, q0, nq, tiles, full, seq, total, &s_abort); break;
-            case 3: ok = match_pass<3>(a, q0, nq, tiles, full, seq, total, &s_abort); break;
-            case 4: ok = match_pass<4>(a, q0, nq, tiles, full, seq, total, &s_abort); break;
-            case 5: ok = match_pass<5>(a, q0, nq, tiles, full, seq, total, &s_abort); break;
-            case 6: ok = match_pass<6>(a, q0, nq, tiles, full, seq, total, &s_abort); break;
-            case 7: ok = match_pass<7>(a, q0, nq, tiles, full, seq, total, &s_abort); break;
-            default: ok = match_pass<8>(a, q0, nq, tiles, full, seq, total, &s_abort); break;
+    for (int it = blockIdx.x; it < a.n_items && ok; it += gridDim.x) {
+        FwdItem item;
+        if (a.items) {
+            item = a.items[it];
+        } else {
+            item.q0 = (long long)it * kFwdItemQueries;
+            item.nq = (int)(Qtot - item.q0 < kFwdItemQueries ? Qtot - item.q0 : kFwdItemQueries);
+            item.obj = 0;
+        }
+        const ObjMeta om = a.L.obj[item.obj];
+        const float rmax = a.L.rmax[item.obj];
+        switch ((item.nq + kThreads - 1) / kThreads) {
+            case 1: ok = match_pass<1>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+            case 2: ok = match_pass<2>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+            case 3: ok = match_pass<3>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+            case 4: ok = match_pass<4>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+            case 5: ok = match_pass<5>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+            case 6: ok = match_pass<6>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+            case 7: ok = match_pass<7>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+            default: ok = match_pass<8>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
         }
     }
     if (!ok && threadIdx.x == 0)   // drain copies still in flight (bounded) before leaving
-        for (int b = 0; b < 2; ++b) mbar_wait(&full[b], (unsigned)((seq + b) >> 1) & 1u);
+        for (int b = 0; b < 2; ++b) mbar_wait(&full[(seq + b) & 1], (unsigned)((seq + b) >> 1) & 1u);
 }
 
 int fwd_grid_size()
@@ -307,6 +305,7 @@ int fwd_grid_size()
 
 cudaError_t launch_fwd_match(const FwdArgs &a, cudaStream_t st)
 {
+    static_assert(kFwdItemQueries == kThreads * QPT, "work items hold kThreads * QPT queries");
     const size_t smem = 2 * (size_t)kTile * 16;
     const int grid = fwd_grid_size();
     fwd_match_kernel<<<grid, kThreads, smem, st>>>(a);

@@ -78,11 +78,11 @@ constexpr int kFinalizeThreads = 32;
 
 __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(const UpdateArgs a)
 {
-    const int PK = a.P * a.K;
     const int pk = blockIdx.x * blockDim.x + threadIdx.x;
     if (pk == 0 && a.col_items) { a.col_items[0] = 0; a.col_items[1] = 0; }
-    if (pk >= PK) return;
-    const int p = pk / a.K;
+    if (pk >= a.L.T) return;
+    const int grp = a.L.part_grp[pk], p = grp % a.L.P, o = grp / a.L.P;
+    const int N = a.L.N;
     double t[3], q[4], g[7];
     const float *th = a.theta + (size_t)pk * 8;
     for (int c = 0; c < 3; ++c) t[c] = th[c];
@@ -97,25 +97,28 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(const Update
         const double *pc = a.pconst + (size_t)p * 12;
         double SS[9];
         sym_full(pc + 3, SS);
-        residual_moments(R, t, (double)a.N, pc, SS, fs, fs + 3, fs[12], &se2, Se, E);
+        residual_moments(R, t, (double)N, pc, SS, fs, fs + 3, fs[12], &se2, Se, E);
         // TCP-CoM term (Eq. 15) inside the 1/N, weight w_com (Eqs. 16-17)
-        const double tcp[3] = {pc[0] / a.N, pc[1] / a.N, pc[2] / a.N};
+        const double tcp[3] = {pc[0] / N, pc[1] / N, pc[2] / N};
+        const double *com = a.L.com + 3 * o;
         double ec[3];
         for (int u = 0; u < 3; ++u)
-            ec[u] = R[u * 3 + 0] * tcp[0] + R[u * 3 + 1] * tcp[1] + R[u * 3 + 2] * tcp[2] + t[u] - a.com[u];
+            ec[u] = R[u * 3 + 0] * tcp[0] + R[u * 3 + 1] * tcp[1] + R[u * 3 + 2] * tcp[2] + t[u] - com[u];
         se2 += a.w_com * (ec[0] * ec[0] + ec[1] * ec[1] + ec[2] * ec[2]);
         for (int u = 0; u < 3; ++u) {
             Se[u] += a.w_com * ec[u];
             for (int v = 0; v < 3; ++v) E[u * 3 + v] += a.w_com * ec[u] * tcp[v];
         }
-        cnt = (double)a.N;
+        cnt = (double)N;
     } else {
         // add the per-chunk collision sums in chunk order
-        const int nchunks = (a.Mc + kColChunk - 1) / kColChunk, used = (nc + kColChunk - 1) / kColChunk;
+        const ObjMeta &om = a.L.obj[o];
+        const int used = (nc + kColChunk - 1) / kColChunk;
+        const double *csp = a.csums + (om.csum_base + (long long)(pk - om.pfirst) * om.chunks) * kColSums;
         double cs[kColSums];
         for (int c = 0; c < kColSums; ++c) cs[c] = 0.0;
         for (int b = 0; b < used; ++b)
-            for (int c = 0; c < kColSums; ++c) cs[c] += a.csums[((size_t)pk * nchunks + b) * kColSums + c];
+            for (int c = 0; c < kColSums; ++c) cs[c] += csp[(size_t)b * kColSums + c];
         double SS[9];
         sym_full(cs + 3, SS);
         residual_moments(R, t, (double)nc, cs, SS, cs + 9, cs + 12, cs[21], &se2, Se, E);
@@ -142,7 +145,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(const Update
     if (a.mode == 2) {
         float *tw = a.theta + (size_t)pk * 8;
         for (int u = 0; u < 7; ++u) a.phi[(size_t)pk * 8 + u] = 0.f;
-        if (pk < a.P) a.h[pk] = 0.f;
+        if (pk < a.L.G) a.h[pk] = 0.f;
         if (!frozen) {
             double nq[4];
             for (int u = 0; u < 4; ++u) nq[u] = q[u] - (double)a.eta_sgd * g[3 + u];
@@ -153,27 +156,43 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(const Update
     }
 }
 
-// SVGD phase, one CTA per preshape, one thread per particle: median-heuristic
-// bandwidth (exact radix select of the lower median of |t_i - t_j|^2, i < j),
-// Stein direction of Eq. 8 read as the mean of Eq. 6 with the kernels of
-// Eqs. 9-10 per block, and the update of Eq. 7.
-__global__ void __launch_bounds__(kMaxK) stein_kernel(const UpdateArgs a)
+// SVGD phase, one CTA of kSteinThreads per preshape; each particle i is served
+// by T = kSteinThreads / K' threads (K' = K rounded up to a power of two), so a
+// preshape of 256 particles still fills 32 warps:
+//  - bandwidth: exact lower median of |t_i - t_j|^2 (i < j) by 4 passes of 8-bit
+//    radix selection on the float bit patterns; every unordered pair is visited
+//    once (thread (i, sub) takes partners i + o (mod K), o = 1 + sub + T m <= K/2,
+//    the o = K/2 pairs only from i < K/2 when K is even); lanes that land in one
+//    bin add with one aggregated shared-memory atomic;
+//  - Stein direction of Eq. 8 read as the mean of Eq. 6 with the kernels of
+//    Eqs. 9-10 per block: thread (i, sub) sums over j = sub, sub + T, ..., the T
+//    partial sums of particle i (adjacent lanes) are added by shuffles;
+//  - the update of Eq. 7.
+constexpr int kSteinThreads = 1024;
+
+__global__ void __launch_bounds__(kSteinThreads) stein_kernel(const UpdateArgs a)
 {
     extern __shared__ float4 sm[];
     float4 *sT = sm;                  // [K] t (xyz)
-    float4 *sQ = sm + a.K;            // [K] q (wxyz)
-    float4 *sDt = sm + 2 * a.K;       // [K] -gamma N g_t
-    float4 *sDq = sm + 3 * a.K;       // [K] -gamma N g_q
+    float4 *sQ = sm + kMaxK;          // [K] q (wxyz)
+    float4 *sDt = sm + 2 * kMaxK;     // [K] -gamma N g_t
+    float4 *sDq = sm + 3 * kMaxK;     // [K] -gamma N g_q
     __shared__ unsigned hist[256];
+    __shared__ unsigned whist[kSteinThreads / 32][256];   // per-warp histograms: no cross-warp atomics
     __shared__ unsigned s_prefix, s_mask, s_rank;
 
-    const int p = blockIdx.x, j = threadIdx.x, K = a.K;
-    const bool active = j < K;
-    const size_t pk = (size_t)p * K + j;
-    const float gN = -a.gamma * (float)a.N;
-    if (active) {
-        const float *th = a.theta + pk * 8;
-        const double *g = a.grad + pk * 8;
+    const int grp = blockIdx.x, base = a.L.grp_off[grp], K = a.L.grp_off[grp + 1] - base;
+    if (K <= 0) return;
+    int Kp = 1;
+    while (Kp < K) Kp <<= 1;
+    const int T = min(kSteinThreads / Kp, 32);        // threads per particle: a power of two <= a warp
+    const int i = threadIdx.x / T, sub = threadIdx.x % T;
+    const bool active = i < K;
+    const float gN = -a.gamma * (float)a.L.N;
+    for (int j = threadIdx.x; j < K; j += blockDim.x) {
+        const size_t pj = (size_t)base + j;
+        const float *th = a.theta + pj * 8;
+        const double *g = a.grad + pj * 8;
         sT[j] = make_float4(th[0], th[1], th[2], 0.f);
         sQ[j] = make_float4(th[3], th[4], th[5], th[6]);
         sDt[j] = make_float4(gN * (float)g[0], gN * (float)g[1], gN * (float)g[2], 0.f);
@@ -187,35 +206,40 @@ __global__ void __launch_bounds__(kMaxK) stein_kernel(const UpdateArgs a)
     } else if (K < 2) {
         h = 1.f;
     } else {
-        // exact lower median of the K(K-1)/2 squared distances by 4 passes of
-        // 8-bit radix selection on their (non-negative) float bit patterns
-        if (j == 0) {
+        if (threadIdx.x == 0) {
             const unsigned long long L = (unsigned long long)K * (K - 1) / 2;
             s_rank = (unsigned)((L - 1) / 2);
             s_prefix = 0u;
             s_mask = 0u;
         }
+        const int half = K / 2;
+        const int trips = (half + T - 1) / T;
+        const int lane = threadIdx.x & 31;
+        const int warp = threadIdx.x >> 5;
         for (int shift = 24; shift >= 0; shift -= 8) {
-            for (int b = j; b < 256; b += blockDim.x) hist[b] = 0u;
+            for (int b = threadIdx.x; b < (kSteinThreads / 32) * 256; b += blockDim.x) (&whist[0][0])[b] = 0u;
             __syncthreads();
             const unsigned prefix = s_prefix, mask = s_mask;
-            // every unordered pair once with the same trip count in every thread: thread j
-            // takes partners j + o (mod K), o = 1 .. K/2, the o = K/2 pairs only from j < K/2
-            // when K is even; lanes that land in one bin add with one aggregated atomic
-            const float4 ti = sT[active ? j : 0];
-            const int lane = j & 31;
-            for (int o = 1; o <= K / 2; ++o) {
-                int jj = j + o;
+            const float4 ti = sT[active ? i : 0];
+            for (int m = 0; m < trips; ++m) {
+                const int o = 1 + sub + T * m;
+                int jj = i + o;
                 jj -= jj >= K ? K : 0;
-                const bool valid = active && !((K & 1) == 0 && o == K / 2 && j >= K / 2);
+                const bool valid = active && o <= half && !((K & 1) == 0 && o == half && i >= half);
                 const unsigned bits = __float_as_uint(pair_d2(ti, sT[valid ? jj : 0]));
                 const bool take = valid && (bits & mask) == prefix;
                 const unsigned key = take ? ((bits >> shift) & 255u) : 256u + lane;
                 const unsigned peers = __match_any_sync(0xffffffffu, key);
-                if (take && lane == __ffs(peers) - 1) atomicAdd(&hist[key], (unsigned)__popc(peers));
+                if (take && lane == __ffs(peers) - 1) atomicAdd(&whist[warp][key], (unsigned)__popc(peers));
             }
             __syncthreads();
-            if (j == 0) {
+            for (int b = threadIdx.x; b < 256; b += blockDim.x) {
+                unsigned c = 0u;
+                for (int w = 0; w < kSteinThreads / 32; ++w) c += whist[w][b];
+                hist[b] = c;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
                 unsigned rank = s_rank, cum = 0u;
                 int b = 0;
                 for (; b < 255; ++b) {
@@ -232,38 +256,45 @@ __global__ void __launch_bounds__(kMaxK) stein_kernel(const UpdateArgs a)
         h = (float)(med / log((double)K));
         h = fmaxf(h, 1e-12f);
     }
-    if (j == 0) a.h[p] = h;
+    if (threadIdx.x == 0) a.h[grp] = h;
 
+    const float4 ti = sT[active ? i : 0], qi = sQ[active ? i : 0];
+    const float inv_h = 1.f / h, two_h = 2.f / h;
+    float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};     // t (3), q (4), sign count
     if (active) {
-        const float4 ti = sT[j], qi = sQ[j];
-        const float inv_h = 1.f / h, two_h = 2.f / h;
-        float ft0 = 0.f, ft1 = 0.f, ft2 = 0.f, fq0 = 0.f, fq1 = 0.f, fq2 = 0.f, fq3 = 0.f, sgn = 0.f;
-        for (int jj = 0; jj < K; ++jj) {
+        for (int jj = sub; jj < K; jj += T) {
             const float4 tj = sT[jj], qj = sQ[jj], dt = sDt[jj], dq = sDq[jj];
             const float ex = ti.x - tj.x, ey = ti.y - tj.y, ez = ti.z - tj.z;
             const float kt = expf(-(ex * ex + ey * ey + ez * ez) * inv_h);
-            ft0 += kt * (dt.x + two_h * ex);
-            ft1 += kt * (dt.y + two_h * ey);
-            ft2 += kt * (dt.z + two_h * ez);
+            f[0] += kt * (dt.x + two_h * ex);
+            f[1] += kt * (dt.y + two_h * ey);
+            f[2] += kt * (dt.z + two_h * ez);
             const float c = qj.x * qi.x + qj.y * qi.y + qj.z * qi.z + qj.w * qi.w;
-            fq0 += c * dq.x; fq1 += c * dq.y; fq2 += c * dq.z; fq3 += c * dq.w;
-            sgn += c < 0.f ? -1.f : 1.f;
+            f[3] += c * dq.x; f[4] += c * dq.y; f[5] += c * dq.z; f[6] += c * dq.w;
+            f[7] += c < 0.f ? -1.f : 1.f;
         }
+    }
+    // the T threads of a particle are adjacent lanes of one warp (T is a power of two <= 32)
+    for (int o = 1; o < T; o <<= 1)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) f[u] += __shfl_xor_sync(0xffffffffu, f[u], o);
+    if (active && sub == 0) {
+        const size_t pk = (size_t)base + i;
         const float invK = 1.f / (float)K;
-        float f[7] = {ft0 * invK, ft1 * invK, ft2 * invK,
-                      (fq0 + sgn * qi.x) * invK, (fq1 + sgn * qi.y) * invK,
-                      (fq2 + sgn * qi.z) * invK, (fq3 + sgn * qi.w) * invK};
+        float g[7] = {f[0] * invK, f[1] * invK, f[2] * invK,
+                      (f[3] + f[7] * qi.x) * invK, (f[4] + f[7] * qi.y) * invK,
+                      (f[5] + f[7] * qi.z) * invK, (f[6] + f[7] * qi.w) * invK};
         // tangent projection at q_i (removes the radial kernel-gradient term)
-        const float d = f[3] * qi.x + f[4] * qi.y + f[5] * qi.z + f[6] * qi.w;
-        f[3] -= d * qi.x; f[4] -= d * qi.y; f[5] -= d * qi.z; f[6] -= d * qi.w;
+        const float d = g[3] * qi.x + g[4] * qi.y + g[5] * qi.z + g[6] * qi.w;
+        g[3] -= d * qi.x; g[4] -= d * qi.y; g[5] -= d * qi.z; g[6] -= d * qi.w;
         float *th = a.theta + pk * 8;
-        for (int u = 0; u < 7; ++u) a.phi[pk * 8 + u] = f[u];
+        for (int u = 0; u < 7; ++u) a.phi[pk * 8 + u] = g[u];
         const double es = a.eta_svgd;
-        double nq[4] = {qi.x + es * f[3], qi.y + es * f[4], qi.z + es * f[5], qi.w + es * f[6]};
+        double nq[4] = {qi.x + es * g[3], qi.y + es * g[4], qi.z + es * g[5], qi.w + es * g[6]};
         const double nn = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
-        th[0] = (float)(ti.x + es * f[0]);
-        th[1] = (float)(ti.y + es * f[1]);
-        th[2] = (float)(ti.z + es * f[2]);
+        th[0] = (float)(ti.x + es * g[0]);
+        th[1] = (float)(ti.y + es * g[1]);
+        th[2] = (float)(ti.z + es * g[2]);
         for (int u = 0; u < 4; ++u) th[3 + u] = (float)(nq[u] / nn);
     }
 }
@@ -276,16 +307,14 @@ cudaError_t init_update_attributes()
 
 cudaError_t launch_finalize(const UpdateArgs &a, cudaStream_t st)
 {
-    const int PK = a.P * a.K;
-    finalize_kernel<<<(PK + kFinalizeThreads - 1) / kFinalizeThreads, kFinalizeThreads, 0, st>>>(a);
+    finalize_kernel<<<(a.L.T + kFinalizeThreads - 1) / kFinalizeThreads, kFinalizeThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_stein(const UpdateArgs &a, cudaStream_t st)
 {
-    const int threads = ((a.K + 31) / 32) * 32;
-    const size_t smem = sizeof(float4) * 4 * (size_t)a.K;
-    stein_kernel<<<a.P, threads, smem, st>>>(a);
+    const size_t smem = sizeof(float4) * 4 * (size_t)kMaxK;
+    stein_kernel<<<a.L.G, kSteinThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -382,11 +411,13 @@ cudaError_t launch_preshape_consts(const float4 *S, int N, double *out12, cudaSt
 // every preshape.  u_j: z = 1 - (2j+1)/K, azimuth j * pi * (3 - sqrt 5);
 // t_j = CoM + radius u_j; q_j the smallest rotation taking +z (the approach
 // axis) to -u_j, pi about x when -u_j = -z.
-__global__ void fibonacci_kernel(int P, int K, const double *com, float radius, float *theta)
+__global__ void fibonacci_kernel(const Layout L, float radius, float *theta)
 {
     const int pk = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pk >= P * K) return;
-    const int j = pk % K;
+    if (pk >= L.T) return;
+    const int grp = L.part_grp[pk];
+    const int j = pk - L.grp_off[grp], K = L.grp_off[grp + 1] - L.grp_off[grp];
+    const double *com = L.com + 3 * (grp / L.P);
     const double ga = 3.14159265358979323846 * (3.0 - sqrt(5.0));
     const double z = 1.0 - (2.0 * j + 1.0) / K;
     const double rho = sqrt(fmax(0.0, 1.0 - z * z));
@@ -406,10 +437,24 @@ __global__ void fibonacci_kernel(int P, int K, const double *com, float radius, 
     th[7] = 0.f;
 }
 
-cudaError_t launch_fibonacci(int P, int K, const double *com, float radius, float *theta, cudaStream_t st)
+cudaError_t launch_fibonacci(const Layout &L, float radius, float *theta, cudaStream_t st)
 {
-    const int n = P * K;
-    fibonacci_kernel<<<(n + 255) / 256, 256, 0, st>>>(P, K, com, radius, theta);
+    fibonacci_kernel<<<(L.T + 255) / 256, 256, 0, st>>>(L, radius, theta);
+    return cudaGetLastError();
+}
+
+// Particle -> group map and group offsets for P groups of K particles (one object).
+__global__ void uniform_groups_kernel(int *part_grp, int *grp_off, int P, int K)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P * K) part_grp[i] = i / K;
+    if (i <= P) grp_off[i] = i * K;
+}
+
+cudaError_t launch_uniform_groups(int *part_grp, int *grp_off, int P, int K, cudaStream_t st)
+{
+    const int n = P * K + 1;
+    uniform_groups_kernel<<<(n + 255) / 256, 256, 0, st>>>(part_grp, grp_off, P, K);
     return cudaGetLastError();
 }
 
@@ -431,9 +476,9 @@ __global__ void set_theta_kernel(const float *theta7, int PK, float *theta8, int
     d[7] = 0.f;
 }
 
-cudaError_t launch_set_theta(const float *theta7, int PK, float *theta8, int *err, cudaStream_t st)
+cudaError_t launch_set_theta(const float *theta7, int T, float *theta8, int *err, cudaStream_t st)
 {
-    set_theta_kernel<<<(PK + 255) / 256, 256, 0, st>>>(theta7, PK, theta8, err);
+    set_theta_kernel<<<(T + 255) / 256, 256, 0, st>>>(theta7, T, theta8, err);
     return cudaGetLastError();
 }
 
@@ -450,27 +495,33 @@ __device__ __forceinline__ unsigned long long select_key(const double *cost, con
     return ((unsigned long long)(ncol[i] > 0) << 63) | (unsigned long long)__double_as_longlong(v);
 }
 
-__global__ void select_kernel(const double *cost, const int *ncol, int total, int *order)
+// One CTA per object: ranks the object's particles; order[pfirst + r] is the
+// global index of the particle of rank r.
+__global__ void select_kernel(const Layout L, const double *cost, const int *ncol, int *order)
 {
     __shared__ unsigned long long keys[kSelectSmem];
+    const ObjMeta &om = L.obj[blockIdx.x];
+    const int total = om.np;
+    const double *c = cost + om.pfirst;
+    const int *nc = ncol + om.pfirst;
     const bool staged = total <= kSelectSmem;
     if (staged)
-        for (int i = threadIdx.x; i < total; i += blockDim.x) keys[i] = select_key(cost, ncol, i);
+        for (int i = threadIdx.x; i < total; i += blockDim.x) keys[i] = select_key(c, nc, i);
     __syncthreads();
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
-        const unsigned long long ki = staged ? keys[i] : select_key(cost, ncol, i);
+        const unsigned long long ki = staged ? keys[i] : select_key(c, nc, i);
         int rank = 0;
         for (int k = 0; k < total; ++k) {
-            const unsigned long long kk = staged ? keys[k] : select_key(cost, ncol, k);
+            const unsigned long long kk = staged ? keys[k] : select_key(c, nc, k);
             rank += kk < ki || (kk == ki && k < i);
         }
-        order[rank] = i;
+        order[om.pfirst + rank] = om.pfirst + i;
     }
 }
 
-cudaError_t launch_select(const double *cost, const int *ncol, int total, int *order, cudaStream_t st)
+cudaError_t launch_select(const Layout &L, const double *cost, const int *ncol, int *order, cudaStream_t st)
 {
-    select_kernel<<<1, 1024, 0, st>>>(cost, ncol, total, order);
+    select_kernel<<<L.nobj, 1024, 0, st>>>(L, cost, ncol, order);
     return cudaGetLastError();
 }
 

@@ -35,15 +35,20 @@ constexpr int kMaxDevices = 64;
 //   object    [ASICP_NOALLOC_MAX_M] float4         1 MiB
 //   screening [ASICP_NOALLOC_MAX_M] 16 B           1 MiB
 //   staging   3 * max(M, P*N, 7/3 P*K) floats     768 KiB
-//   rmax (float), error word (int)
+//   particle -> preshape map [P*K] int, preshape offsets [P+1] int   64 KiB each
+//   object table, rmax (float), error word (int)
 constexpr size_t kOffPoses = 0;
 constexpr size_t kOffGripper = kOffPoses + (size_t)ASICP_NOALLOC_MAX_PK * 8 * 4;
 constexpr size_t kOffObject = kOffGripper + (size_t)ASICP_NOALLOC_MAX_PN * 16;
 constexpr size_t kOffScreen = kOffObject + (size_t)ASICP_NOALLOC_MAX_M * 16;
 constexpr size_t kOffStage = kOffScreen + (size_t)ASICP_NOALLOC_MAX_M * 16;
 constexpr size_t kStageFloats = 3 * (size_t)ASICP_NOALLOC_MAX_M;
-constexpr size_t kOffRmax = kOffStage + kStageFloats * 4;
+constexpr size_t kOffPartGrp = kOffStage + kStageFloats * 4;
+constexpr size_t kOffGrpOff = kOffPartGrp + (size_t)ASICP_NOALLOC_MAX_PK * 4;
+constexpr size_t kOffObjMeta = kOffGrpOff + ((size_t)ASICP_NOALLOC_MAX_PK + 64) * 4;
+constexpr size_t kOffRmax = kOffObjMeta + 256;
 constexpr size_t kOffErr = kOffRmax + 256;
+static_assert(sizeof(ObjMeta) <= 256, "object table slot too small");
 static_assert(kOffErr + 256 <= kScratchBytes, "scratch layout exceeds the static array");
 static_assert(kStageFloats >= 3 * (size_t)ASICP_NOALLOC_MAX_PN && kStageFloats >= 7 * (size_t)ASICP_NOALLOC_MAX_PK,
               "staging area too small");
@@ -105,6 +110,9 @@ extern "C" asicp_status asicp_match_noalloc(const float *theta, int P, int K, co
     float *stage = reinterpret_cast<float *>(base + kOffStage);
     float *rmax = reinterpret_cast<float *>(base + kOffRmax);
     int *err = reinterpret_cast<int *>(base + kOffErr);
+    int *part_grp = reinterpret_cast<int *>(base + kOffPartGrp);
+    int *grp_off = reinterpret_cast<int *>(base + kOffGrpOff);
+    ObjMeta *objmeta = reinterpret_cast<ObjMeta *>(base + kOffObjMeta);
     const int PK = P * K;
     const int Mpad = (M + kRefTilePts - 1) / kRefTilePts * kRefTilePts;
 
@@ -126,18 +134,30 @@ extern "C" asicp_status asicp_match_noalloc(const float *theta, int P, int K, co
     if (!rx) return ASICP_ERR_CUDA;
     NOALLOC_CK(launch_pack_points(rx, M, obj, err, st));
     NOALLOC_CK(launch_ref_prep(obj, M, Mpad, screen, rmax, st));
+    NOALLOC_CK(launch_uniform_groups(part_grp, grp_off, P, K, st));
+    ObjMeta om{};          // one object holding every particle (copied by value below)
+    om.R = obj;
+    om.Rx = screen;
+    om.C = obj;
+    om.M = M; om.Mpad = Mpad; om.Mc = M; om.chunks = 0;
+    om.pfirst = 0; om.np = PK;
+    NOALLOC_CK(cudaMemcpyAsync(objmeta, &om, sizeof(ObjMeta), cudaMemcpyHostToDevice, st));
 
     FwdArgs fa{};
+    fa.L.P = P; fa.L.N = N; fa.L.G = P; fa.L.nobj = 1; fa.L.T = PK;
+    fa.L.part_grp = part_grp;
+    fa.L.grp_off = grp_off;
+    fa.L.obj = objmeta;
+    fa.L.com = nullptr;
+    fa.L.rmax = rmax;
     fa.S = grip;
     fa.theta = poses;
-    fa.R = obj;
-    fa.Rx = screen;
-    fa.rmax = rmax;
+    fa.items = nullptr;    // consecutive work items of object 0
+    fa.n_items = (int)(((long long)PK * N + kFwdItemQueries - 1) / kFwdItemQueries);
     fa.err = err;
-    fa.M = M; fa.Mpad = Mpad; fa.N = N; fa.K = K; fa.PK = PK;
     fa.nn_idx = nn_idx;
     NOALLOC_CK(launch_fwd_match(fa, st));
-    NOALLOC_CK(cudaStreamSynchronize(st));
+    NOALLOC_CK(cudaStreamSynchronize(st));   // also keeps `om` alive until its copy is done
     int e = 0;
     NOALLOC_CK(cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost));
 #undef NOALLOC_CK

@@ -18,6 +18,11 @@ from paper_2412_08346_gb300 import asicp, synth
 NEAR_TIE_REL = 1e-6
 PHI_TOL = 1e-6
 COST_GRAD_REL = 1e-4
+# absolute floors for values at the rounding level of the per-particle sums (a cost
+# or gradient that cancels to ~0 has no meaningful relative error): the sums carry
+# ~1e-14 relative error of terms of magnitude <= ~0.1 m^2 / 0.3 m
+COST_ABS = 1e-14
+GRAD_ABS = 1e-13
 
 
 def make_config(w: synth.Workload, stream=None, debug=True, profile=False, **over):
@@ -133,11 +138,13 @@ def check_step(orc, w, before_theta, st, k, report, check_update=True, sample=No
             report["colliding_particles"] = report.get("colliding_particles", 0) + 1
         else:
             cost_o, g_o = orc.match_terms(p, th, st["nn_idx"][pk])
-        assert abs(st["cost"][pk] - cost_o) <= COST_GRAD_REL * abs(cost_o), f"particle {pk}: cost {st['cost'][pk]} vs {cost_o}"
+        assert abs(st["cost"][pk] - cost_o) <= COST_GRAD_REL * abs(cost_o) + COST_ABS, \
+            f"particle {pk}: cost {st['cost'][pk]} vs {cost_o}"
         for blk in (slice(0, 3), slice(3, 7)):
             e = rel_err(st["grad"][pk, blk], g_o[blk], floor=1e-300)
             report["max_grad_rel"] = max(report.get("max_grad_rel", 0.0), e)
-            assert e <= COST_GRAD_REL, f"particle {pk}: gradient block {blk} relative error {e:.3e}"
+            assert np.linalg.norm(st["grad"][pk, blk] - g_o[blk]) <= COST_GRAD_REL * np.linalg.norm(g_o[blk]) + GRAD_ABS, \
+                f"particle {pk}: gradient block {blk} relative error {e:.3e}"
         report["max_cost_rel"] = max(report.get("max_cost_rel", 0.0), abs(st["cost"][pk] - cost_o) / abs(cost_o))
     report["particles"] = report.get("particles", 0) + len(list(pks))
     if not check_update or sample is not None:

@@ -284,3 +284,133 @@ def test_kernel_times_from_graph_replays(stream):
         asicp.asicp_destroy(ctx)
     assert n == [2 * (w.k_max + 1)] * 4 + [2 * w.k_stein]
     assert all(t > 0 for t in ms)
+
+
+def _uneven_batch(seed=43):
+    """4 objects with uneven point counts and per-(object, preshape) particle counts."""
+    g = np.random.default_rng(seed)
+    P, N = 2, 256
+    pre = synth.make_preshapes(P, N, 24, seed)
+    sizes = [900, 2500, 4100, 1500]
+    objs = [synth.partial_object(M, seed + 100 * (o + 1)) for o, M in enumerate(sizes)]
+    K = g.choice([8, 16, 24], size=(len(sizes), P)).astype(np.int32)
+    return pre, objs, K
+
+
+def test_batched_objects_match_solo_runs(stream):
+    """Objects optimised together (one launch per kernel covering all of them) give bit-identical
+    poses, costs and rankings to running each object alone."""
+    pre, objs, K = _uneven_batch()
+    P, k_max, k_stein = 2, 6, 3
+
+    def make(nobj):
+        cfg = asicp.asicp_config_default(P=P, K=8, k_max=k_max, k_stein=k_stein, conv_tol=-1.0, cuda_stream=stream,
+                                         n_objects=nobj)
+        return asicp.asicp_create(cfg)
+
+    ctx = make(len(objs))
+    try:
+        asicp.asicp_set_particle_counts(ctx, K.ravel())
+        for o, ob in enumerate(objs):
+            asicp.asicp_set_object_at(ctx, o, ob.points)
+        for p, ps in enumerate(pre):
+            asicp.asicp_set_gripper_sdf(ctx, p, ps.S, ps.sdf, ps.origin, ps.voxel)
+        asicp.asicp_run(ctx)
+        T = int(K.sum())
+        th_b = np.zeros((T, 7), np.float32)
+        cost_b = np.zeros(T)
+        asicp.asicp_get_state(ctx, theta=th_b, cost=cost_b)
+        best_b = []
+        for o in range(len(objs)):
+            bt = np.zeros(5 * 7, np.float32)
+            bc = np.zeros(5, np.float32)
+            bp = np.zeros(5, np.int32)
+            asicp.asicp_best_grasps_at(ctx, o, 5, bt, bc, bp)
+            best_b.append((bt, bc, bp))
+    finally:
+        asicp.asicp_destroy(ctx)
+
+    first = 0
+    for o, ob in enumerate(objs):
+        n = int(K[o].sum())
+        ctx = make(1)
+        try:
+            asicp.asicp_set_particle_counts(ctx, K[o])
+            asicp.asicp_set_object(ctx, ob.points)
+            for p, ps in enumerate(pre):
+                asicp.asicp_set_gripper_sdf(ctx, p, ps.S, ps.sdf, ps.origin, ps.voxel)
+            asicp.asicp_run(ctx)
+            th = np.zeros((n, 7), np.float32)
+            cost = np.zeros(n)
+            asicp.asicp_get_state(ctx, theta=th, cost=cost)
+            bt = np.zeros(5 * 7, np.float32)
+            bc = np.zeros(5, np.float32)
+            bp = np.zeros(5, np.int32)
+            asicp.asicp_best_grasps(ctx, 5, bt, bc, bp)
+        finally:
+            asicp.asicp_destroy(ctx)
+        assert np.array_equal(th, th_b[first:first + n]), f"object {o}: poses differ from the solo run"
+        assert np.array_equal(cost, cost_b[first:first + n]), f"object {o}: costs differ from the solo run"
+        for a, b in zip((bt, bc, bp), best_b[o]):
+            assert np.array_equal(a, b)
+        first += n
+
+
+def test_batched_step_teacher_forced(stream):
+    """One batched SVGD step against the oracle, object by object (uneven sizes and particle counts)."""
+    pre, objs, K = _uneven_batch(seed=47)
+    import oracle
+    P, N = 2, 256
+    cfg = asicp.asicp_config_default(P=P, K=8, k_max=4, k_stein=2, conv_tol=-1.0, debug=1, cuda_stream=stream,
+                                     n_objects=len(objs))
+    ctx = asicp.asicp_create(cfg)
+    try:
+        asicp.asicp_set_particle_counts(ctx, K.ravel())
+        for o, ob in enumerate(objs):
+            asicp.asicp_set_object_at(ctx, o, ob.points)
+        for p, ps in enumerate(pre):
+            asicp.asicp_set_gripper_sdf(ctx, p, ps.S, ps.sdf, ps.origin, ps.voxel)
+        T = int(K.sum())
+        th0 = []
+        for o, ob in enumerate(objs):
+            for p in range(P):
+                th0.append(oracle.fibonacci_init(int(K[o, p]), ob.points.astype(np.float64).mean(0), 0.06))
+        asicp.asicp_set_state(ctx, np.ascontiguousarray(np.concatenate(th0), dtype=np.float32), 0)
+        before = tl.read_theta(ctx, T)
+        asicp.asicp_step(ctx, 1)
+        Mtot = sum(int(K[o].sum()) * len(ob.points) for o, ob in enumerate(objs))
+        st = {"theta": np.zeros((T, 7), np.float32), "cost": np.zeros(T), "grad": np.zeros((T, 7)),
+              "ncol": np.zeros(T, np.int32), "nn_idx": np.zeros((T, N), np.int32),
+              "s_prime": np.zeros((T, N, 3), np.float32), "col_list": np.zeros(Mtot, np.int32),
+              "col_nn": np.zeros(Mtot, np.int32)}
+        asicp.asicp_get_state(ctx, **st)
+    finally:
+        asicp.asicp_destroy(ctx)
+    rep = {}
+    cfirst = 0
+    for o, ob in enumerate(objs):
+        orc = oracle.Oracle(np.stack([ps.S for ps in pre]), [(ps.sdf, ps.origin, ps.voxel) for ps in pre], ob.points)
+        M = len(ob.points)
+        first_o = sum(int(K[q].sum()) for q in range(o))
+        for pk in range(first_o, first_o + int(K[o].sum())):
+            p = next(pp for pp in range(P) if pk < first_o + int(K[o, :pp + 1].sum()))
+            th = before[pk].astype(np.float64)
+            tl.check_nn(st["s_prime"][pk], orc.R, st["nn_idx"][pk], rep)
+            n = int(st["ncol"][pk])
+            base = cfirst + (pk - first_o) * M
+            lst_g = st["col_list"][base:base + n]
+            lst_o, vals = orc.collision_points(p, th)
+            if not np.array_equal(lst_g, lst_o):
+                diff = np.setxor1d(lst_g, lst_o)
+                assert np.all(np.abs(vals[diff]) <= tl.PHI_TOL)
+                continue
+            if n > 0:
+                cost_o, g_o = orc.collision_terms(p, th, lst_g, st["col_nn"][base:base + n])
+            else:
+                cost_o, g_o = orc.match_terms(p, th, st["nn_idx"][pk])
+            assert abs(st["cost"][pk] - cost_o) <= tl.COST_GRAD_REL * abs(cost_o) + tl.COST_ABS
+            for blk in (slice(0, 3), slice(3, 7)):
+                e = np.linalg.norm(st["grad"][pk, blk] - g_o[blk])
+                assert e <= tl.COST_GRAD_REL * np.linalg.norm(g_o[blk]) + tl.GRAD_ABS
+        cfirst += int(K[o].sum()) * M
+    print("batched step:", rep)
