@@ -66,10 +66,16 @@ typedef enum {
  *                  every kernel covers all of them, each particle matched against its
  *                  own object (Section IV-D's "combine into multidimensional tensors",
  *                  extended across objects)
+ *   autotune      1: the first asicp_run times the forward-matching kernel shapes on its
+ *                  workload and keeps the fastest (see asicp_autotune); 0: use fwd_shape
+ *   fwd_shape     forward-matching kernel shape, 0 .. ASICP_FWD_SHAPES-1 (0 = default;
+ *                  the shapes differ in speed only, never in results)
  * Particles are numbered object by object, preshape by preshape: the group
  * g = object * P + preshape holds K_g particles (K_g = K unless set with
  * asicp_set_particle_counts); T = sum of K_g is the particle count of every
  * per-particle array below. */
+#define ASICP_FWD_SHAPES 4
+
 typedef struct {
     int P, K;
     int k_max, k_stein;
@@ -85,6 +91,8 @@ typedef struct {
     int profile;
     void *cuda_stream;
     int n_objects;
+    int autotune;
+    int fwd_shape;
 } asicp_config;
 
 /* Host pointers (or device pointers) the library fills in asicp_get_state; any
@@ -224,6 +232,15 @@ asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[5], long long launches
 #define ASICP_NOALLOC_MAX_M 65536
 asicp_status asicp_match_noalloc(const float *theta, int P, int K, const float *S_xyz, int N,
                                  const float *R_xyz, int M, int *nn_idx, void *cuda_stream);
+
+/* Time every shape of the forward-matching kernel (queries per thread 8 or 4 with
+ *128 or 256 threads, screening chunks of 64 or 32 object points) on the context's
+ * current objects and poses (the Fibonacci initial poses when none are set) and
+ * keep the fastest for later steps and runs.  *chosen receives the shape index
+ * (0 .. 3), ms[4] the mean launch time of each shape (either may be NULL).  The
+ * results of every shape are identical; only their speed differs.
+ * Errors: STATE (inputs not set), CUDA. */
+asicp_status asicp_autotune(asicp_ctx *ctx, int *chosen, float *ms);
 
 /* Message of the last failing call on ctx (owned by ctx, valid until its next call). */
 const char *asicp_last_error(const asicp_ctx *ctx);

@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "STATE", 3: "CUDA", 4: "OOM", 5: "
 EXPORTED = ("asicp_config_default", "asicp_create", "asicp_destroy", "asicp_set_object",
             "asicp_set_gripper_sdf", "asicp_set_state", "asicp_step", "asicp_run", "asicp_best_grasps",
             "asicp_get_state", "asicp_kernel_times", "asicp_last_error", "asicp_match_noalloc",
-            "asicp_set_object_at", "asicp_set_particle_counts", "asicp_best_grasps_at")
+            "asicp_set_object_at", "asicp_set_particle_counts", "asicp_best_grasps_at", "asicp_autotune")
 
 
 class AsicpError(RuntimeError):
@@ -42,7 +42,7 @@ class asicp_config(C.Structure):
                 ("g1", C.c_float), ("eta_sgd", C.c_float), ("eta_svgd", C.c_float), ("w_com", C.c_float),
                 ("bandwidth_mode", C.c_int), ("h_fixed", C.c_float), ("conv_tol", C.c_float),
                 ("init_radius", C.c_float), ("debug", C.c_int), ("profile", C.c_int),
-                ("cuda_stream", C.c_void_p), ("n_objects", C.c_int)]
+                ("cuda_stream", C.c_void_p), ("n_objects", C.c_int), ("autotune", C.c_int), ("fwd_shape", C.c_int)]
 
 
 class asicp_state_view(C.Structure):
@@ -84,6 +84,7 @@ def load(build_if_missing: bool = True):
     lib.asicp_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), ip]
     lib.asicp_match_noalloc.argtypes = [vp, ip, ip, vp, ip, vp, ip, vp, vp]
     lib.asicp_set_object_at.argtypes = [vp, ip, vp, ip, vp, ip]
+    lib.asicp_autotune.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_float)]
     lib.asicp_set_particle_counts.argtypes = [vp, vp, ip]
     lib.asicp_best_grasps_at.argtypes = [vp, ip, ip, vp, vp, vp, C.POINTER(C.c_int)]
     lib.asicp_last_error.argtypes = [vp]
@@ -213,6 +214,18 @@ def asicp_match_noalloc(theta, S_xyz, R_xyz, nn_idx, P: int, K: int, stream=None
                                     int(R_xyz.shape[0]), _ptr(nn_idx), stream)
     if st != ASICP_OK:
         raise AsicpError(st, "asicp_match_noalloc failed")
+
+
+FWD_VARIANTS = ("qpt8-chunk64", "qpt8-chunk32", "qpt4-chunk64", "qpt4-chunk32")
+FWD_SHAPES = len(FWD_VARIANTS)          # ASICP_FWD_SHAPES
+
+
+def asicp_autotune(ctx):
+    """Pick the fastest forward-matching kernel shape; returns (index, [ms per shape])."""
+    chosen = C.c_int(0)
+    ms = (C.c_float * FWD_SHAPES)()
+    _check(ctx, load().asicp_autotune(ctx, C.byref(chosen), ms))
+    return chosen.value, list(ms)
 
 
 def asicp_last_error(ctx) -> str:

@@ -20,6 +20,7 @@
 #include <vector>
 
 using namespace asicp;
+static_assert(kFwdVariants == ASICP_FWD_SHAPES, "kernel shape count differs from the header");
 
 namespace {
 
@@ -89,6 +90,9 @@ struct asicp_ctx {
     std::vector<SdfMeta> meta;
     std::vector<DevMem> grids;
     int k_next = 0;
+
+    int fwd_variant = 0;              // forward-matching kernel shape (autotuner's choice)
+    bool tuned = false;
 
     // layout (rebuilt when objects, particle counts or N change)
     bool layout_dirty = true;
@@ -366,6 +370,7 @@ void iterate(asicp_ctx *c, int mode, float gamma)
     fa.n_items = c->n_items;
     fa.err = c->errw.as<int>();
     fa.nn_idx = c->nnidx.as<int>();
+    fa.variant = c->fwd_variant;
     if (c->cfg.debug) {
         fa.dbg_d2 = c->dbg_d2.as<float>();
         fa.dbg_sp = c->dbg_sp.as<float>();
@@ -443,7 +448,7 @@ std::vector<const void *> loop_key(const asicp_ctx *c)
             c->grad.p, c->prev.p, c->frozen.p, c->phi.p, c->h.p, c->order.p, c->errw.p, c->nnidx.p, c->dbg_d2.p,
             c->dbg_sp.p, c->dbg_colnn.p, reinterpret_cast<const void *>((size_t)c->T),
             reinterpret_cast<const void *>((size_t)c->G), reinterpret_cast<const void *>((size_t)c->n_items),
-            reinterpret_cast<const void *>((size_t)c->N)};
+            reinterpret_cast<const void *>((size_t)c->N), reinterpret_cast<const void *>((size_t)c->fwd_variant)};
 }
 
 // Replay the captured loop on the caller's stream, capturing it first when the
@@ -515,6 +520,42 @@ __global__ void gather_best_kernel(const int *order, int first, int n, const int
     oi[r] = part_grp[i] % P;
 }
 
+// Time every forward-matching kernel shape on the context's current work (poses
+// as they are) and keep the fastest.  ms[v] receives the mean launch time.
+void autotune_impl(asicp_ctx *c, float *ms_out)
+{
+    const int reps = 3;
+    cudaEvent_t e0 = c->take_event(), e1 = c->take_event();
+    float best = 0.f;
+    int best_v = 0;
+    for (int v = 0; v < kFwdVariants; ++v) {
+        FwdArgs fa{};
+        fa.L = c->layout();
+        fa.S = c->S.as<float4>();
+        fa.theta = c->theta.as<float>();
+        fa.items = c->items.as<FwdItem>();
+        fa.n_items = c->n_items;
+        fa.err = c->errw.as<int>();
+        fa.nn_idx = c->nnidx.as<int>();
+        fa.variant = v;
+        ck(launch_fwd_match(fa, c->st), "autotune warm-up");
+        ck(cudaEventRecord(e0, c->st), "cudaEventRecord");
+        for (int r = 0; r < reps; ++r) ck(launch_fwd_match(fa, c->st), "autotune launch");
+        ck(cudaEventRecord(e1, c->st), "cudaEventRecord");
+        ck(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        float t = 0.f;
+        ck(cudaEventElapsedTime(&t, e0, e1), "cudaEventElapsedTime");
+        t /= reps;
+        if (ms_out) ms_out[v] = t;
+        if (v == 0 || t < best) { best = t; best_v = v; }
+    }
+    c->pool.push_back(e0);
+    c->pool.push_back(e1);
+    sync_and_check_err(c, "autotune");
+    c->fwd_variant = best_v;
+    c->tuned = true;
+}
+
 void set_object_impl(asicp_ctx *ctx, int o, const float *R_xyz, int M, const float *C_xyz, int Mc)
 {
     if (o < 0 || o >= ctx->nobj) fail(ASICP_ERR_INVALID_ARG, "set_object: object index out of range");
@@ -576,6 +617,8 @@ void asicp_config_default(asicp_config *cfg)
     cfg->profile = 0;
     cfg->cuda_stream = nullptr;
     cfg->n_objects = 1;
+    cfg->autotune = 0;
+    cfg->fwd_shape = 0;
 }
 
 asicp_status asicp_create(const asicp_config *cfg, asicp_ctx **out)
@@ -586,13 +629,15 @@ asicp_status asicp_create(const asicp_config *cfg, asicp_ctx **out)
         cfg->k_stein > cfg->k_max || (cfg->schedule != 0 && cfg->schedule != 1) ||
         (cfg->schedule == 0 && !(cfg->C_cycles > 0.f)) || !(cfg->eta_sgd >= 0.f) ||
         (cfg->bandwidth_mode == 1 && !(cfg->h_fixed > 0.f)) || !std::isfinite(cfg->w_com) ||
-        !(cfg->init_radius >= 0.f) || cfg->n_objects < 1 || cfg->n_objects > 4096)
+        !(cfg->init_radius >= 0.f) || cfg->n_objects < 1 || cfg->n_objects > 4096 ||
+        cfg->fwd_shape < 0 || cfg->fwd_shape >= kFwdVariants)
         return ASICP_ERR_INVALID_ARG;
     asicp_ctx *c = new (std::nothrow) asicp_ctx();
     if (!c) return ASICP_ERR_OOM;
     c->cfg = *cfg;
     c->st = static_cast<cudaStream_t>(cfg->cuda_stream);
     c->nobj = cfg->n_objects;
+    c->fwd_variant = cfg->fwd_shape;
     c->pre_set.assign(cfg->P, 0);
     c->meta.assign(cfg->P, SdfMeta{});
     c->grids.resize(cfg->P);
@@ -765,6 +810,7 @@ asicp_status asicp_run(asicp_ctx *ctx, const float *theta0)
             ck(launch_fibonacci(ctx->layout(), ctx->cfg.init_radius, ctx->theta.as<float>(), ctx->st), "fibonacci init");
         }
         ctx->theta_set = true;
+        if (ctx->cfg.autotune && !ctx->tuned) autotune_impl(ctx, nullptr);
         run_loop_graph(ctx);
         ctx->k_next = ctx->cfg.k_max;
         ctx->stepped = true;
@@ -845,6 +891,21 @@ asicp_status asicp_get_state(asicp_ctx *ctx, const asicp_state_view *v)
         }
         copy_out(v->frozen, ctx->frozen.p, sizeof(int) * T, ctx->st, "copy frozen");
         sync_and_check_err(ctx, "get_state");
+    });
+}
+
+asicp_status asicp_autotune(asicp_ctx *ctx, int *chosen, float *ms)
+{
+    return guarded(ctx, [&] {
+        if (!ctx->inputs_ready()) fail(ASICP_ERR_STATE, "autotune: objects and every preshape must be set first");
+        build_layout(ctx);
+        if (!ctx->theta_set) {
+            ck(launch_fibonacci(ctx->layout(), ctx->cfg.init_radius, ctx->theta.as<float>(), ctx->st), "fibonacci init");
+            ctx->theta_set = true;
+            ctx->stepped = false;
+        }
+        autotune_impl(ctx, ms);
+        if (chosen) *chosen = ctx->fwd_variant;
     });
 }
 

@@ -174,10 +174,13 @@ struct FwdArgs {
     int *nn_idx;             // [T][N] nearest object point per query
     float *dbg_d2;           // [T][N] or null
     float *dbg_sp;           // [T][N][3] or null
+    int variant;             // kernel shape (0 .. kFwdVariants - 1), chosen by the autotuner
 };
-cudaError_t launch_fwd_match(const FwdArgs &a, cudaStream_t st);
-int fwd_grid_size();                   // persistent grid; first call sets kernel attributes
 constexpr int kFwdItemQueries = 1024;  // queries per forward-matching work item
+constexpr int kFwdVariants = 4;        // kernel shapes of the forward matching
+cudaError_t launch_fwd_match(const FwdArgs &a, cudaStream_t st);
+int fwd_grid_size();                   // first call sets the kernels' attributes
+const char *fwd_variant_name(int v);
 cudaError_t init_collision_attributes();
 cudaError_t init_update_attributes();
 cudaError_t launch_ref_prep(const float4 *R, int M, int Mpad, void *Rx, float *rmax, cudaStream_t st);

@@ -37,10 +37,16 @@ namespace asicp {
 
 namespace {
 
-constexpr int kThreads = 128;            // threads per CTA
-constexpr int QPT = 8;                   // queries per thread
-constexpr int kChunk = 64;               // screening chunk (object points)
 constexpr int kTile = kRefTilePts;       // object points per shared-memory tile
+
+// Kernel shapes the autotuner chooses from: (queries per thread, screening chunk,
+// threads per CTA); every shape holds kFwdItemQueries queries per work item.
+template <int QPT_, int CHUNK_>
+struct FwdShape {
+    static constexpr int QPT = QPT_;
+    static constexpr int kChunk = CHUNK_;
+    static constexpr int kThreads = kFwdItemQueries / QPT_;
+};
 constexpr long long kWaitCycles = 1LL << 32;   // bounded mbarrier wait (~2 s)
 
 __device__ __forceinline__ unsigned long long pack2(float lo, float hi)
@@ -132,10 +138,11 @@ __device__ __forceinline__ void exact_scan(const float4 *__restrict__ R, int lo,
 // all on one object) over that object's whole cloud.  Object tiles stream
 // through the two shared buffers; `seq` counts the tiles this CTA has consumed,
 // which gives each buffer's mbarrier phase.
-template <int Q>
+template <class Shape, int Q>
 __device__ __forceinline__ bool match_pass(const FwdArgs &a, const ObjMeta &om, float rmax, long long q0, int nq,
                                            ulonglong2 *tiles, unsigned long long *full, int &seq, int *s_abort)
 {
+    constexpr int kThreads = Shape::kThreads, kChunk = Shape::kChunk;
     const int ntiles = om.Mpad / kTile;
     const unsigned tile_bytes = kTile * 16u;
     if (threadIdx.x == 0) {    // both buffers are free: the previous pass ended with a barrier
@@ -246,8 +253,10 @@ __device__ __forceinline__ bool match_pass(const FwdArgs &a, const ObjMeta &om, 
 // first when objects differ, so the tail is short); an item is at most
 // kThreads * QPT queries of one object, and a partial item uses the smallest
 // queries-per-thread instantiation that covers it.
-__global__ void __launch_bounds__(kThreads, 3) fwd_match_kernel(const FwdArgs a)
+template <class Shape>
+__global__ void __launch_bounds__(Shape::kThreads, 3 * 128 / Shape::kThreads) fwd_match_kernel(const FwdArgs a)
 {
+    constexpr int kThreads = Shape::kThreads;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     ulonglong2 *tiles = reinterpret_cast<ulonglong2 *>(smem_raw);
     __shared__ __align__(8) unsigned long long full[2];
@@ -274,42 +283,80 @@ __global__ void __launch_bounds__(kThreads, 3) fwd_match_kernel(const FwdArgs a)
         }
         const ObjMeta om = a.L.obj[item.obj];
         const float rmax = a.L.rmax[item.obj];
-        switch ((item.nq + kThreads - 1) / kThreads) {
-            case 1: ok = match_pass<1>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-            case 2: ok = match_pass<2>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-            case 3: ok = match_pass<3>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-            case 4: ok = match_pass<4>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-            case 5: ok = match_pass<5>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-            case 6: ok = match_pass<6>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-            case 7: ok = match_pass<7>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-            default: ok = match_pass<8>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+        const int qn = (item.nq + kThreads - 1) / kThreads;
+        if (Shape::QPT == 8) {
+            switch (qn) {
+                case 1: ok = match_pass<Shape, 1>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+                case 2: ok = match_pass<Shape, 2>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+                case 3: ok = match_pass<Shape, 3>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+                case 4: ok = match_pass<Shape, 4>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+                case 5: ok = match_pass<Shape, 5>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+                case 6: ok = match_pass<Shape, 6>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+                case 7: ok = match_pass<Shape, 7>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+                default: ok = match_pass<Shape, 8>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+            }
+        } else {   // QPT 4
+            switch (qn) {
+                case 1: ok = match_pass<Shape, 1>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+                case 2: ok = match_pass<Shape, 2>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+                case 3: ok = match_pass<Shape, 3>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+                default: ok = match_pass<Shape, 4>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
+            }
         }
     }
     if (!ok && threadIdx.x == 0)   // drain copies still in flight (bounded) before leaving
         for (int b = 0; b < 2; ++b) mbar_wait(&full[(seq + b) & 1], (unsigned)((seq + b) >> 1) & 1u);
 }
 
-int fwd_grid_size()
+using Shape0 = FwdShape<8, 64>;   // 128 threads
+using Shape1 = FwdShape<8, 32>;
+using Shape2 = FwdShape<4, 64>;   // 256 threads
+using Shape3 = FwdShape<4, 32>;
+
+template <class Shape>
+int shape_grid()
 {
     static int grid = 0;
     if (grid == 0) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(fwd_match_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kTile * 16);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_match_kernel, kThreads, 2 * kTile * 16);
+        cudaFuncSetAttribute(fwd_match_kernel<Shape>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kTile * 16);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_match_kernel<Shape>, Shape::kThreads,
+                                                      2 * kTile * 16);
         grid = sms * (per_sm > 0 ? per_sm : 1);
     }
     return grid;
 }
 
+int fwd_grid_size()
+{
+    return shape_grid<Shape0>() + shape_grid<Shape1>() + shape_grid<Shape2>() + shape_grid<Shape3>();
+}
+
+const char *fwd_variant_name(int v)
+{
+    static const char *names[kFwdVariants] = {"qpt8-chunk64", "qpt8-chunk32", "qpt4-chunk64", "qpt4-chunk32"};
+    return (v >= 0 && v < kFwdVariants) ? names[v] : "unknown";
+}
+
+template <class Shape>
+cudaError_t launch_shape(const FwdArgs &a, cudaStream_t st)
+{
+    static_assert(kFwdItemQueries == Shape::kThreads * Shape::QPT, "work items hold kThreads * QPT queries");
+    const size_t smem = 2 * (size_t)kTile * 16;
+    fwd_match_kernel<Shape><<<shape_grid<Shape>(), Shape::kThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fwd_match(const FwdArgs &a, cudaStream_t st)
 {
-    static_assert(kFwdItemQueries == kThreads * QPT, "work items hold kThreads * QPT queries");
-    const size_t smem = 2 * (size_t)kTile * 16;
-    const int grid = fwd_grid_size();
-    fwd_match_kernel<<<grid, kThreads, smem, st>>>(a);
-    return cudaGetLastError();
+    switch (a.variant) {
+        case 1: return launch_shape<Shape1>(a, st);
+        case 2: return launch_shape<Shape2>(a, st);
+        case 3: return launch_shape<Shape3>(a, st);
+        default: return launch_shape<Shape0>(a, st);
+    }
 }
 
 // Reference preparation for the screening stage: pair layout of (-2 r, |r|^2)

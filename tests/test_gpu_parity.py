@@ -414,3 +414,42 @@ def test_batched_step_teacher_forced(stream):
                 assert e <= tl.COST_GRAD_REL * np.linalg.norm(g_o[blk]) + tl.GRAD_ABS
         cfirst += int(K[o].sum()) * M
     print("batched step:", rep)
+
+
+def test_every_forward_shape_gives_the_same_correspondences(stream):
+    """Each forward-matching kernel shape (queries per thread x screening chunk) on a ragged case
+    (N=700, M=5000: partial query block, partial chunk and tile): identical indices, equal to the
+    oracle's; the autotuner picks the shape it timed fastest."""
+    w = synth.custom_case(P=2, K=20, N=700, M=5000, grid=24, k_max=3, seed=19)
+    P, K, N, Mc = 2, w.K, 700, len(w.objects[0].points)
+    orc = tl.make_oracle(w)
+    import oracle
+    com = orc.R.mean(0)
+    theta0 = np.tile(oracle.fibonacci_init(K, com, 0.08), (P, 1)).astype(np.float32)
+    got = []
+    for v in range(asicp.FWD_SHAPES):
+        ctx = _ctx(w, stream, debug=1, fwd_shape=v)
+        try:
+            keep = tl.upload(ctx, w)
+            asicp.asicp_set_state(ctx, theta0, 0)
+            before = tl.read_theta(ctx, P * K)
+            asicp.asicp_step(ctx, 0)
+            st = tl.read_state(ctx, P, K, N, Mc)
+            got.append(st["nn_idx"].copy())
+            if v == 0:
+                tl.check_step(orc, w, before, st, 0, {})
+            del keep
+        finally:
+            asicp.asicp_destroy(ctx)
+    for v in range(1, len(got)):
+        assert np.array_equal(got[v], got[0]), f"shape {v} differs from shape 0"
+
+    ctx = _ctx(w, stream)
+    try:
+        keep = tl.upload(ctx, w)
+        chosen, ms = asicp.asicp_autotune(ctx)
+        assert 0 <= chosen < asicp.FWD_SHAPES
+        assert all(t > 0 for t in ms) and ms[chosen] == min(ms)
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
