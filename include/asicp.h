@@ -74,7 +74,7 @@ typedef enum {
  * g = object * P + preshape holds K_g particles (K_g = K unless set with
  * asicp_set_particle_counts); T = sum of K_g is the particle count of every
  * per-particle array below. */
-#define ASICP_FWD_SHAPES 4
+#define ASICP_FWD_SHAPES 7
 
 typedef struct {
     int P, K;
@@ -233,12 +233,13 @@ asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[5], long long launches
 asicp_status asicp_match_noalloc(const float *theta, int P, int K, const float *S_xyz, int N,
                                  const float *R_xyz, int M, int *nn_idx, void *cuda_stream);
 
-/* Time every shape of the forward-matching kernel (queries per thread 8 or 4 with
- *128 or 256 threads, screening chunks of 64 or 32 object points) on the context's
- * current objects and poses (the Fibonacci initial poses when none are set) and
- * keep the fastest for later steps and runs.  *chosen receives the shape index
- * (0 .. 3), ms[4] the mean launch time of each shape (either may be NULL).  The
- * results of every shape are identical; only their speed differs.
+/* Time every shape of the forward-matching kernel (queries per thread, screening
+ * chunk, threads per CTA, shared-memory tile size) on the context's current
+ * objects and poses (the Fibonacci initial poses when none are set) and keep the
+ * fastest for later steps and runs.  *chosen receives the shape index
+ * (0 .. ASICP_FWD_SHAPES-1), ms[ASICP_FWD_SHAPES] the mean launch time of each
+ * shape (either may be NULL).  The results of every shape are identical; only
+ * their speed differs.
  * Errors: STATE (inputs not set), CUDA. */
 asicp_status asicp_autotune(asicp_ctx *ctx, int *chosen, float *ms);
 

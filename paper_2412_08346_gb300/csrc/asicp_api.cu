@@ -16,7 +16,9 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <queue>
 #include <string>
+#include <utility>
 #include <vector>
 
 using namespace asicp;
@@ -101,7 +103,7 @@ struct asicp_ctx {
     std::vector<int> grp_off_h;
     std::vector<ObjMeta> objmeta_h;
 
-    DevMem partgrp, grpoff, objmeta, items, com, rmax, colitems, collist, box, stage, S, pconst, dmeta, theta, fsums,
+    DevMem partgrp, grpoff, objmeta, items, ctaoff, com, rmax, colitems, collist, box, stage, S, pconst, dmeta, theta, fsums,
         csums, ncol, colidx, cost, grad, prev, frozen, phi, h, order, errw, out7, outc, outi, nnidx, dbg_d2, dbg_sp,
         dbg_colnn;
 
@@ -207,6 +209,66 @@ double gamma_of(const asicp_config &c, int k)
 }
 
 // Offsets, work items and buffers for the current objects, particle counts and N.
+// Work plan of the forward matching for kernel shape v.  Items are whole
+// multiples of the shape's CTA size (at most threads x queries per thread) of one
+// object, sized so that about kPlanRounds items of equal cost fall to each CTA
+// of the persistent grid; they are dealt out longest first, each to the CTA
+// with the least work so far (cost = queries x padded object points), and
+// every CTA gets a contiguous range of the item table.
+void plan_fwd_items(asicp_ctx *c, int v)
+{
+    constexpr int kPlanRounds = 4;
+    const int grid = fwd_shape_grid(v), threads = fwd_shape_threads(v), qmax = fwd_shape_queries(v), N = c->N;
+    const std::vector<ObjMeta> &om = c->objmeta_h;
+    double W = 0.0;
+    for (const ObjMeta &m : om) W += (double)m.np * N * m.Mpad;
+    const double unit = W / ((double)grid * kPlanRounds);
+    std::vector<FwdItem> items;
+    for (int o = 0; o < (int)om.size(); ++o) {
+        const ObjMeta &m = om[o];
+        long long nq = (long long)std::ceil(unit / std::max(1, m.Mpad) / threads) * threads;
+        nq = std::min<long long>(std::max<long long>(nq, threads), qmax);
+        const long long q0 = (long long)m.pfirst * N, q1 = (long long)(m.pfirst + m.np) * N;
+        for (long long q = q0; q < q1; q += nq) {
+            FwdItem it;
+            it.q0 = q;
+            it.nq = (int)std::min<long long>(nq, q1 - q);
+            it.obj = o;
+            items.push_back(it);
+        }
+    }
+    auto cost = [&](const FwdItem &x) { return (long long)x.nq * om[x.obj].Mpad; };
+    std::stable_sort(items.begin(), items.end(), [&](const FwdItem &x, const FwdItem &y) { return cost(x) > cost(y); });
+    // least-loaded CTA first (ties: lowest CTA index)
+    using Slot = std::pair<long long, int>;
+    std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+    for (int b = 0; b < grid; ++b) heap.push({0, b});
+    std::vector<int> owner(items.size());
+    std::vector<int> count(grid + 1, 0);
+    for (size_t i = 0; i < items.size(); ++i) {
+        Slot s = heap.top();
+        heap.pop();
+        owner[i] = s.second;
+        ++count[s.second + 1];
+        heap.push({s.first + cost(items[i]), s.second});
+    }
+    std::vector<int> off(grid + 1, 0);
+    for (int b = 0; b < grid; ++b) off[b + 1] = off[b] + count[b + 1];
+    std::vector<FwdItem> placed(items.size());
+    std::vector<int> fill(off.begin(), off.end() - 1);
+    for (size_t i = 0; i < items.size(); ++i) placed[fill[owner[i]]++] = items[i];
+
+    c->items.ensure(sizeof(FwdItem) * std::max<size_t>(1, placed.size()), "matching work items");
+    c->ctaoff.ensure(sizeof(int) * (grid + 1), "matching work plan");
+    if (!placed.empty())
+        ck(cudaMemcpyAsync(c->items.p, placed.data(), sizeof(FwdItem) * placed.size(), cudaMemcpyHostToDevice, c->st),
+           "work items");
+    ck(cudaMemcpyAsync(c->ctaoff.p, off.data(), sizeof(int) * (grid + 1), cudaMemcpyHostToDevice, c->st),
+       "work plan");
+    ck(cudaStreamSynchronize(c->st), "work plan");
+    c->n_items = (int)placed.size();
+}
+
 void build_layout(asicp_ctx *c)
 {
     if (!c->layout_dirty) return;
@@ -219,7 +281,6 @@ void build_layout(asicp_ctx *c)
     for (int g = 0; g < G; ++g)
         for (int i = off[g]; i < off[g + 1]; ++i) part_grp[i] = g;
     std::vector<ObjMeta> om(c->nobj);
-    std::vector<FwdItem> items;
     long long colidx_total = 0, csum_total = 0;
     for (int o = 0; o < c->nobj; ++o) {
         const ObjBufs &b = c->objs[o];
@@ -237,19 +298,7 @@ void build_layout(asicp_ctx *c)
         m.csum_base = csum_total;
         colidx_total += (long long)m.np * m.Mc;
         csum_total += (long long)m.np * m.chunks;
-        const long long q0 = (long long)m.pfirst * N, q1 = (long long)(m.pfirst + m.np) * N;
-        for (long long q = q0; q < q1; q += kFwdItemQueries) {
-            FwdItem it;
-            it.q0 = q;
-            it.nq = (int)std::min<long long>(kFwdItemQueries, q1 - q);
-            it.obj = o;
-            items.push_back(it);
-        }
     }
-    // longest items first: the persistent matching kernel deals them out round-robin
-    std::stable_sort(items.begin(), items.end(), [&](const FwdItem &x, const FwdItem &y) {
-        return (long long)x.nq * om[x.obj].Mpad > (long long)y.nq * om[y.obj].Mpad;
-    });
 
     if (T != c->T) {
         c->theta_set = false;
@@ -257,7 +306,6 @@ void build_layout(asicp_ctx *c)
     }
     c->T = T;
     c->G = G;
-    c->n_items = (int)items.size();
     c->colidx_total = colidx_total;
     c->csum_total = csum_total;
     c->grp_off_h = off;
@@ -266,7 +314,6 @@ void build_layout(asicp_ctx *c)
     c->partgrp.ensure(sizeof(int) * T, "particle groups");
     c->grpoff.ensure(sizeof(int) * (G + 1), "group offsets");
     c->objmeta.ensure(sizeof(ObjMeta) * c->nobj, "object table");
-    c->items.ensure(sizeof(FwdItem) * std::max<size_t>(1, items.size()), "matching work items");
     c->theta.ensure(sizeof(float) * 8 * (size_t)T, "poses");
     c->fsums.ensure(sizeof(double) * T * kFwdSums, "fsums");
     c->csums.ensure(sizeof(double) * std::max<long long>(1, csum_total) * kColSums, "csums");
@@ -295,11 +342,9 @@ void build_layout(asicp_ctx *c)
     ck(cudaMemcpyAsync(c->grpoff.p, off.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, c->st), "group offsets");
     ck(cudaMemcpyAsync(c->objmeta.p, om.data(), sizeof(ObjMeta) * c->nobj, cudaMemcpyHostToDevice, c->st),
        "object table");
-    if (!items.empty())
-        ck(cudaMemcpyAsync(c->items.p, items.data(), sizeof(FwdItem) * items.size(), cudaMemcpyHostToDevice, c->st),
-           "work items");
     ck(cudaStreamSynchronize(c->st), "layout");
     c->layout_dirty = false;
+    plan_fwd_items(c, c->fwd_variant);
 }
 
 __global__ void reset_convergence_kernel(double *prev, int *frozen, float *phi, int T, int *col_items)
@@ -367,6 +412,7 @@ void iterate(asicp_ctx *c, int mode, float gamma)
     fa.S = c->S.as<float4>();
     fa.theta = c->theta.as<float>();
     fa.items = c->items.as<FwdItem>();
+    fa.cta_off = c->ctaoff.as<int>();
     fa.n_items = c->n_items;
     fa.err = c->errw.as<int>();
     fa.nn_idx = c->nnidx.as<int>();
@@ -443,7 +489,7 @@ void run_loop(asicp_ctx *c)
 // read at replay, so new objects of the same sizes reuse the graph).
 std::vector<const void *> loop_key(const asicp_ctx *c)
 {
-    return {c->partgrp.p, c->grpoff.p, c->objmeta.p, c->items.p, c->com.p, c->rmax.p, c->colitems.p, c->collist.p,
+    return {c->partgrp.p, c->grpoff.p, c->objmeta.p, c->items.p, c->ctaoff.p, c->com.p, c->rmax.p, c->colitems.p, c->collist.p,
             c->S.p, c->pconst.p, c->dmeta.p, c->theta.p, c->fsums.p, c->csums.p, c->ncol.p, c->colidx.p, c->cost.p,
             c->grad.p, c->prev.p, c->frozen.p, c->phi.p, c->h.p, c->order.p, c->errw.p, c->nnidx.p, c->dbg_d2.p,
             c->dbg_sp.p, c->dbg_colnn.p, reinterpret_cast<const void *>((size_t)c->T),
@@ -529,11 +575,13 @@ void autotune_impl(asicp_ctx *c, float *ms_out)
     float best = 0.f;
     int best_v = 0;
     for (int v = 0; v < kFwdVariants; ++v) {
+        plan_fwd_items(c, v);
         FwdArgs fa{};
         fa.L = c->layout();
         fa.S = c->S.as<float4>();
         fa.theta = c->theta.as<float>();
         fa.items = c->items.as<FwdItem>();
+        fa.cta_off = c->ctaoff.as<int>();
         fa.n_items = c->n_items;
         fa.err = c->errw.as<int>();
         fa.nn_idx = c->nnidx.as<int>();
@@ -553,6 +601,7 @@ void autotune_impl(asicp_ctx *c, float *ms_out)
     c->pool.push_back(e1);
     sync_and_check_err(c, "autotune");
     c->fwd_variant = best_v;
+    plan_fwd_items(c, best_v);
     c->tuned = true;
 }
 

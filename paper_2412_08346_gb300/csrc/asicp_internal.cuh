@@ -169,6 +169,7 @@ struct FwdArgs {
     const float4 *S;         // [P][N] gripper points (gripper frame)
     const float *theta;      // [T][8]
     const FwdItem *items;    // [n_items] work items (null: object 0, consecutive 1024-query items)
+    const int *cta_off;      // [grid + 1]: CTA b runs items cta_off[b] .. cta_off[b+1]-1 (null: round-robin)
     int n_items;
     int *err;                // error word
     int *nn_idx;             // [T][N] nearest object point per query
@@ -177,9 +178,12 @@ struct FwdArgs {
     int variant;             // kernel shape (0 .. kFwdVariants - 1), chosen by the autotuner
 };
 constexpr int kFwdItemQueries = 1024;  // queries per forward-matching work item
-constexpr int kFwdVariants = 4;        // kernel shapes of the forward matching
+constexpr int kFwdVariants = 7;        // kernel shapes of the forward matching
 cudaError_t launch_fwd_match(const FwdArgs &a, cudaStream_t st);
 int fwd_grid_size();                   // first call sets the kernels' attributes
+int fwd_shape_grid(int v);             // CTAs of kernel shape v (a whole number per SM)
+int fwd_shape_threads(int v);          // threads per CTA of kernel shape v
+int fwd_shape_queries(int v);          // queries per work item (at most) of kernel shape v
 const char *fwd_variant_name(int v);
 cudaError_t init_collision_attributes();
 cudaError_t init_update_attributes();

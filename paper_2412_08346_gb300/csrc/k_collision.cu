@@ -174,60 +174,76 @@ __device__ __forceinline__ float fmin3(float a, float b, float c)
     return d;
 }
 
-// Warp-wide exact nearest point (exact-form float32 distance, ties to the lowest
-// index) of query (x, y, z) among the points ref0 + stride k, k < nk (lanes take
-// k = lane, lane + 32, ...).
-__device__ __forceinline__ void warp_exact_argmin(const float4 *sS, int N, int ref0, int stride, int nk, float x,
-                                                  float y, float z, int lane, float &best, int &bi)
+// Total order of float32 values (no NaN) as unsigned keys, and back.
+__device__ __forceinline__ unsigned ord_key(float f)
 {
-    best = __int_as_float(0x7f800000);
-    bi = 0x7fffffff;
-    for (int k = lane; k < nk; k += 32) {
-        const int r = ref0 + stride * k;
-        if (r >= N) continue;
-        const float4 s = sS[r];
-        const float d = dist2_f32(s.x, s.y, s.z, x, y, z);
-        if (d < best || (d == best && r < bi)) { best = d; bi = r; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob < best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
+
+__device__ __forceinline__ float key_val(unsigned k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// (best, bi) <- the smaller of itself and the partner lane's, ties to the lower index.
+__device__ __forceinline__ void argmin_xor(float &best, int &bi, int o)
+{
+    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob < best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+}
+
+// Operands of the collision sums: sum index -> (a, b) as indices into a
+// colliding point's record {s_x, s_y, s_z, c_x, c_y, c_z, 1, 0}; sum 21 (|c|^2)
+// adds the three squares of c.
+__constant__ unsigned char kColSel[kColSums][2] = {
+    {0, 6}, {1, 6}, {2, 6},                                  // sum s
+    {0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2},          // sum s s^T (upper triangle)
+    {3, 6}, {4, 6}, {5, 6},                                  // sum c
+    {3, 0}, {3, 1}, {3, 2}, {4, 0}, {4, 1}, {4, 2}, {5, 0}, {5, 1}, {5, 2},   // sum c s^T
+    {3, 3}};                                                 // sum |c|^2
 }  // namespace
 
 // Persistent: CTAs take (particle, chunk of kColChunk colliding points) items
 // from the list the collision kernel filled.  Per item the particle's
-// transformed contact cloud S' is built in shared memory twice: exact (float4)
-// and in the screening layout (-2 s', |s'|^2), pairs of points interleaved so
-// that lane l owns the chunk of points l + 32 k.  Each warp matches kQW
-// colliding points c:
-//  1. screening: every lane evaluates d~ = |s'|^2 - 2 c.s' over its chunk
-//     (packed f32x2 FMAs, 3-input min); shuffles give the best chunk minimum b1
-//     (lane l1) and the best of the other chunks b2;
+// transformed contact cloud S' is built in shared memory twice, both arranged
+// by lane chunks (chunk l = points l + 32 k): in the screening layout
+// (-2 s', |s'|^2), point pairs (l + 64 m, l + 32 + 64 m) at slot 32 m + l, and
+// exact (float4), chunk l contiguous with a stride of KC + 1 (no bank
+// conflicts).  Each warp matches kQW colliding points c:
+//  1. screening: lane l evaluates d~ = |s'|^2 - 2 c.s' over chunk l (packed
+//     f32x2 FMAs, 3-input min); warp min-reductions give the best chunk minimum
+//     b1 (lane l1, the lowest on ties) and the best of the other chunks b2;
 //  2. exact choice: with delta = u (7 Smax^2 + 6.1 |c| Smax) bounding the error of
 //     d~ (Smax = max |s'|), the nearest point lies in chunk l1 unless b2 <= b1 +
-//     2 delta; the warp re-evaluates chunk l1 (or, in that rare case, the whole
-//     cloud) with the exact-form distance, ties to the lowest index.
-// The sums the collision cost and gradient are linear in are accumulated per item
-// (double-float, exact products):
+//     2 delta; four lanes per colliding point re-evaluate chunk l1 with the
+//     exact-form distance, ties to the lowest index; in the rare other case the
+//     warp scans the whole cloud that way.
+// The sums the collision cost and gradient are linear in are then accumulated
+// per item (double-float, exact products) by 8 threads per sum over 8
+// colliding points each, merged in a fixed tree:
 //   sum s (3), sum s s^T (xx,xy,xz,yy,yz,zz) (6), sum c (3), sum c s^T (9), sum |c|^2 (1)
 // with s the matched gripper point in the gripper frame; the finalize kernel adds
 // the chunks of a particle in chunk order, so the result does not depend on
 // which CTA took which item.
 __global__ void __launch_bounds__(kColThreads) collide_nn_kernel(const CollideArgs a)
 {
-    constexpr int kQW = kColChunk / (kColThreads / 32);     // colliding points per warp
+    constexpr int kWarps = kColThreads / 32;
+    constexpr int kQW = kColChunk / kWarps;                  // colliding points per warp
+    static_assert(kQW == 8 && kColChunk == 64, "lane groups of four per colliding point");
+    static_assert(kColSums * 8 <= kColThreads, "eight threads per sum");
     extern __shared__ __align__(16) unsigned char smem_nn[];
     const int N = a.L.N;
     const int Npad = (N + 63) / 64 * 64;
-    float4 *sS = reinterpret_cast<float4 *>(smem_nn);                          // [N] exact S'
-    ulonglong2 *sX = reinterpret_cast<ulonglong2 *>(smem_nn + sizeof(float4) * Npad);   // [Npad] screening
-    __shared__ double sred[kColThreads / 32][kColSums];
+    const int KC = Npad / 32, KCs = KC + 1;                  // points per lane chunk, exact-layout stride
+    ulonglong2 *sXA = reinterpret_cast<ulonglong2 *>(smem_nn);             // [Npad/2] {-2x pair}{-2y pair}
+    ulonglong2 *sXB = sXA + Npad / 2;                                      // [Npad/2] {-2z pair}{w pair}
+    float4 *sE = reinterpret_cast<float4 *>(sXB + Npad / 2);               // [32][KC + 1] exact S'
+    __shared__ float4 sC[kColChunk];                          // colliding points of the item
+    __shared__ float sRec[kColChunk][8];                      // {s, c, 1, 0} per matched colliding point
     __shared__ int s_item;
-    __shared__ float s_smax[kColThreads / 32];
+    __shared__ float s_smax[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int slots = Npad / 64;                 // point pairs per lane
     for (;;) {
@@ -240,23 +256,31 @@ __global__ void __launch_bounds__(kColThreads) collide_nn_kernel(const CollideAr
         const ObjMeta om = a.L.obj[grp / a.L.P];
         const int n = a.ncol[pk];
         const int *colidx = a.colidx + om.colidx_base + (long long)(pk - om.pfirst) * om.Mc;
+        const int l0 = chunk * kColChunk;
         const float *th = a.theta + (size_t)pk * 8;
         const float tx = th[0], ty = th[1], tz = th[2];
         float Rm[9];
         quat_rot_f32(th[3], th[4], th[5], th[6], Rm);
         const float4 *S = a.S + (size_t)p * N;
+        if (threadIdx.x < kColChunk) {
+            const int j = threadIdx.x;
+            float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (l0 + j < n) c = om.C[colidx[l0 + j]];
+            sC[j] = c;
+        }
         float smax2 = 0.f;
-        // pair (l + 64 m, l + 32 + 64 m) of lane l at screening slot m * 32 + l
         for (int q = threadIdx.x; q < Npad / 2; q += kColThreads) {
             const int l = q & 31, m = q >> 5;
             float ax[2], ay[2], az[2], w[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int r = l + 32 * h + 64 * m;
+                float4 e = make_float4(__int_as_float(0x7f800000), __int_as_float(0x7f800000),
+                                       __int_as_float(0x7f800000), 0.f);
                 if (r < N) {
                     const float4 sv = S[r];
                     const float3 o = xform_f32(Rm, tx, ty, tz, sv.x, sv.y, sv.z);
-                    sS[r] = make_float4(o.x, o.y, o.z, 0.f);
+                    e = make_float4(o.x, o.y, o.z, 0.f);
                     ax[h] = -2.f * o.x; ay[h] = -2.f * o.y; az[h] = -2.f * o.z;
                     w[h] = __fmaf_rn(o.x, o.x, __fmaf_rn(o.y, o.y, __fmul_rn(o.z, o.z)));
                     smax2 = fmaxf(smax2, w[h]);
@@ -264,34 +288,33 @@ __global__ void __launch_bounds__(kColThreads) collide_nn_kernel(const CollideAr
                     ax[h] = ay[h] = az[h] = 0.f;
                     w[h] = __int_as_float(0x7f800000);
                 }
+                sE[l * KCs + 2 * m + h] = e;
             }
             ulonglong2 A, B;
             A.x = pk2(ax[0], ax[1]); A.y = pk2(ay[0], ay[1]);
             B.x = pk2(az[0], az[1]); B.y = pk2(w[0], w[1]);
-            sX[2 * q] = A;
-            sX[2 * q + 1] = B;
+            sXA[q] = A;
+            sXB[q] = B;
         }
         for (int o = 16; o > 0; o >>= 1) smax2 = fmaxf(smax2, __shfl_xor_sync(0xffffffffu, smax2, o));
         if (lane == 0) s_smax[warp] = smax2;
         __syncthreads();
         float sm2 = 0.f;
-        for (int w8 = 0; w8 < kColThreads / 32; ++w8) sm2 = fmaxf(sm2, s_smax[w8]);
+        for (int w8 = 0; w8 < kWarps; ++w8) sm2 = fmaxf(sm2, s_smax[w8]);
         const float smax = sqrtf(sm2) * 1.0001f;
 
-        const int l0 = chunk * kColChunk + warp * kQW;
-        float cx[kQW], cy[kQW], cz[kQW], cm[kQW];
+        // 1. screening of this warp's colliding points, lane l over chunk l
         unsigned long long qx[kQW], qy[kQW], qz[kQW];
+        float cm[kQW];
 #pragma unroll
         for (int q = 0; q < kQW; ++q) {
-            float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (l0 + q < n) c = om.C[colidx[l0 + q]];
-            cx[q] = c.x; cy[q] = c.y; cz[q] = c.z;
+            const float4 c = sC[warp * kQW + q];
             qx[q] = pk2(c.x, c.x); qy[q] = pk2(c.y, c.y); qz[q] = pk2(c.z, c.z);
             cm[q] = __int_as_float(0x7f800000);
         }
         for (int m = 0; m < slots; ++m) {
-            const ulonglong2 A = sX[2 * (m * 32 + lane)];
-            const ulonglong2 B = sX[2 * (m * 32 + lane) + 1];
+            const ulonglong2 A = sXA[m * 32 + lane];
+            const ulonglong2 B = sXB[m * 32 + lane];
 #pragma unroll
             for (int q = 0; q < kQW; ++q) {
                 const unsigned long long d = ffma2(qx[q], A.x, ffma2(qy[q], A.y, ffma2(qz[q], B.x, B.y)));
@@ -300,47 +323,94 @@ __global__ void __launch_bounds__(kColThreads) collide_nn_kernel(const CollideAr
                 cm[q] = fmin3(cm[q], d0, d1);
             }
         }
-        dfloat acc[kColSums];
-#pragma unroll
-        for (int c = 0; c < kColSums; ++c) acc[c] = dfloat{0.f, 0.f};
+        // best chunk l1 (lowest lane on ties) and whether another chunk may hold the nearest point
+        const int g = lane >> 2, gs = lane & 3;       // lane group g works on colliding point g
+        int my_l1 = 0;
+        unsigned full_scan = 0u;
 #pragma unroll
         for (int q = 0; q < kQW; ++q) {
-            // best chunk (ties to the lower lane) and the best of the other chunks
-            float b1 = cm[q];
-            int l1 = lane;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, b1, o);
-                const int ol = __shfl_xor_sync(0xffffffffu, l1, o);
-                if (ob < b1 || (ob == b1 && ol < l1)) { b1 = ob; l1 = ol; }
-            }
-            float b2 = lane == l1 ? __int_as_float(0x7f800000) : cm[q];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) b2 = fminf(b2, __shfl_xor_sync(0xffffffffu, b2, o));
-            const float cn = sqrtf(cx[q] * cx[q] + cy[q] * cy[q] + cz[q] * cz[q]) * 1.001f;
+            const unsigned key = ord_key(cm[q]);
+            const unsigned k1 = __reduce_min_sync(0xffffffffu, key);
+            const int l1 = __ffs(__ballot_sync(0xffffffffu, key == k1)) - 1;
+            const unsigned k2 = __reduce_min_sync(0xffffffffu, lane == l1 ? 0xffffffffu : key);
+            const float4 c = sC[warp * kQW + q];
+            const float cn = sqrtf(c.x * c.x + c.y * c.y + c.z * c.z) * 1.001f;
             const float win = 2.02f * 5.9604645e-8f * (7.f * smax * smax + 6.1f * cn * smax);
-            float best;
-            int bi;
-            if (b2 <= b1 + win)      // another chunk may hold the nearest point: whole cloud
-                warp_exact_argmin(sS, N, 0, 1, N, cx[q], cy[q], cz[q], lane, best, bi);
-            else                     // chunk l1: points l1 + 32 k
-                warp_exact_argmin(sS, N, l1, 32, Npad / 32, cx[q], cy[q], cz[q], lane, best, bi);
-            if (lane != q || l0 + q >= n) continue;       // lane q records colliding point q
-            if (a.dbg_colnn) a.dbg_colnn[om.colidx_base + (long long)(pk - om.pfirst) * om.Mc + l0 + q] = bi;
-            const float4 s = S[bi];
-            const float sv[3] = {s.x, s.y, s.z}, cv[3] = {cx[q], cy[q], cz[q]};
-            acc[0] = dfloat{sv[0], 0.f}; acc[1] = dfloat{sv[1], 0.f}; acc[2] = dfloat{sv[2], 0.f};
-            df_add_prod(acc[3], sv[0], sv[0]); df_add_prod(acc[4], sv[0], sv[1]); df_add_prod(acc[5], sv[0], sv[2]);
-            df_add_prod(acc[6], sv[1], sv[1]); df_add_prod(acc[7], sv[1], sv[2]); df_add_prod(acc[8], sv[2], sv[2]);
-            acc[9] = dfloat{cv[0], 0.f}; acc[10] = dfloat{cv[1], 0.f}; acc[11] = dfloat{cv[2], 0.f};
-#pragma unroll
-            for (int u = 0; u < 3; ++u)
-#pragma unroll
-                for (int v = 0; v < 3; ++v) df_add_prod(acc[12 + 3 * u + v], cv[u], sv[v]);
-            df_add_prod(acc[21], cv[0], cv[0]); df_add_prod(acc[21], cv[1], cv[1]); df_add_prod(acc[21], cv[2], cv[2]);
+            if (key_val(k2) <= key_val(k1) + win) full_scan |= 1u << q;
+            if (g == q) my_l1 = l1;
         }
-        block_reduce_store<kColSums>(
-            acc, sred, a.csums + (om.csum_base + (long long)(pk - om.pfirst) * om.chunks + chunk) * kColSums);
+        // 2. exact choice: four lanes per colliding point over its chunk l1
+        const float4 cq = sC[warp * kQW + g];
+        float best = __int_as_float(0x7f800000);
+        int bi = 0x7fffffff;
+        for (int k = gs; k < KC; k += 4) {
+            const int r = my_l1 + 32 * k;
+            if (r >= N) break;
+            const float4 e = sE[my_l1 * KCs + k];
+            const float d = dist2_f32(e.x, e.y, e.z, cq.x, cq.y, cq.z);
+            if (d < best) { best = d; bi = r; }
+        }
+        argmin_xor(best, bi, 1);
+        argmin_xor(best, bi, 2);
+        if (bi >= N) bi = 0;     // no finite distance at all (not reached with finite inputs)
+        // rare: the whole cloud, lane l over chunk l
+        while (full_scan) {
+            const int q = __ffs(full_scan) - 1;
+            full_scan &= full_scan - 1;
+            const float4 c = sC[warp * kQW + q];
+            float fb = __int_as_float(0x7f800000);
+            int fi = 0x7fffffff;
+            for (int k = 0; k < KC; ++k) {
+                const int r = lane + 32 * k;
+                if (r >= N) break;
+                const float4 e = sE[lane * KCs + k];
+                const float d = dist2_f32(e.x, e.y, e.z, c.x, c.y, c.z);
+                if (d < fb) { fb = d; fi = r; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) argmin_xor(fb, fi, o);
+            if (g == q) { best = fb; bi = fi < N ? fi : 0; }
+        }
+        if (gs == 0) {
+            const int j = warp * kQW + g;
+            const bool valid = l0 + j < n;
+            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (valid) {
+                s = S[bi];
+                if (a.dbg_colnn) a.dbg_colnn[om.colidx_base + (long long)(pk - om.pfirst) * om.Mc + l0 + j] = bi;
+            }
+            sRec[j][0] = s.x; sRec[j][1] = s.y; sRec[j][2] = s.z;
+            sRec[j][3] = valid ? cq.x : 0.f; sRec[j][4] = valid ? cq.y : 0.f; sRec[j][5] = valid ? cq.z : 0.f;
+            sRec[j][6] = valid ? 1.f : 0.f; sRec[j][7] = 0.f;
+        }
+        __syncthreads();
+        // 3. the item's sums: thread (sum e, part) adds colliding points part + 8 u, u = 0 .. 7
+        if (threadIdx.x < (kColSums * 8 + 31) / 32 * 32) {
+            const int e = threadIdx.x >> 3, part = threadIdx.x & 7;
+            dfloat acc{0.f, 0.f};
+            if (e < kColSums) {
+                const int ia = kColSel[e][0], ib = kColSel[e][1];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float *rec = sRec[part + 8 * u];
+                    df_add_prod(acc, rec[ia], rec[ib]);
+                    if (e == kColSums - 1) {
+                        df_add_prod(acc, rec[4], rec[4]);
+                        df_add_prod(acc, rec[5], rec[5]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                dfloat y;
+                y.hi = __shfl_xor_sync(0xffffffffu, acc.hi, o);
+                y.lo = __shfl_xor_sync(0xffffffffu, acc.lo, o);
+                df_merge(acc, y);
+            }
+            if (part == 0 && e < kColSums)
+                a.csums[(om.csum_base + (long long)(pk - om.pfirst) * om.chunks + chunk) * kColSums + e] =
+                    (double)acc.hi + (double)acc.lo;
+        }
         __syncthreads();   // shared buffers and s_item are reused by the next item
     }
 }
@@ -354,7 +424,7 @@ cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st)
 cudaError_t init_collision_attributes()
 {
     return cudaFuncSetAttribute(collide_nn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(2 * sizeof(float4) * kMaxN));
+                                (int)(2 * sizeof(float4) * kMaxN + 32 * sizeof(float4)));
 }
 
 cudaError_t launch_collide_nn(const CollideArgs &a, cudaStream_t st)
@@ -366,7 +436,7 @@ cudaError_t launch_collide_nn(const CollideArgs &a, cudaStream_t st)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         grid = 4 * sms;
     }
-    const size_t smem = 2 * sizeof(float4) * (size_t)((a.L.N + 63) / 64 * 64);
+    const size_t smem = 2 * sizeof(float4) * (size_t)((a.L.N + 63) / 64 * 64) + 32 * sizeof(float4);
     collide_nn_kernel<<<grid, kColThreads, smem, st>>>(a);
     return cudaGetLastError();
 }

@@ -37,15 +37,18 @@ namespace asicp {
 
 namespace {
 
-constexpr int kTile = kRefTilePts;       // object points per shared-memory tile
-
-// Kernel shapes the autotuner chooses from: (queries per thread, screening chunk,
-// threads per CTA); every shape holds kFwdItemQueries queries per work item.
-template <int QPT_, int CHUNK_>
+// Kernel shapes the autotuner chooses from: queries per thread, screening
+// chunk, threads per CTA, object points per shared-memory tile (two buffers),
+// and the CTAs per SM the register budget is set for.
+template <int QPT_, int CHUNK_, int THREADS_, int TILE_, int MINB_>
 struct FwdShape {
     static constexpr int QPT = QPT_;
     static constexpr int kChunk = CHUNK_;
-    static constexpr int kThreads = kFwdItemQueries / QPT_;
+    static constexpr int kThreads = THREADS_;
+    static constexpr int kTile = TILE_;
+    static constexpr int kMinBlocks = MINB_;
+    static constexpr int kItem = QPT_ * THREADS_;     // queries per work item at most
+    static_assert(kItem <= kFwdItemQueries && kRefTilePts % TILE_ == 0 && TILE_ % CHUNK_ == 0, "shape");
 };
 constexpr long long kWaitCycles = 1LL << 32;   // bounded mbarrier wait (~2 s)
 
@@ -142,7 +145,7 @@ template <class Shape, int Q>
 __device__ __forceinline__ bool match_pass(const FwdArgs &a, const ObjMeta &om, float rmax, long long q0, int nq,
                                            ulonglong2 *tiles, unsigned long long *full, int &seq, int *s_abort)
 {
-    constexpr int kThreads = Shape::kThreads, kChunk = Shape::kChunk;
+    constexpr int kThreads = Shape::kThreads, kChunk = Shape::kChunk, kTile = Shape::kTile;
     const int ntiles = om.Mpad / kTile;
     const unsigned tile_bytes = kTile * 16u;
     if (threadIdx.x == 0) {    // both buffers are free: the previous pass ended with a barrier
@@ -249,19 +252,35 @@ __device__ __forceinline__ bool match_pass(const FwdArgs &a, const ObjMeta &om, 
     return true;
 }
 
-// Persistent: CTA b takes work items b, b + gridDim.x, ... (listed longest
-// first when objects differ, so the tail is short); an item is at most
-// kThreads * QPT queries of one object, and a partial item uses the smallest
-// queries-per-thread instantiation that covers it.
+// match_pass with the smallest queries-per-thread count Q >= qn (Q <= QMAX).
+template <class Shape, int QMAX>
+__device__ __forceinline__ bool dispatch_pass(int qn, const FwdArgs &a, const ObjMeta &om, float rmax, long long q0,
+                                              int nq, ulonglong2 *tiles, unsigned long long *full, int &seq,
+                                              int *s_abort)
+{
+    if constexpr (QMAX > 1) {
+        if (qn < QMAX) return dispatch_pass<Shape, QMAX - 1>(qn, a, om, rmax, q0, nq, tiles, full, seq, s_abort);
+    }
+    return match_pass<Shape, QMAX>(a, om, rmax, q0, nq, tiles, full, seq, s_abort);
+}
+
+// Persistent: CTA b runs the work items the host planned for it
+// (cta_off[b] .. cta_off[b + 1] - 1, balanced by their cost), or without a plan
+// items b, b + gridDim.x, ...; an item is at most kThreads * QPT queries of one
+// object, and a partial item uses the smallest queries-per-thread
+// instantiation that covers it.
 template <class Shape>
-__global__ void __launch_bounds__(Shape::kThreads, 3 * 128 / Shape::kThreads) fwd_match_kernel(const FwdArgs a)
+__global__ void __launch_bounds__(Shape::kThreads, Shape::kMinBlocks) fwd_match_kernel(const FwdArgs a)
 {
     constexpr int kThreads = Shape::kThreads;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     ulonglong2 *tiles = reinterpret_cast<ulonglong2 *>(smem_raw);
     __shared__ __align__(8) unsigned long long full[2];
     __shared__ int s_abort;
-    if (blockIdx.x >= a.n_items) return;
+    const int it0 = a.cta_off ? a.cta_off[blockIdx.x] : blockIdx.x;
+    const int it1 = a.cta_off ? a.cta_off[blockIdx.x + 1] : a.n_items;
+    const int step = a.cta_off ? 1 : gridDim.x;
+    if (it0 >= it1) return;
     if (threadIdx.x == 0) {
         s_abort = 0;
         mbar_init(&full[0], 1);
@@ -272,91 +291,107 @@ __global__ void __launch_bounds__(Shape::kThreads, 3 * 128 / Shape::kThreads) fw
     const long long Qtot = (long long)a.L.T * a.L.N;
     int seq = 0;
     bool ok = true;
-    for (int it = blockIdx.x; it < a.n_items && ok; it += gridDim.x) {
+    for (int it = it0; it < it1 && ok; it += step) {
         FwdItem item;
         if (a.items) {
             item = a.items[it];
         } else {
-            item.q0 = (long long)it * kFwdItemQueries;
-            item.nq = (int)(Qtot - item.q0 < kFwdItemQueries ? Qtot - item.q0 : kFwdItemQueries);
+            item.q0 = (long long)it * Shape::kItem;
+            item.nq = (int)(Qtot - item.q0 < Shape::kItem ? Qtot - item.q0 : Shape::kItem);
             item.obj = 0;
         }
         const ObjMeta om = a.L.obj[item.obj];
         const float rmax = a.L.rmax[item.obj];
         const int qn = (item.nq + kThreads - 1) / kThreads;
-        if (Shape::QPT == 8) {
-            switch (qn) {
-                case 1: ok = match_pass<Shape, 1>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-                case 2: ok = match_pass<Shape, 2>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-                case 3: ok = match_pass<Shape, 3>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-                case 4: ok = match_pass<Shape, 4>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-                case 5: ok = match_pass<Shape, 5>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-                case 6: ok = match_pass<Shape, 6>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-                case 7: ok = match_pass<Shape, 7>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-                default: ok = match_pass<Shape, 8>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-            }
-        } else {   // QPT 4
-            switch (qn) {
-                case 1: ok = match_pass<Shape, 1>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-                case 2: ok = match_pass<Shape, 2>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-                case 3: ok = match_pass<Shape, 3>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-                default: ok = match_pass<Shape, 4>(a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort); break;
-            }
-        }
+        ok = dispatch_pass<Shape, Shape::QPT>(qn, a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort);
     }
     if (!ok && threadIdx.x == 0)   // drain copies still in flight (bounded) before leaving
         for (int b = 0; b < 2; ++b) mbar_wait(&full[(seq + b) & 1], (unsigned)((seq + b) >> 1) & 1u);
 }
 
-using Shape0 = FwdShape<8, 64>;   // 128 threads
-using Shape1 = FwdShape<8, 32>;
-using Shape2 = FwdShape<4, 64>;   // 256 threads
-using Shape3 = FwdShape<4, 32>;
+using Shape0 = FwdShape<8, 64, 128, 2048, 3>;
+using Shape1 = FwdShape<8, 32, 128, 2048, 3>;
+using Shape2 = FwdShape<4, 64, 256, 2048, 2>;
+using Shape3 = FwdShape<4, 32, 256, 2048, 2>;
+using Shape4 = FwdShape<4, 64, 128, 1024, 5>;
+using Shape5 = FwdShape<8, 64, 128, 1024, 4>;
+using Shape6 = FwdShape<6, 64, 128, 1024, 4>;
 
 template <class Shape>
 int shape_grid()
 {
     static int grid = 0;
     if (grid == 0) {
+        const int smem = 2 * Shape::kTile * 16;
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(fwd_match_kernel<Shape>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kTile * 16);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_match_kernel<Shape>, Shape::kThreads,
-                                                      2 * kTile * 16);
+        cudaFuncSetAttribute(fwd_match_kernel<Shape>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_match_kernel<Shape>, Shape::kThreads, smem);
         grid = sms * (per_sm > 0 ? per_sm : 1);
     }
     return grid;
 }
 
-int fwd_grid_size()
-{
-    return shape_grid<Shape0>() + shape_grid<Shape1>() + shape_grid<Shape2>() + shape_grid<Shape3>();
-}
-
-const char *fwd_variant_name(int v)
-{
-    static const char *names[kFwdVariants] = {"qpt8-chunk64", "qpt8-chunk32", "qpt4-chunk64", "qpt4-chunk32"};
-    return (v >= 0 && v < kFwdVariants) ? names[v] : "unknown";
-}
-
 template <class Shape>
 cudaError_t launch_shape(const FwdArgs &a, cudaStream_t st)
 {
-    static_assert(kFwdItemQueries == Shape::kThreads * Shape::QPT, "work items hold kThreads * QPT queries");
-    const size_t smem = 2 * (size_t)kTile * 16;
+    const size_t smem = 2 * (size_t)Shape::kTile * 16;
     fwd_match_kernel<Shape><<<shape_grid<Shape>(), Shape::kThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
+// Apply f to the shape with index v (a default-constructed Shape tag).
+template <class F>
+auto with_shape(int v, F &&f)
+{
+    switch (v) {
+        case 1: return f(Shape1{});
+        case 2: return f(Shape2{});
+        case 3: return f(Shape3{});
+        case 4: return f(Shape4{});
+        case 5: return f(Shape5{});
+        case 6: return f(Shape6{});
+        default: return f(Shape0{});
+    }
+}
+static_assert(kFwdVariants == 7, "shape table");
+static_assert(Shape0::kItem == kFwdItemQueries, "unplanned launches use shape 0's items");
+
+int fwd_shape_grid(int v)
+{
+    return with_shape(v, [](auto sh) { return shape_grid<decltype(sh)>(); });
+}
+
+int fwd_shape_threads(int v)
+{
+    return with_shape(v, [](auto sh) { return decltype(sh)::kThreads; });
+}
+
+int fwd_shape_queries(int v)
+{
+    return with_shape(v, [](auto sh) { return decltype(sh)::kItem; });
+}
+
+int fwd_grid_size()
+{
+    int total = 0;
+    for (int v = 0; v < kFwdVariants; ++v) total += fwd_shape_grid(v);
+    return total;
+}
+
+const char *fwd_variant_name(int v)
+{
+    static const char *names[kFwdVariants] = {"qpt8-chunk64-t128-tile2048", "qpt8-chunk32-t128-tile2048",
+                                              "qpt4-chunk64-t256-tile2048", "qpt4-chunk32-t256-tile2048",
+                                              "qpt4-chunk64-t128-tile1024", "qpt8-chunk64-t128-tile1024",
+                                              "qpt6-chunk64-t128-tile1024"};
+    return (v >= 0 && v < kFwdVariants) ? names[v] : "unknown";
+}
+
 cudaError_t launch_fwd_match(const FwdArgs &a, cudaStream_t st)
 {
-    switch (a.variant) {
-        case 1: return launch_shape<Shape1>(a, st);
-        case 2: return launch_shape<Shape2>(a, st);
-        case 3: return launch_shape<Shape3>(a, st);
-        default: return launch_shape<Shape0>(a, st);
-    }
+    return with_shape(a.variant, [&](auto sh) { return launch_shape<decltype(sh)>(a, st); });
 }
 
 // Reference preparation for the screening stage: pair layout of (-2 r, |r|^2)
@@ -381,13 +416,13 @@ __global__ void ref_prep_kernel(const float4 *R, int M, int Mpad, ulonglong2 *Rx
                 w[k] = __int_as_float(0x7f800000);
             }
         }
-        // pair layout within a tile: tile-local pair index q' -> {A, B} at 2 q', 2 q' + 1
-        const int tile = (2 * q) / kTile, ql = q - tile * (kTile / 2);
+        // pair layout: point pair q -> {A, B} at 2 q, 2 q + 1 (any tile of an even
+        // number of points is a contiguous range)
         ulonglong2 A, B;
         A.x = pack2(ax[0], ax[1]); A.y = pack2(ay[0], ay[1]);
         B.x = pack2(az[0], az[1]); B.y = pack2(w[0], w[1]);
-        Rx[(size_t)tile * kTile + 2 * ql] = A;
-        Rx[(size_t)tile * kTile + 2 * ql + 1] = B;
+        Rx[2 * (size_t)q] = A;
+        Rx[2 * (size_t)q + 1] = B;
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
