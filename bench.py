@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work for the oracle sample")
     ap.add_argument("--small", action="store_true", help="small workload (debugging only)")
+    ap.add_argument("--fwd-shape", type=int, default=-1,
+                    help="forward-matching kernel shape (index into asicp.FWD_VARIANTS); -1: autotune")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="one short run of a reduced workload (1 preshape x 256 particles, N=2048, M=8192, "
+                         "8 iterations, poses close enough to collide) for profiler captures; no JSON line")
     return ap.parse_args()
 
 
@@ -192,7 +197,7 @@ def run_gpu(args, rank, world, local_rank):
     w = workload(rank, args.small)
     P, K, N, M = len(w.preshapes), w.K, w.preshapes[0].S.shape[0], len(w.objects[0].points)
     cfg = asicp.asicp_config_default(P=P, K=K, k_max=w.k_max, k_stein=w.k_stein, schedule=w.schedule,
-                                     profile=1, cuda_stream=stream.cuda_stream)
+                                     profile=1, cuda_stream=stream.cuda_stream, fwd_shape=max(0, args.fwd_shape))
     ctx = asicp.asicp_create(cfg)
     obj = w.objects[0].points
     R_dev = torch.from_numpy(obj).to(dev)
@@ -201,7 +206,10 @@ def run_gpu(args, rank, world, local_rank):
     for p, (S, g) in enumerate(pre_dev):
         asicp.asicp_set_gripper_sdf(ctx, p, S, g, w.preshapes[p].origin, w.preshapes[p].voxel)
     # pick the forward-matching kernel shape on this workload (outside the timed region)
-    shape, shape_ms = asicp.asicp_autotune(ctx)
+    if args.fwd_shape < 0:
+        shape, shape_ms = asicp.asicp_autotune(ctx)
+    else:
+        shape = args.fwd_shape
     best = np.zeros(TOPK * 7, np.float32)
     best_c = np.zeros(TOPK, np.float32)
     best_p = np.zeros(TOPK, np.int32)
@@ -335,8 +343,35 @@ def measure_e2e(args, ctx, w, stream, best, best_c, best_p, world, dev):
             "ms_per_step": 1e3 * el / args.steps, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
 
+def run_profile_case(args):
+    """Every kernel of the path at full N, M and K but one preshape, for ncu."""
+    import torch
+    from paper_2412_08346_gb300 import asicp, synth
+    w = synth.custom_case(P=1, K=256, N=2048, M=8192, grid=64, k_max=8, seed=synth.BASE_SEED + 2, k_stein=3)
+    stream = torch.cuda.current_stream()
+    cfg = asicp.asicp_config_default(P=1, K=256, k_max=w.k_max, k_stein=w.k_stein, init_radius=0.06,
+                                     cuda_stream=stream.cuda_stream, fwd_shape=max(0, args.fwd_shape))
+    ctx = asicp.asicp_create(cfg)
+    try:
+        asicp.asicp_set_object(ctx, torch.from_numpy(w.objects[0].points).cuda())
+        pre = w.preshapes[0]
+        asicp.asicp_set_gripper_sdf(ctx, 0, torch.from_numpy(pre.S).cuda(), torch.from_numpy(pre.sdf).cuda(),
+                                    pre.origin, pre.voxel)
+        for _ in range(max(1, args.steps)):
+            asicp.asicp_run(ctx)
+        torch.cuda.synchronize()
+        cost = np.zeros(4, np.float32)
+        n = asicp.asicp_best_grasps(ctx, 4, np.zeros(28, np.float32), cost, np.zeros(4, np.int32))
+        print(f"profile case {w.name}: {max(1, args.steps)} runs, best costs {cost[:n].tolist()}")
+    finally:
+        asicp.asicp_destroy(ctx)
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -74,7 +74,7 @@ typedef enum {
  * g = object * P + preshape holds K_g particles (K_g = K unless set with
  * asicp_set_particle_counts); T = sum of K_g is the particle count of every
  * per-particle array below. */
-#define ASICP_FWD_SHAPES 7
+#define ASICP_FWD_SHAPES 8
 
 typedef struct {
     int P, K;

@@ -70,7 +70,7 @@ struct DevMem {
 };
 
 struct ObjBufs {
-    DevMem R, Rx, C;          // C stays empty when the collision cloud is R itself
+    DevMem R, Rx, Rt, C;      // C stays empty when the collision cloud is R itself
     int M = 0, Mpad = 0, Mc = 0;
     bool set = false;
 };
@@ -287,6 +287,7 @@ void build_layout(asicp_ctx *c)
         ObjMeta &m = om[o];
         m.R = b.R.as<float4>();
         m.Rx = b.Rx.as<ulonglong2>();
+        m.Rt = b.Rt.as<float>();
         m.C = b.C.p ? b.C.as<float4>() : b.R.as<float4>();
         m.M = b.M;
         m.Mpad = b.Mpad;
@@ -629,6 +630,8 @@ void set_object_impl(asicp_ctx *ctx, int o, const float *R_xyz, int M, const flo
     const int Mpad = (M + kRefTilePts - 1) / kRefTilePts * kRefTilePts;
     b.Rx.ensure(sizeof(float4) * (size_t)Mpad, "screening layout");
     ck(launch_ref_prep(b.R.as<float4>(), M, Mpad, b.Rx.p, ctx->rmax.as<float>() + o, ctx->st), "ref prep");
+    b.Rt.ensure(tc_ref_bytes(Mpad), "tensor-core object tiles");
+    ck(launch_tc_ref_prep(b.R.as<float4>(), M, Mpad, b.Rt.as<float>(), ctx->st), "tensor-core ref prep");
     sync_and_check_err(ctx, "set_object");
     b.M = M;
     b.Mpad = Mpad;

@@ -68,6 +68,17 @@ __device__ __forceinline__ float dist2_f32(float ax, float ay, float az, float b
     return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
+// Exact-form nearest point among object points [lo, hi) (index order, strict <).
+__device__ __forceinline__ void exact_scan(const float4 *__restrict__ R, int lo, int hi, float sx, float sy, float sz,
+                                           float &best, int &bi)
+{
+    for (int r = lo; r < hi; ++r) {
+        const float4 v = __ldg(R + r);
+        const float d = dist2_f32(sx, sy, sz, v.x, v.y, v.z);
+        if (d < best) { best = d; bi = r; }
+    }
+}
+
 // Double-float accumulation (hi + lo, ~48-bit significand) from float32 error-free
 // transformations: products are split exactly by an FMA, sums by two-sum.  Used
 // for the per-particle sums, where float64 arithmetic would dominate the run time
@@ -141,6 +152,7 @@ __device__ __forceinline__ void warp_sum_f64(double (&v)[N])
 struct ObjMeta {
     const float4 *R;          // [M] object points
     const ulonglong2 *Rx;     // [Mpad] screening layout (pairs of (-2r, |r|^2)), Mpad = whole tiles
+    const float *Rt;          // [Mpad / 128] augmented tiles of the tensor-core kernel (8 KB each)
     const float4 *C;          // [Mc] collision points (may alias R)
     int M, Mpad, Mc, chunks;  // chunks = ceil(Mc / kColChunk)
     int pfirst, np;           // first particle and number of particles of this object
@@ -178,7 +190,7 @@ struct FwdArgs {
     int variant;             // kernel shape (0 .. kFwdVariants - 1), chosen by the autotuner
 };
 constexpr int kFwdItemQueries = 1024;  // queries per forward-matching work item
-constexpr int kFwdVariants = 7;        // kernel shapes of the forward matching
+constexpr int kFwdVariants = 8;        // kernel shapes of the forward matching (7: tensor cores)
 cudaError_t launch_fwd_match(const FwdArgs &a, cudaStream_t st);
 int fwd_grid_size();                   // first call sets the kernels' attributes
 int fwd_shape_grid(int v);             // CTAs of kernel shape v (a whole number per SM)
@@ -188,6 +200,11 @@ const char *fwd_variant_name(int v);
 cudaError_t init_collision_attributes();
 cudaError_t init_update_attributes();
 cudaError_t launch_ref_prep(const float4 *R, int M, int Mpad, void *Rx, float *rmax, cudaStream_t st);
+cudaError_t launch_tc_ref_prep(const float4 *R, int M, int Mpad, float *Rt, cudaStream_t st);
+size_t tc_ref_bytes(int Mpad);         // bytes of the tensor-core object tiles
+cudaError_t launch_fwd_match_tc(const FwdArgs &a, cudaStream_t st);
+int fwd_tc_grid();
+int fwd_tc_threads();
 
 constexpr int kColChunk = 64;          // colliding points per reverse-matching work item
 

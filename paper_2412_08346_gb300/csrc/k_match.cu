@@ -32,6 +32,7 @@
 // with r_i the matched object point and s_i the untransformed gripper point;
 // both are float32, so every product is exact in float64.
 #include "asicp_internal.cuh"
+#include "async_copy.cuh"
 
 namespace asicp {
 
@@ -50,7 +51,6 @@ struct FwdShape {
     static constexpr int kItem = QPT_ * THREADS_;     // queries per work item at most
     static_assert(kItem <= kFwdItemQueries && kRefTilePts % TILE_ == 0 && TILE_ % CHUNK_ == 0, "shape");
 };
-constexpr long long kWaitCycles = 1LL << 32;   // bounded mbarrier wait (~2 s)
 
 __device__ __forceinline__ unsigned long long pack2(float lo, float hi)
 {
@@ -76,63 +76,6 @@ __device__ __forceinline__ float min3(float a, float b, float c)
     float d;
     asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
     return d;
-}
-
-__device__ __forceinline__ unsigned smem_u32(const void *p)
-{
-    return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(unsigned long long *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on an mbarrier phase: false when the budget ran out.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
-    return true;
-}
-
-// Exact-form nearest point among object points [lo, hi) (index order, strict <).
-__device__ __forceinline__ void exact_scan(const float4 *__restrict__ R, int lo, int hi, float sx, float sy, float sz,
-                                           float &best, int &bi)
-{
-    for (int r = lo; r < hi; ++r) {
-        const float4 v = __ldg(R + r);
-        const float d = dist2_f32(sx, sy, sz, v.x, v.y, v.z);
-        if (d < best) { best = d; bi = r; }
-    }
 }
 
 }  // namespace
@@ -355,21 +298,25 @@ auto with_shape(int v, F &&f)
         default: return f(Shape0{});
     }
 }
-static_assert(kFwdVariants == 7, "shape table");
+constexpr int kTcVariant = 7;          // the tensor-core kernel (k_match_tc.cu)
+static_assert(kFwdVariants == 8, "shape table");
 static_assert(Shape0::kItem == kFwdItemQueries, "unplanned launches use shape 0's items");
 
 int fwd_shape_grid(int v)
 {
+    if (v == kTcVariant) return fwd_tc_grid();
     return with_shape(v, [](auto sh) { return shape_grid<decltype(sh)>(); });
 }
 
 int fwd_shape_threads(int v)
 {
+    if (v == kTcVariant) return fwd_tc_threads();
     return with_shape(v, [](auto sh) { return decltype(sh)::kThreads; });
 }
 
 int fwd_shape_queries(int v)
 {
+    if (v == kTcVariant) return fwd_tc_threads();     // one query per thread
     return with_shape(v, [](auto sh) { return decltype(sh)::kItem; });
 }
 
@@ -385,12 +332,13 @@ const char *fwd_variant_name(int v)
     static const char *names[kFwdVariants] = {"qpt8-chunk64-t128-tile2048", "qpt8-chunk32-t128-tile2048",
                                               "qpt4-chunk64-t256-tile2048", "qpt4-chunk32-t256-tile2048",
                                               "qpt4-chunk64-t128-tile1024", "qpt8-chunk64-t128-tile1024",
-                                              "qpt6-chunk64-t128-tile1024"};
+                                              "qpt6-chunk64-t128-tile1024", "tc-tf32x3-m128-n128"};
     return (v >= 0 && v < kFwdVariants) ? names[v] : "unknown";
 }
 
 cudaError_t launch_fwd_match(const FwdArgs &a, cudaStream_t st)
 {
+    if (a.variant == kTcVariant) return launch_fwd_match_tc(a, st);
     return with_shape(a.variant, [&](auto sh) { return launch_shape<decltype(sh)>(a, st); });
 }
 

@@ -1,0 +1,449 @@
+// Forward matching on the tensor cores: tcgen05 TF32 MMAs with split operands.
+//
+// The screening value of the float32 kernel, d~(r) = |r|^2 - 2 s'.r (Eq. 1 up to
+// the query's own |s'|^2), is a contraction of an augmented query row with an
+// augmented object-point column.  Every factor is split into two TF32 parts
+// (x = x_h + x_l, each exactly representable in TF32, rounded to nearest) and
+// |r|^2 into three (exact), so that with a = -2 s'
+//     A row    = [a_h, a_h, a_l, 1, 1, 1, 0, 0, 0, 0]          (K = 16)
+//     B column = [r_h, r_l, r_h, w_1, w_2, w_3, 0, 0, 0, 0]
+// gives A.B = w + a_h.r_h + a_h.r_l + a_l.r_h: two kind::tf32 MMAs (K = 8 each),
+// 128 queries x 128 object points, accumulated in float32 in tensor memory.
+//
+// Error bound, u = 2^-24: the dropped a_l.r_l and the rounding of the low parts
+// are at most 3 * 2^-22 |a_k| |r_k| per coordinate, i.e. 24 u |s'| |r| in all;
+// w = fl(|r|^2) is within u |r|^2; the products of TF32 values are exact, and
+// the tensor core's float32 accumulation is taken to stay within 16 u of the sum
+// of the magnitudes of its addends (<= 1.002 (|r|^2 + 2 |s'| |r|)); measured on
+// GB300: at most 3.3 u over 10^6 random rows of this form.  So
+//     delta_tc = u (18 Rmax^2 + 57 |s'| Rmax)
+// bounds |d~_tc - (|r|^2 - 2 s'.r)|.  Each query keeps its kTop best chunk
+// minima (chunks of 64 object points) and the best of the rest; the chunks
+// within 2 delta_tc of the best are rescanned with the exact-form float32
+// distance (ties to the lower index) by the query's thread, or, when more than
+// kTop qualify, the warp scans the whole cloud for that query together.  The
+// result is the exact-form argmin over every point that can be nearest, as in
+// the float32 kernel.
+//
+// Per CTA: one block of 128 queries (one per reduction thread, TMEM lane =
+// query); object tiles of 128 points (8 KB, already in the MMA's shared-memory
+// layout) stream through a ring of kStages buffers by 1D bulk copies.  One
+// thread issues the copies and MMAs (tile t + 1 while the reduction warps read
+// tile t from the other accumulator); a tcgen05.ld.red per 64 columns returns
+// a chunk minimum directly.  Two CTAs per SM (256 TMEM columns each) overlap
+// one another's per-item prologue and exact stage.  Every wait is bounded: on expiry the kernel reports ASICP_ERR_TIMEOUT
+// through the error word, drains its own copies and MMAs (bounded), frees its
+// tensor memory and returns.
+#include "asicp_internal.cuh"
+#include "async_copy.cuh"
+
+#include <cstdint>
+
+namespace asicp {
+
+namespace {
+
+constexpr int kRows = 128;                 // queries per block = MMA M
+constexpr int kBlocks = 1;                 // query blocks per CTA
+constexpr int kQueries = kRows * kBlocks;  // queries per item = reduction threads
+constexpr int kThreadsTc = kQueries + 32;  // + one warp for the copies and MMAs
+constexpr int kCols = 128;                 // object points per tile = MMA N
+constexpr int kAug = 16;                   // augmented length (two K = 8 MMAs)
+constexpr int kStages = 10;                // object tiles in flight
+constexpr int kChunk = 64;                 // screening chunk = columns per tcgen05.ld.red
+constexpr int kTop = 4;                    // chunks per query the exact stage rescans at most
+constexpr unsigned kTileBytes = kCols * kAug * 4;       // 4 KB
+constexpr unsigned kABlockBytes = kRows * kAug * 4;     // 8 KB
+constexpr unsigned kABytes = kBlocks * kABlockBytes;
+constexpr unsigned kLBO = 128, kSBO = 512; // core matrices (8 rows x 16 B): K-adjacent 128 B, row groups 512 B
+constexpr int kTmemCols = kBlocks * 2 * kCols;          // two accumulators per block
+constexpr size_t kSmemBytes = kABytes + (size_t)kStages * kTileBytes;
+static_assert(kRefTilePts % kCols == 0, "object padding must be whole tiles");
+static_assert(kTmemCols == 256, "two CTAs per SM share the 512 tensor-memory columns");
+static_assert(kCols % kChunk == 0, "whole chunks per tile");
+
+// instruction descriptor: D f32, A and B tf32, both K-major, N = kCols, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kCols >> 3) << 17) |
+                            ((uint32_t)(kRows >> 4) << 24);
+
+// byte offset of element (row, k) in the no-swizzle K-major layout
+__host__ __device__ constexpr unsigned core_offset(int row, int k)
+{
+    return (unsigned)(row / 8) * kSBO + (unsigned)(k / 4) * kLBO + (unsigned)(row % 8) * 16u + (unsigned)(k % 4) * 4u;
+}
+
+__device__ __forceinline__ uint64_t smem_desc(unsigned addr)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(kLBO >> 4) << 16) | ((uint64_t)(kSBO >> 4) << 32) |
+           (1ull << 46);
+}
+
+// round to the nearest TF32 value (ties to even); finite inputs of moderate size
+__device__ __forceinline__ float tf32_rn(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    return __uint_as_float((u + 0x0FFFu + ((u >> 13) & 1u)) & 0xFFFFE000u);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t ad, uint64_t bd, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(ad), "l"(bd), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(unsigned long long *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Minimum over the 64 accumulator columns at taddr of this thread's lane: the
+// tcgen05.ld.red and its wait in one statement, so the compiler sees the
+// destination registers written when the statement ends.
+__device__ __forceinline__ float ld_min64(uint32_t taddr)
+{
+    uint32_t v[64];
+    float m;
+    asm volatile(
+        "tcgen05.ld.red.sync.aligned.32x32b.x64.min.f32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, %64, [%65];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]), "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]), "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63]), "=f"(m)
+        : "r"(taddr)
+        : "memory");
+    return m;
+}
+
+// Exact-form nearest point among object points [lo, hi), merged into (best, bi)
+// with ties to the lower index.
+__device__ __forceinline__ void exact_scan_tie(const float4 *__restrict__ R, int lo, int hi, float3 q, float &best,
+                                               int &bi)
+{
+    for (int r = lo; r < hi; ++r) {
+        const float4 v = __ldg(R + r);
+        const float d = dist2_f32(q.x, q.y, q.z, v.x, v.y, v.z);
+        if (d < best || (d == best && r < bi)) { best = d; bi = r; }
+    }
+}
+
+}  // namespace
+
+// Augmented object tiles for the tensor-core kernel: point r goes to tile
+// r / 128, row r % 128 of that tile's MMA layout; padding points (r >= M) get
+// r = 0 and |r|^2 = 1e30, so they never screen in.
+__global__ void tc_ref_prep_kernel(const float4 *R, int M, int Mpad, float *Rt)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= Mpad) return;
+    float x = 0.f, y = 0.f, z = 0.f, w = 1e30f;
+    if (r < M) {
+        const float4 p = R[r];
+        x = p.x; y = p.y; z = p.z;
+        w = (float)((double)x * x + (double)y * y + (double)z * z);
+    }
+    const float c[3] = {x, y, z};
+    float v[kAug];
+    for (int k = 0; k < 3; ++k) {
+        const float h = tf32_rn(c[k]);
+        const float l = tf32_rn(c[k] - h);
+        v[k] = h; v[3 + k] = l; v[6 + k] = h;
+    }
+    const float w1 = tf32_rn(w), w2 = tf32_rn(w - w1);
+    v[9] = w1; v[10] = w2; v[11] = (w - w1) - w2;
+    v[12] = v[13] = v[14] = v[15] = 0.f;
+    unsigned char *tile = reinterpret_cast<unsigned char *>(Rt) + (size_t)(r / kCols) * kTileBytes;
+    for (int k = 0; k < kAug; ++k) *reinterpret_cast<float *>(tile + core_offset(r % kCols, k)) = v[k];
+}
+
+cudaError_t launch_tc_ref_prep(const float4 *R, int M, int Mpad, float *Rt, cudaStream_t st)
+{
+    tc_ref_prep_kernel<<<(Mpad + 255) / 256, 256, 0, st>>>(R, M, Mpad, Rt);
+    return cudaGetLastError();
+}
+
+size_t tc_ref_bytes(int Mpad) { return (size_t)Mpad / kCols * kTileBytes; }
+
+// Warp roles: warps 0-3 (one query per thread; warp w reads TMEM lanes
+// 32 w .. 32 w + 31) build the
+// augmented query rows, reduce the accumulators and make the exact choice;
+// lane 0 of warp 4 streams the object tiles and issues the MMAs.  They meet on
+// mbarriers only (no CTA-wide barrier inside the loop):
+//   bfull[s]  tile in stage s has landed          (copy -> MMA)
+//   bempty[s] the MMAs reading stage s are done    (MMA commit -> copy)
+//   accf[b]   accumulator b holds a finished tile  (MMA commit -> reduction)
+//   acce[b]   accumulator b has been read          (reduction -> MMA, 128 arrivals)
+//   afull     the item's query rows are written    (reduction warps -> MMA, 128 arrivals)
+__global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    unsigned char *sA = smem_tc;
+    unsigned char *sB = smem_tc + kABytes;
+    __shared__ __align__(8) unsigned long long bfull[kStages], bempty[kStages], accf[2], acce[2], afull;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int it0 = a.cta_off ? a.cta_off[blockIdx.x] : blockIdx.x;
+    const int it1 = a.cta_off ? a.cta_off[blockIdx.x + 1] : a.n_items;
+    const int step = a.cta_off ? 1 : gridDim.x;
+    if (it0 >= it1) return;
+    const long long Qtot = (long long)a.L.T * a.L.N;
+    auto item_at = [&](int it) {
+        FwdItem item;
+        if (a.items) {
+            item = a.items[it];
+        } else {
+            item.q0 = (long long)it * kQueries;
+            item.nq = (int)(Qtot - item.q0 < kQueries ? Qtot - item.q0 : kQueries);
+            item.obj = 0;
+        }
+        return item;
+    };
+    auto fail = [&]() {
+        if (!s_abort) atomicExch(a.err, kDevTimeout);
+        s_abort = 1;
+    };
+
+    if (tid == 0) {
+        s_abort = 0;
+        for (int s = 0; s < kStages; ++s) { mbar_init(&bfull[s], 1); mbar_init(&bempty[s], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], kQueries); }
+        mbar_init(&afull, kQueries);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp == kQueries / 32) {
+        // ------------------------------------------------ copies and MMAs (one thread)
+        if (lane == 0) {
+            int p_it = it0, p_tile = 0, p_ntiles = 0;
+            const unsigned char *p_src = nullptr;
+            long long p_seq = 0, seq = 0;
+            auto producer_item = [&]() {
+                if (p_it >= it1) return;
+                const ObjMeta &om = a.L.obj[item_at(p_it).obj];
+                p_src = reinterpret_cast<const unsigned char *>(om.Rt);
+                p_ntiles = om.Mpad / kCols;
+            };
+            // copy the next tile into its stage once the MMAs that last read the stage are done
+            auto issue_load = [&]() -> bool {
+                const int stage = (int)(p_seq % kStages);
+                if (!mbar_wait(&bempty[stage], (unsigned)(((p_seq / kStages) & 1) ^ 1))) return false;
+                mbar_arrive_tx(&bfull[stage], kTileBytes);
+                bulk_load(sB + (size_t)stage * kTileBytes, p_src + (size_t)p_tile * kTileBytes, kTileBytes,
+                          &bfull[stage]);
+                ++p_seq;
+                if (++p_tile == p_ntiles) {
+                    p_tile = 0;
+                    p_it += step;
+                    producer_item();
+                }
+                return true;
+            };
+            producer_item();
+            int ia = 0;
+            for (int it = it0; it < it1 && !s_abort; it += step, ++ia) {
+                const int ntiles = a.L.obj[item_at(it).obj].Mpad / kCols;
+                if (!mbar_wait(&afull, (unsigned)(ia & 1))) { fail(); break; }
+                tc_fence_after();
+                for (int t = 0; t < ntiles; ++t, ++seq) {
+                    // copies run kStages - 2 tiles ahead: the stage they reuse was read by MMA(seq - 2)
+                    while (p_it < it1 && p_seq <= seq + kStages - 2)
+                        if (!issue_load()) { fail(); break; }
+                    const int stage = (int)(seq % kStages), buf = (int)(seq & 1);
+                    if (s_abort || !mbar_wait(&bfull[stage], (unsigned)((seq / kStages) & 1)) ||
+                        !mbar_wait(&acce[buf], (unsigned)(((seq >> 1) & 1) ^ 1))) {
+                        fail();
+                        break;
+                    }
+                    tc_fence_after();
+                    const unsigned b0 = smem_u32(sB + (size_t)stage * kTileBytes);
+#pragma unroll
+                    for (int blk = 0; blk < kBlocks; ++blk) {
+                        const uint32_t d = tmem + (uint32_t)(blk * 2 + buf) * kCols;
+                        const unsigned a0 = smem_u32(sA + blk * kABlockBytes);
+                        mma_tf32(d, smem_desc(a0), smem_desc(b0), 0u);
+                        mma_tf32(d, smem_desc(a0 + 256), smem_desc(b0 + 256), 1u);
+                    }
+                    mma_commit(&bempty[stage]);
+                    mma_commit(&accf[buf]);
+                }
+            }
+            if (s_abort) {
+                // drain (bounded): the MMAs issued, then the copies no MMA consumed
+                if (seq > 0) mbar_wait(&accf[(seq - 1) & 1], (unsigned)(((seq - 1) >> 1) & 1));
+                for (long long q = seq; q < p_seq; ++q) mbar_wait(&bfull[q % kStages], (unsigned)((q / kStages) & 1));
+            }
+        }
+    } else {
+        // ------------------------------------------------ query rows, reduction, exact choice
+        const int blk = warp / 4, row = tid % kRows;      // query block; row = TMEM lane
+        const uint32_t lane_base = (uint32_t)((warp % 4) * 32) << 16;
+        long long seq = 0;
+        for (int it = it0; it < it1; it += step) {
+            if (__any_sync(0xffffffffu, s_abort)) break;
+            const FwdItem item = item_at(it);
+            const ObjMeta om = a.L.obj[item.obj];
+            const float rmax = a.L.rmax[item.obj];
+            const int ntiles = om.Mpad / kCols;
+            const bool valid = tid < item.nq;
+            const long long g = item.q0 + tid;
+            float3 o = make_float3(0.f, 0.f, 0.f);
+            if (valid) {
+                const int pk = (int)(g / a.L.N), i = (int)(g - (long long)pk * a.L.N);
+                const int pre = a.L.part_grp[pk] % a.L.P;
+                const float *th = a.theta + (size_t)pk * 8;
+                float Rm[9];
+                quat_rot_f32(th[3], th[4], th[5], th[6], Rm);
+                const float4 s = a.S[(size_t)pre * a.L.N + i];
+                o = xform_f32(Rm, th[0], th[1], th[2], s.x, s.y, s.z);
+            }
+            {
+                // the previous item's MMAs are complete (its last accumulator was waited for)
+                const float c[3] = {-2.f * o.x, -2.f * o.y, -2.f * o.z};
+                float v[kAug];
+                for (int k = 0; k < 3; ++k) {
+                    const float h = tf32_rn(c[k]);
+                    v[k] = h; v[3 + k] = h; v[6 + k] = tf32_rn(c[k] - h);
+                }
+                v[9] = v[10] = v[11] = 1.f;
+                v[12] = v[13] = v[14] = v[15] = 0.f;
+                for (int j = 0; j < kAug / 4; ++j)
+                    *reinterpret_cast<float4 *>(sA + blk * kABlockBytes + core_offset(row, 4 * j)) =
+                        make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&afull);
+            }
+            const float sn = sqrtf(o.x * o.x + o.y * o.y + o.z * o.z) * 1.001f;
+            const float win = 2.02f * 5.9604645e-8f * (18.f * rmax * rmax + 57.f * sn * rmax);
+            // the kTop best chunk minima (ascending) with their chunk ids, and the best of the rest
+            float bk[kTop], brest = __int_as_float(0x7f800000);
+            int ck[kTop];
+#pragma unroll
+            for (int k = 0; k < kTop; ++k) { bk[k] = __int_as_float(0x7f800000); ck[k] = 0; }
+            bool good = true;
+            for (int t = 0; t < ntiles; ++t, ++seq) {
+                const int buf = (int)(seq & 1);
+                good = mbar_wait_warp(&accf[buf], (unsigned)((seq >> 1) & 1));
+                if (!__all_sync(0xffffffffu, good && !s_abort)) { good = false; break; }
+                tc_fence_after();
+                float mv[kCols / kChunk];
+#pragma unroll
+                for (int h = 0; h < kCols / kChunk; ++h)
+                    mv[h] = ld_min64(tmem + lane_base + (uint32_t)(blk * 2 + buf) * kCols + (uint32_t)(h * kChunk));
+                tc_fence_before();
+                mbar_arrive(&acce[buf]);
+#pragma unroll
+                for (int h = 0; h < kCols / kChunk; ++h) {
+                    // insert (v, chunk gc); strict < keeps the earlier chunk first on equal minima
+                    float v = mv[h];
+                    int gc = t * (kCols / kChunk) + h;
+#pragma unroll
+                    for (int k = 0; k < kTop; ++k) {
+                        const bool lt = v < bk[k];
+                        const float bv = bk[k];
+                        const int cv = ck[k];
+                        bk[k] = lt ? v : bv;
+                        ck[k] = lt ? gc : cv;
+                        v = lt ? bv : v;
+                        gc = lt ? cv : gc;
+                    }
+                    brest = fminf(brest, v);
+                }
+            }
+            if (!good) { fail(); break; }
+
+            // exact choice among the chunks that can hold the nearest point: up to kTop
+            // chunks per query by its own thread, or, when more qualify, the whole cloud
+            // by the warp together (one such query at a time)
+            const float thr = bk[0] + win;
+            const bool whole = valid && brest <= thr;
+            float best = __int_as_float(0x7f800000);
+            int bi = 0x7fffffff;
+            if (valid && !whole) {
+#pragma unroll
+                for (int k = 0; k < kTop; ++k)
+                    if (bk[k] <= thr)
+                        exact_scan_tie(om.R, ck[k] * kChunk, min((ck[k] + 1) * kChunk, om.M), o, best, bi);
+            }
+            unsigned pending = __ballot_sync(0xffffffffu, whole);
+            while (pending) {
+                const int src = __ffs(pending) - 1;
+                pending &= pending - 1;
+                const float qx = __shfl_sync(0xffffffffu, o.x, src), qy = __shfl_sync(0xffffffffu, o.y, src),
+                            qz = __shfl_sync(0xffffffffu, o.z, src);
+                float wb = __int_as_float(0x7f800000);
+                int wi = 0x7fffffff;
+                for (int r = lane; r < om.M; r += 32) {
+                    const float4 v = __ldg(om.R + r);
+                    const float d = dist2_f32(qx, qy, qz, v.x, v.y, v.z);
+                    if (d < wb) { wb = d; wi = r; }
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const float ob = __shfl_xor_sync(0xffffffffu, wb, off);
+                    const int oi = __shfl_xor_sync(0xffffffffu, wi, off);
+                    if (ob < wb || (ob == wb && oi < wi)) { wb = ob; wi = oi; }
+                }
+                if (lane == src) { best = wb; bi = wi; }
+            }
+            if (valid) {
+                if (bi >= om.M) bi = 0;    // no finite distance at all (not reached with finite inputs)
+                a.nn_idx[g] = bi;
+                if (a.dbg_d2) a.dbg_d2[g] = best;
+                if (a.dbg_sp) {
+                    a.dbg_sp[g * 3 + 0] = o.x;
+                    a.dbg_sp[g * 3 + 1] = o.y;
+                    a.dbg_sp[g * 3 + 2] = o.z;
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+// Two CTAs per SM: each allocates half of tensor memory (256 columns), and the
+// shared-memory request leaves no room for a third.
+int fwd_tc_grid()
+{
+    static int grid = 0;
+    if (grid == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(fwd_match_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        cudaFuncSetAttribute(fwd_match_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        grid = 2 * sms;
+    }
+    return grid;
+}
+
+int fwd_tc_threads() { return kQueries; }
+
+cudaError_t launch_fwd_match_tc(const FwdArgs &a, cudaStream_t st)
+{
+    fwd_match_tc_kernel<<<fwd_tc_grid(), kThreadsTc, kSmemBytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace asicp

@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(kSteinThreads) stein_kernel(const UpdateArgs a
     __shared__ unsigned hist[256];
     __shared__ unsigned whist[kSteinThreads / 32][256];   // per-warp histograms: no cross-warp atomics
     __shared__ unsigned s_prefix, s_mask, s_rank;
+    __shared__ float s_h;
 
     const int grp = blockIdx.x, base = a.L.grp_off[grp], K = a.L.grp_off[grp + 1] - base;
     if (K <= 0) return;
@@ -252,9 +253,12 @@ __global__ void __launch_bounds__(kSteinThreads) stein_kernel(const UpdateArgs a
             }
             __syncthreads();
         }
-        const double med = (double)__uint_as_float(s_prefix);
-        h = (float)(med / log((double)K));
-        h = fmaxf(h, 1e-12f);
+        if (threadIdx.x == 0) {     // float64 division and logarithm once, not per thread
+            const double med = (double)__uint_as_float(s_prefix);
+            s_h = fmaxf((float)(med / log((double)K)), 1e-12f);
+        }
+        __syncthreads();
+        h = s_h;
     }
     if (threadIdx.x == 0) a.h[grp] = h;
 

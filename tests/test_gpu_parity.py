@@ -453,3 +453,45 @@ def test_every_forward_shape_gives_the_same_correspondences(stream):
         del keep
     finally:
         asicp.asicp_destroy(ctx)
+
+
+def _step_indices(w, stream, theta0, shape, k=0):
+    """Correspondences and transformed points of one teacher-forced step with kernel shape `shape`."""
+    P, K, N, Mc = len(w.preshapes), w.K, w.preshapes[0].S.shape[0], len(w.objects[0].points)
+    ctx = _ctx(w, stream, debug=1, fwd_shape=shape)
+    try:
+        keep = tl.upload(ctx, w)
+        asicp.asicp_set_state(ctx, theta0, k)
+        asicp.asicp_step(ctx, k)
+        st = tl.read_state(ctx, P, K, N, Mc)
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
+    return st
+
+
+def test_tensor_core_matching_equals_float32_matching(stream):
+    """The tensor-core kernel (split-TF32 screening + exact choice) against the float32 kernel at the
+    paper's N and M (3 preshapes x 64 particles, N=2048, M=8192; 1.2e6 queries): identical indices
+    except near-ties (|d2 difference| <= 1e-6 relative in float64), and ties broken alike."""
+    w = synth.custom_case(P=3, K=64, N=2048, M=8192, grid=32, k_max=2, seed=synth.BASE_SEED + 2)
+    import oracle
+    com = w.objects[0].points.astype(np.float64).mean(0)
+    tc = asicp.FWD_VARIANTS.index("tc-tf32x3-m128-n128")
+    for radius in (0.15, 0.03):          # far from the object, and fingers in contact
+        th = np.tile(oracle.fibonacci_init(w.K, com, radius), (3, 1)).astype(np.float32)
+        a = _step_indices(w, stream, th, 0)
+        b = _step_indices(w, stream, th, tc)
+        assert np.array_equal(a["s_prime"], b["s_prime"])
+        diff = np.nonzero(a["nn_idx"] != b["nn_idx"])
+        n_diff = len(diff[0])
+        print(f"radius {radius}: {n_diff} of {a['nn_idx'].size} indices differ")
+        if n_diff:
+            R = w.objects[0].points.astype(np.float64)
+            sp = a["s_prime"][diff].astype(np.float64)
+            da = ((sp - R[a["nn_idx"][diff]]) ** 2).sum(-1)
+            db = ((sp - R[b["nn_idx"][diff]]) ** 2).sum(-1)
+            rel = np.abs(da - db) / np.maximum(np.minimum(da, db), 1e-300)
+            assert rel.max() <= tl.NEAR_TIE_REL, f"non-tie mismatch, relative gap {rel.max():.3e}"
+            assert n_diff <= 1e-4 * a["nn_idx"].size
+        assert np.allclose(a["cost"], b["cost"], rtol=1e-6, atol=0)
