@@ -10,6 +10,7 @@ namespace asicp {
 
 namespace {
 constexpr int kColThreads = 256;
+constexpr int kColU = 4;          // collision points per thread per compaction round
 
 // Trilinear interpolation of a node-centred grid at gripper-frame point (x, y, z).
 // Returns false when the point lies outside the grid's node box (the grid covers
@@ -69,7 +70,7 @@ __device__ __forceinline__ void block_reduce_store(dfloat (&acc)[NV], double (*s
 //     block prefix), so results do not depend on scheduling.
 __global__ void __launch_bounds__(kColThreads) collide_kernel(const CollideArgs a)
 {
-    __shared__ int swarp[kColThreads / 32];
+    __shared__ int swarp[kColU][kColThreads / 32];
     __shared__ double sred[kColThreads / 32][kFwdSums];
     const int pk = blockIdx.x;
     const int grp = a.L.part_grp[pk], p = grp % a.L.P;
@@ -105,31 +106,53 @@ __global__ void __launch_bounds__(kColThreads) collide_kernel(const CollideArgs 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *colidx = a.colidx + om.colidx_base + (long long)(pk - om.pfirst) * Mc;
     int count = 0;
-    for (int c0 = 0; c0 < Mc; c0 += kColThreads) {
-        const int c = c0 + threadIdx.x;
-        bool hit = false;
-        if (c < Mc) {
-            const float4 v = om.C[c];
-            const float dx = __fsub_rn(v.x, tx), dy = __fsub_rn(v.y, ty), dz = __fsub_rn(v.z, tz);
-            const float lx = __fmaf_rn(Rm[0], dx, __fmaf_rn(Rm[3], dy, __fmul_rn(Rm[6], dz)));
-            const float ly = __fmaf_rn(Rm[1], dx, __fmaf_rn(Rm[4], dy, __fmul_rn(Rm[7], dz)));
-            const float lz = __fmaf_rn(Rm[2], dx, __fmaf_rn(Rm[5], dy, __fmul_rn(Rm[8], dz)));
-            if (lx >= m.lo[0] && lx <= m.hi[0] && ly >= m.lo[1] && ly <= m.hi[1] && lz >= m.lo[2] && lz <= m.hi[2]) {
-                float val;
-                hit = sdf_lookup(m, lx, ly, lz, val) && val > 0.f;
+    // kU points per thread per round (their loads and lookups overlap), one
+    // compaction per round in ascending point order (round slot, warp, lane)
+    for (int c0 = 0; c0 < Mc; c0 += kColThreads * kColU) {
+        float4 v[kColU];
+#pragma unroll
+        for (int u = 0; u < kColU; ++u) {
+            const int c = c0 + u * kColThreads + threadIdx.x;
+            v[u] = c < Mc ? om.C[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        bool hit[kColU];
+#pragma unroll
+        for (int u = 0; u < kColU; ++u) {
+            const int c = c0 + u * kColThreads + threadIdx.x;
+            hit[u] = false;
+            if (c < Mc) {
+                const float dx = __fsub_rn(v[u].x, tx), dy = __fsub_rn(v[u].y, ty), dz = __fsub_rn(v[u].z, tz);
+                const float lx = __fmaf_rn(Rm[0], dx, __fmaf_rn(Rm[3], dy, __fmul_rn(Rm[6], dz)));
+                const float ly = __fmaf_rn(Rm[1], dx, __fmaf_rn(Rm[4], dy, __fmul_rn(Rm[7], dz)));
+                const float lz = __fmaf_rn(Rm[2], dx, __fmaf_rn(Rm[5], dy, __fmul_rn(Rm[8], dz)));
+                if (lx >= m.lo[0] && lx <= m.hi[0] && ly >= m.lo[1] && ly <= m.hi[1] && lz >= m.lo[2] &&
+                    lz <= m.hi[2]) {
+                    float val;
+                    hit[u] = sdf_lookup(m, lx, ly, lz, val) && val > 0.f;
+                }
             }
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, hit);
-        if (lane == 0) swarp[warp] = __popc(bal);
-        __syncthreads();
-        int off = 0, tot = 0;
+        unsigned bal[kColU];
 #pragma unroll
-        for (int w = 0; w < kColThreads / 32; ++w) {
-            const int n = swarp[w];
-            off += w < warp ? n : 0;
-            tot += n;
+        for (int u = 0; u < kColU; ++u) {
+            bal[u] = __ballot_sync(0xffffffffu, hit[u]);
+            if (lane == 0) swarp[u][warp] = __popc(bal[u]);
         }
-        if (hit) colidx[count + off + __popc(bal & ((1u << lane) - 1u))] = c;
+        __syncthreads();
+        int before = 0, tot = 0;
+#pragma unroll
+        for (int u = 0; u < kColU; ++u) {
+            int mine = 0;
+#pragma unroll
+            for (int w = 0; w < kColThreads / 32; ++w) {
+                const int n = swarp[u][w];
+                mine += w < warp ? n : 0;
+                tot += n;
+            }
+            if (hit[u])
+                colidx[count + before + mine + __popc(bal[u] & ((1u << lane) - 1u))] = c0 + u * kColThreads + threadIdx.x;
+            before = tot;
+        }
         count += tot;
         __syncthreads();
     }

@@ -74,7 +74,7 @@ __device__ __forceinline__ float pair_d2(float4 a, float4 b)
 //  3. mode 2: the SGD-ICP update of Eq. 3 (A = I); modes 0 (evaluate only) and 1
 //     (SVGD, done by stein_kernel) leave the poses alone.
 //  Thread 0 of CTA 0 also clears the collision work-list counters for the next pass.
-constexpr int kFinalizeThreads = 32;
+constexpr int kFinalizeThreads = 4;      // 192 CTAs for 768 particles: float64 chains spread over every SM
 
 __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(const UpdateArgs a)
 {
@@ -159,16 +159,19 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(const Update
 // SVGD phase, one CTA of kSteinThreads per preshape; each particle i is served
 // by T = kSteinThreads / K' threads (K' = K rounded up to a power of two), so a
 // preshape of 256 particles still fills 32 warps:
-//  - bandwidth: exact lower median of |t_i - t_j|^2 (i < j) by 4 passes of 8-bit
-//    radix selection on the float bit patterns; every unordered pair is visited
-//    once (thread (i, sub) takes partners i + o (mod K), o = 1 + sub + T m <= K/2,
-//    the o = K/2 pairs only from i < K/2 when K is even); lanes that land in one
-//    bin add with one aggregated shared-memory atomic;
+//  - bandwidth: exact lower median of |t_i - t_j|^2 (i < j): the value range is
+//    narrowed by histograms over linear bins (usually one pass) until the bin
+//    holding the median has at most kSelCand values, which are then ranked
+//    exactly; every unordered pair is visited once per pass (thread (i, sub)
+//    takes partners i + o (mod K), o = 1 + sub + T m <= K/2, the o = K/2 pairs
+//    only from i < K/2 when K is even);
 //  - Stein direction of Eq. 8 read as the mean of Eq. 6 with the kernels of
 //    Eqs. 9-10 per block: thread (i, sub) sums over j = sub, sub + T, ..., the T
 //    partial sums of particle i (adjacent lanes) are added by shuffles;
 //  - the update of Eq. 7.
 constexpr int kSteinThreads = 1024;
+constexpr int kSelBins = 1024;         // histogram bins per narrowing pass of the median selection
+constexpr int kSelCand = 1024;         // values ranked exactly at the end
 
 __global__ void __launch_bounds__(kSteinThreads) stein_kernel(const UpdateArgs a)
 {
@@ -177,9 +180,10 @@ __global__ void __launch_bounds__(kSteinThreads) stein_kernel(const UpdateArgs a
     float4 *sQ = sm + kMaxK;          // [K] q (wxyz)
     float4 *sDt = sm + 2 * kMaxK;     // [K] -gamma N g_t
     float4 *sDq = sm + 3 * kMaxK;     // [K] -gamma N g_q
-    __shared__ unsigned hist[256];
-    __shared__ unsigned whist[kSteinThreads / 32][256];   // per-warp histograms: no cross-warp atomics
-    __shared__ unsigned s_prefix, s_mask, s_rank;
+    __shared__ unsigned hist[kSelBins];
+    __shared__ float cand[kSelCand];
+    __shared__ unsigned s_wsum[kSteinThreads / 32];
+    __shared__ unsigned s_lo, s_hi, s_rank, s_n, s_bin, s_before, s_fill;
     __shared__ float s_h;
 
     const int grp = blockIdx.x, base = a.L.grp_off[grp], K = a.L.grp_off[grp + 1] - base;
@@ -207,55 +211,110 @@ __global__ void __launch_bounds__(kSteinThreads) stein_kernel(const UpdateArgs a
     } else if (K < 2) {
         h = 1.f;
     } else {
-        if (threadIdx.x == 0) {
-            const unsigned long long L = (unsigned long long)K * (K - 1) / 2;
-            s_rank = (unsigned)((L - 1) / 2);
-            s_prefix = 0u;
-            s_mask = 0u;
-        }
+        const unsigned long long L = (unsigned long long)K * (K - 1) / 2;
         const int half = K / 2;
         const int trips = (half + T - 1) / T;
-        const int lane = threadIdx.x & 31;
-        const int warp = threadIdx.x >> 5;
-        for (int shift = 24; shift >= 0; shift -= 8) {
-            for (int b = threadIdx.x; b < (kSteinThreads / 32) * 256; b += blockDim.x) (&whist[0][0])[b] = 0u;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const float4 ti = sT[active ? i : 0];
+        // squared distance of this thread's m-th pair, or -1 when it has none
+        auto pair_at = [&](int m) -> float {
+            const int o = 1 + sub + T * m;
+            int jj = i + o;
+            jj -= jj >= K ? K : 0;
+            const bool valid = active && o <= half && !((K & 1) == 0 && o == half && i >= half);
+            return valid ? pair_d2(ti, sT[jj]) : -1.f;
+        };
+        // range of all pair values (non-negative floats order like their bit patterns)
+        unsigned vmin = 0xffffffffu, vmax = 0u;
+        for (int m = 0; m < trips; ++m) {
+            const float v = pair_at(m);
+            if (v >= 0.f) { vmin = min(vmin, __float_as_uint(v)); vmax = max(vmax, __float_as_uint(v)); }
+        }
+        vmin = __reduce_min_sync(0xffffffffu, vmin);
+        vmax = __reduce_max_sync(0xffffffffu, vmax);
+        if (threadIdx.x == 0) { s_lo = 0xffffffffu; s_hi = 0u; s_rank = (unsigned)((L - 1) / 2); }
+        __syncthreads();
+        if (lane == 0) { atomicMin(&s_lo, vmin); atomicMax(&s_hi, vmax); }
+        __syncthreads();
+        // narrow [lo, hi] (it holds the answer, with s_rank values of the set below lo)
+        // by histograms over kSelBins linear bins until the bin holding the answer has at
+        // most kSelCand values, then rank those exactly; binning is monotone in the value,
+        // so a bin holds a contiguous run of the sorted values
+        float med = 0.f;
+        for (int pass = 0;; ++pass) {
+            const float lo = __uint_as_float(s_lo), hi = __uint_as_float(s_hi);
+            if (!(lo < hi) || pass == 32) { med = lo; break; }   // (32: not reached with finite values)
+            const float scale = (float)kSelBins / (hi - lo);
+            auto bin_of = [&](float v) { return min(kSelBins - 1, (int)((v - lo) * scale)); };
+            for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) hist[b] = 0u;
             __syncthreads();
-            const unsigned prefix = s_prefix, mask = s_mask;
-            const float4 ti = sT[active ? i : 0];
             for (int m = 0; m < trips; ++m) {
-                const int o = 1 + sub + T * m;
-                int jj = i + o;
-                jj -= jj >= K ? K : 0;
-                const bool valid = active && o <= half && !((K & 1) == 0 && o == half && i >= half);
-                const unsigned bits = __float_as_uint(pair_d2(ti, sT[valid ? jj : 0]));
-                const bool take = valid && (bits & mask) == prefix;
-                const unsigned key = take ? ((bits >> shift) & 255u) : 256u + lane;
-                const unsigned peers = __match_any_sync(0xffffffffu, key);
-                if (take && lane == __ffs(peers) - 1) atomicAdd(&whist[warp][key], (unsigned)__popc(peers));
+                const float v = pair_at(m);
+                if (v >= lo && v <= hi) atomicAdd(&hist[bin_of(v)], 1u);
             }
             __syncthreads();
-            for (int b = threadIdx.x; b < 256; b += blockDim.x) {
-                unsigned c = 0u;
-                for (int w = 0; w < kSteinThreads / 32; ++w) c += whist[w][b];
-                hist[b] = c;
+            // exclusive scan over the bins (one bin per thread), then the bin holding rank s_rank
+            const int b = threadIdx.x;
+            const unsigned cnt = b < kSelBins ? hist[b] : 0u;
+            unsigned inc = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31) s_wsum[warp] = inc;
+            __syncthreads();
+            unsigned before = inc - cnt;
+            for (int w = 0; w < warp; ++w) before += s_wsum[w];
+            const unsigned rank = s_rank;
+            if (b < kSelBins && cnt > 0 && before <= rank && rank < before + cnt) {
+                s_bin = (unsigned)b;
+                s_before = before;
+                s_n = cnt;
+                s_fill = 0u;
+                s_lo = 0xffffffffu;
+                s_hi = 0u;
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                unsigned rank = s_rank, cum = 0u;
-                int b = 0;
-                for (; b < 255; ++b) {
-                    if (rank < cum + hist[b]) break;
-                    cum += hist[b];
+            const int bsel = (int)s_bin;
+            const unsigned n = s_n;
+            if (n <= (unsigned)kSelCand) {
+                // gather the bin's values and rank them exactly
+                for (int m = 0; m < trips; ++m) {
+                    const float v = pair_at(m);
+                    if (v >= lo && v <= hi && bin_of(v) == bsel) cand[atomicAdd(&s_fill, 1u)] = v;
                 }
-                s_rank = rank - cum;
-                s_prefix = prefix | ((unsigned)b << shift);
-                s_mask = mask | (255u << shift);
+                __syncthreads();
+                const unsigned r = s_rank - s_before;
+                for (unsigned c = threadIdx.x; c < n; c += blockDim.x) {
+                    const float v = cand[c];
+                    unsigned less = 0u, equal = 0u;
+                    for (unsigned e = 0; e < n; ++e) {
+                        less += cand[e] < v;
+                        equal += cand[e] == v;
+                    }
+                    if (less <= r && r < less + equal) s_lo = __float_as_uint(v);
+                }
+                __syncthreads();
+                med = __uint_as_float(s_lo);
+                break;
             }
+            // too many: the bin's own value range becomes the new [lo, hi]
+            unsigned bmin = 0xffffffffu, bmax = 0u;
+            for (int m = 0; m < trips; ++m) {
+                const float v = pair_at(m);
+                if (v >= lo && v <= hi && bin_of(v) == bsel) {
+                    bmin = min(bmin, __float_as_uint(v));
+                    bmax = max(bmax, __float_as_uint(v));
+                }
+            }
+            bmin = __reduce_min_sync(0xffffffffu, bmin);
+            bmax = __reduce_max_sync(0xffffffffu, bmax);
+            if (lane == 0) { atomicMin(&s_lo, bmin); atomicMax(&s_hi, bmax); }
+            if (threadIdx.x == 0) s_rank -= s_before;
             __syncthreads();
         }
         if (threadIdx.x == 0) {     // float64 division and logarithm once, not per thread
-            const double med = (double)__uint_as_float(s_prefix);
-            s_h = fmaxf((float)(med / log((double)K)), 1e-12f);
+            s_h = fmaxf((float)((double)med / log((double)K)), 1e-12f);
         }
         __syncthreads();
         h = s_h;
