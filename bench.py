@@ -37,6 +37,9 @@ sys.path.insert(0, ROOT)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
+# DRAM bytes (read + write) of one forward-matching launch from the committed ncu capture
+# (profiles/fwd_match_kernel_profile-case-P1-K256-N2048-M8192.md); null once the kernel changes
+FWD_DRAM_BYTES_PER_LAUNCH = 406528
 OPS_PER_PAIR = 3          # FMA-pipe work per particle*point pair: 3 FMAs (the min runs on the separate ALU pipe)
 TOPK = 16
 
@@ -286,7 +289,10 @@ def run_gpu(args, rank, world, local_rank):
                        "fwd_shape": asicp.FWD_VARIANTS[shape]},
             "ms_per_grasp_set": max_ms / args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpairs/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": FWD_DRAM_BYTES_PER_LAUNCH,
+                         "traffic_basis": "dram__bytes_read+write of one fwd_match_kernel launch (ncu, shape "
+                                          "qpt8-chunk64-t128-tile1024); every input is L2-resident, so it does not "
+                                          "grow with the launch",
                          "kernel": "fwd_match_kernel", "peak_basis":
                              f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 FMA/clk x {SM_MAX_MHZ_NOMINAL:.0f} MHz / "
                              f"{OPS_PER_PAIR} FMA per pair",
