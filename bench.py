@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--small", action="store_true", help="small workload (debugging only)")
     ap.add_argument("--fwd-shape", type=int, default=-1,
                     help="forward-matching kernel shape (index into asicp.FWD_VARIANTS); -1: autotune")
+    ap.add_argument("--batched", type=int, default=0, metavar="OBJECTS",
+                    help="time OBJECTS objects (point counts 1k-32k, 128/256/512 particles per preshape) optimised "
+                         "together against each object alone; prints its own JSON line")
     ap.add_argument("--profile-case", action="store_true",
                     help="one short run of a reduced workload (1 preshape x 256 particles, N=2048, M=8192, "
                          "8 iterations, poses close enough to collide) for profiler captures; no JSON line")
@@ -373,8 +376,93 @@ def run_profile_case(args):
         asicp.asicp_destroy(ctx)
 
 
+def run_batched(args):
+    """Many objects in one context (one launch per kernel for all of them, one captured loop) against the
+    plain path (each object in its own context, run one after the other); same per-object results."""
+    import torch
+    from paper_2412_08346_gb300 import asicp, synth
+    w, K = synth.batched_case(args.batched)
+    nobj, P = len(w.objects), len(w.preshapes)
+    stream = torch.cuda.current_stream()
+    pre_dev = [(torch.from_numpy(p.S).cuda(), torch.from_numpy(p.sdf).cuda()) for p in w.preshapes]
+    obj_dev = [torch.from_numpy(o.points).cuda() for o in w.objects]
+
+    def make(n, counts, shape):
+        cfg = asicp.asicp_config_default(P=P, K=int(K.max()), k_max=w.k_max, k_stein=w.k_stein,
+                                         schedule=w.schedule, cuda_stream=stream.cuda_stream, n_objects=n,
+                                         fwd_shape=max(0, shape))
+        ctx = asicp.asicp_create(cfg)
+        asicp.asicp_set_particle_counts(ctx, np.ascontiguousarray(counts.ravel(), np.int32))
+        for p, (S, g) in enumerate(pre_dev):
+            asicp.asicp_set_gripper_sdf(ctx, p, S, g, w.preshapes[p].origin, w.preshapes[p].voxel)
+        return ctx
+
+    def best_cost(ctx, o=None):
+        th, c, pr = np.zeros(7, np.float32), np.zeros(1, np.float32), np.zeros(1, np.int32)
+        if o is None:
+            asicp.asicp_best_grasps(ctx, 1, th, c, pr)
+        else:
+            asicp.asicp_best_grasps_at(ctx, o, 1, th, c, pr)
+        return float(c[0])
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), out
+
+    ctx = make(nobj, K, args.fwd_shape)
+    try:
+        for o, R in enumerate(obj_dev):
+            asicp.asicp_set_object_at(ctx, o, R)
+        shape = asicp.asicp_autotune(ctx)[0] if args.fwd_shape < 0 else args.fwd_shape
+
+        def batched_set():
+            asicp.asicp_run(ctx)
+            return [best_cost(ctx, o) for o in range(nobj)]
+        batched_set()                                    # warm-up (captures the loop)
+        runs = [timed(batched_set) for _ in range(max(1, args.steps))]
+        batched_ms = sum(r[0] for r in runs) / len(runs)
+        batched_cost = runs[-1][1]
+    finally:
+        asicp.asicp_destroy(ctx)
+
+    solo_ms, solo_cost = 0.0, []
+    for o in range(nobj):
+        c1 = make(1, K[o], shape)
+        try:
+            asicp.asicp_set_object(c1, obj_dev[o])
+
+            def solo_set():
+                asicp.asicp_run(c1)
+                return best_cost(c1)
+            solo_set()                                   # warm-up (captures the loop)
+            t, c = timed(solo_set)
+            solo_ms += t
+            solo_cost.append(c)
+        finally:
+            asicp.asicp_destroy(c1)
+    rel = max(abs(a - b) / max(abs(b), 1e-30) for a, b in zip(batched_cost, solo_cost))
+    pairs = sum(int(K[o].sum()) * w.preshapes[0].S.shape[0] * len(w.objects[o].points) for o in range(nobj))
+    print(json.dumps({
+        "metric": "ms per grasp set, objects optimised together vs each alone, at equal cost",
+        "value": batched_ms / nobj, "unit": "ms/grasp set", "higher_is_better": False,
+        "solo_ms_per_grasp_set": solo_ms / nobj, "speedup_vs_solo": solo_ms / batched_ms,
+        "batched_pairs_per_s": pairs * (w.k_max + 1) / (batched_ms / 1e3),
+        "max_best_cost_rel_diff_vs_solo": rel, "steps": len(runs), "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "objects": nobj, "M_min": min(len(o.points) for o in w.objects),
+                   "M_max": max(len(o.points) for o in w.objects), "particles": int(K.sum()),
+                   "pairs_per_iteration": pairs, "fwd_shape": asicp.FWD_VARIANTS[shape]}}), flush=True)
+
+
 def main():
     args = parse()
+    if args.batched:
+        run_batched(args)
+        return
     if args.profile_case:
         run_profile_case(args)
         return

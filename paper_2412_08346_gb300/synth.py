@@ -312,3 +312,18 @@ def custom_case(P: int, K: int, N: int, M: int, grid: int, k_max: int, seed: int
     obj = partial_object(M, seed + 1000, kind=kind)
     return Workload(f"partial-P{P}-K{K}-N{N}-M{M}-sdf{grid}-it{k_max}", pre, [obj], K=K, k_max=k_max,
                     k_stein=k_stein_for(k_max) if k_stein is None else k_stein, schedule=schedule)
+
+
+def batched_case(n_objects: int = 64, seed: int = BASE_SEED + 3, k_max: int = 100):
+    """Many objects optimised together: point counts log-uniform in [1024, 32768], particles per
+    (object, preshape) drawn from {128, 256, 512}; 3 preshapes, N=2048, 64^3 SDF.
+
+    Returns (workload, K) with K an int32 array [n_objects, 3] of particle counts (object-major)."""
+    g = rng(seed)
+    Ms = np.exp(g.uniform(np.log(1024.0), np.log(32768.0), n_objects)).astype(int)
+    K = g.choice(np.array([128, 256, 512], np.int32), size=(n_objects, 3)).astype(np.int32)
+    pre = make_preshapes(3, 2048, 64, seed)
+    objs = [partial_object(int(Ms[o]), seed + 1000 * (o + 1)) for o in range(n_objects)]
+    w = Workload(f"batched-{n_objects}obj-M1k-32k-K128-512-P3-N2048-sdf64-it{k_max}", pre, objs, K=int(K.max()),
+                 k_max=k_max, k_stein=k_stein_for(k_max), schedule=0)
+    return w, K
