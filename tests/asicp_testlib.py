@@ -1,9 +1,10 @@
 """Helpers shared by the parity tests: set a workload up on both sides and
 compare the CUDA path (through the C-ABI binding) with the FP64 oracle.
 
-Tolerances (derived in the design doc's parity section):
+Tolerances:
 * correspondences: bit-exact, except near-ties where the FP64 squared distance
-  of the GPU's choice exceeds the minimum by at most NEAR_TIE_REL relative;
+  of the GPU's choice exceeds the minimum by at most NEAR_TIE_REL relative (the
+  float32 exact-form distance the GPU ranks by has ~3 ulp = 2e-7 relative error);
 * collision flags: equal, except points whose FP64 SDF value lies within
   PHI_TOL of zero (float32 transform and interpolation error is ~1e-7 m);
 * cost and gradient: relative error <= COST_GRAD_REL per particle and per block
