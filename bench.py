@@ -40,7 +40,8 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # DRAM bytes (read + write) of one forward-matching launch from the committed ncu capture
 # (profiles/fwd_match_kernel_profile-case-P1-K256-N2048-M8192.md); null once the kernel changes
 FWD_DRAM_BYTES_PER_LAUNCH = 406528
-OPS_PER_PAIR = 3          # FMA-pipe work per particle*point pair: 3 FMAs (the min runs on the separate ALU pipe)
+OPS_PER_PAIR = 4          # algorithmic FP32-lane work per particle*point pair: 3 FMA + 1 compare
+FMA_PER_PAIR = 3          # of which FMA-pipe work (the compare runs as half a 3-input min on the ALU pipe)
 TOPK = 16
 
 
@@ -262,6 +263,7 @@ def run_gpu(args, rank, world, local_rank):
     pairs_per_launch = P * K * N * M
     achieved = pairs_per_launch / match_avg_s / 1e9
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / OPS_PER_PAIR / 1e9
+    peak_fma = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / FMA_PER_PAIR / 1e9
     # match, collide, collide_nn, finalize per pass, Stein per SVGD pass, + init, reset, select, gather
     launches_per_step = 4 * (w.k_max + 1) + w.k_stein + 4
 
@@ -297,8 +299,9 @@ def run_gpu(args, rank, world, local_rank):
                                           "qpt8-chunk64-t128-tile1024); every input is L2-resident, so it does not "
                                           "grow with the launch",
                          "kernel": "fwd_match_kernel", "peak_basis":
-                             f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 FMA/clk x {SM_MAX_MHZ_NOMINAL:.0f} MHz / "
-                             f"{OPS_PER_PAIR} FMA per pair",
+                             f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz / "
+                             f"{OPS_PER_PAIR} lane operations per pair (3 FMA + 1 compare)",
+                         "frac_fma_pipe": achieved / peak_fma, "peak_fma_pipe": peak_fma,
                          "launch_ms": match_avg_s * 1e3,
                          "kernel_share": ms[0] / max(1e-9, sum(ms))},
             "kernel_ms_per_step": {k: v / args.steps for k, v in zip(asicp.KERNEL_KINDS, ms)},
