@@ -12,8 +12,8 @@ from paper_2412_08346_gb300 import asicp
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    with open(os.path.join(ROOT, "include", "asicp.h")) as f:
+def _declared(header="asicp.h"):
+    with open(os.path.join(ROOT, "include", header)) as f:
         text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(asicp_[a-z_]+)\s*\(", text)))
@@ -26,6 +26,27 @@ def test_header_symbols_are_exported():
     for n in names:
         assert hasattr(lib, n), f"{n} declared in include/asicp.h but not exported"
     assert sorted(asicp.EXPORTED) == names
+
+
+def test_proposal_header_symbols_are_exported():
+    from paper_2412_08346_gb300 import proposal
+    lib = asicp.load()
+    names = _declared("asicp_proposal.h")
+    assert "asicp_prop_create" in names and len(names) == 9
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/asicp_proposal.h but not exported"
+    assert sorted(proposal.PROP_EXPORTED) == names
+    from oracle import proposal as orc
+    for P in (1, 3, 10):
+        assert proposal.num_params(P) == orc.num_params(P)
+
+
+def test_proposal_create_rejects_bad_sizes_without_touching_the_gpu():
+    from paper_2412_08346_gb300 import proposal
+    for args in ((0, 256, 4), (3, 8, 4), (3, 256, 0), (17, 256, 4)):
+        with pytest.raises(asicp.AsicpError) as e:
+            proposal.Proposal(*args)
+        assert e.value.status == asicp.ASICP_ERR_INVALID_ARG
 
 
 def test_defaults_follow_table1():
