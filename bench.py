@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--batched", type=int, default=0, metavar="OBJECTS",
                     help="time OBJECTS objects (point counts 1k-32k, 128/256/512 particles per preshape) optimised "
                          "together against each object alone; prints its own JSON line")
+    ap.add_argument("--learned", default="", metavar="TRAIN,TEST",
+                    help="train the initial-pose proposal on TRAIN objects (targets from the plain method) and "
+                         "compare it with the plain method on TEST held-out objects; prints its own JSON line")
+    ap.add_argument("--learned-epochs", type=int, default=60)
     ap.add_argument("--profile-case", action="store_true",
                     help="one short run of a reduced workload (1 preshape x 256 particles, N=2048, M=8192, "
                          "8 iterations, poses close enough to collide) for profiler captures; no JSON line")
@@ -461,8 +465,39 @@ def run_batched(args):
                    "pairs_per_iteration": pairs, "fwd_shape": asicp.FWD_VARIANTS[shape]}}), flush=True)
 
 
+def run_learned(args):
+    """Learned initial poses (64 particles per preshape, 30 iterations) against the plain method
+    (256 Fibonacci particles, 100 iterations) and against Fibonacci at the learned budget."""
+    import torch
+    from paper_2412_08346_gb300 import learned_init, proposal, synth
+    n_train, n_test = (int(x) for x in args.learned.split(","))
+    stream = torch.cuda.current_stream().cuda_stream
+    pre = synth.make_preshapes(3, 2048, 64, synth.BASE_SEED + 5)
+    train_clouds = learned_init.object_clouds(n_train, 2048, synth.BASE_SEED + 50_000)
+    test_clouds = learned_init.object_clouds(n_test, 2048, synth.BASE_SEED + 90_000)
+    t0 = time.perf_counter()
+    targets, _ = learned_init.converged_targets(train_clouds, pre, stream=stream)
+    t_data = time.perf_counter() - t0
+    net = proposal.Proposal(3, 2048, 32, stream)
+    net.set_params(synth.proposal_params(3, synth.BASE_SEED))
+    t0 = time.perf_counter()
+    hist = learned_init.train(net, train_clouds, targets, epochs=args.learned_epochs, batch=32, lr=1e-3, seed=1)
+    t_train = time.perf_counter() - t0
+    res = learned_init.compare(net, test_clouds, pre, stream)
+    res.update({"metric": "ms per grasp set, learned initial poses vs the plain method, at equal cost",
+                "value": res["budgets"][0]["learned_ms_per_grasp_set"], "unit": "ms/grasp set",
+                "higher_is_better": False,
+                "train_objects": n_train, "train_targets_s": t_data, "train_s": t_train,
+                "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "epochs": len(hist),
+                "data": "synthetic", "dtype": "bf16 weights, f32 accumulate"})
+    print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
+    if args.learned:
+        run_learned(args)
+        return
     if args.batched:
         run_batched(args)
         return

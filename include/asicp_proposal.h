@@ -6,18 +6,18 @@
  * and names learned initial poses as future work (Conclusions).  This library
  * provides that proposal: a PointNet-style encoder of the object cloud (shared
  * per-point MLP 3 -> 64 -> 128 -> 256, max-pool over points, MLP 256 -> 256 ->
- * P x 16 x 9) whose outputs parameterise, per preshape, a mixture of 16 SE(3)
+ * P x 16 x 10) whose outputs parameterise, per preshape, a mixture of 16 SE(3)
  * densities (weights, translation means and isotropic spreads relative to the
- * cloud's centroid, Watson rotation means with a fixed concentration 8).
+ * cloud's centroid, Watson rotation densities: mean axis and concentration).
  * Weights and stored activations are bfloat16, products are accumulated in
  * float32; master weights, gradients and the Adam state are float32.
  *
  * Parameter layout (flat float32): W1 [64][3], b1 [64], W2 [128][64], b2 [128],
- * W3 [256][128], b3 [256], W4 [256][256], b4 [256], W5 [P*144][256], b5 [P*144].
- * Raw outputs per preshape p, component c (o[p][c][0..8]): logit, translation
+ * W3 [256][128], b3 [256], W4 [256][256], b4 [256], W5 [P*160][256], b5 [P*160].
+ * Raw outputs per preshape p, component c (o[p][c][0..9]): logit, translation
  * mean / 0.1 m (3), log spread (sigma = 0.1 m exp(clip(o4, -4, 1))), rotation
- * (4, normalised).  Loss of one object: mean over preshapes and target poses of
- * -log p(target).
+ * (4, normalised), log concentration (kappa = 4 exp(clip(o9, -2, 3))).  Loss
+ * of one object: mean over preshapes and target poses of -log p(target).
  *
  * Pointers may be host or device memory (copied with cudaMemcpyDefault) unless
  * stated otherwise; every call runs on the handle's stream and returns when its
@@ -35,7 +35,7 @@ extern "C" {
 #endif
 
 #define ASICP_PROP_COMPONENTS 16
-#define ASICP_PROP_RAW 9              /* raw outputs per component */
+#define ASICP_PROP_RAW 10             /* raw outputs per component */
 #define ASICP_PROP_MAX_TARGETS 128    /* target poses per preshape and object */
 
 typedef struct asicp_prop asicp_prop;
@@ -54,7 +54,7 @@ asicp_status asicp_prop_destroy(asicp_prop *prop);
 asicp_status asicp_prop_set_params(asicp_prop *prop, const float *params);
 asicp_status asicp_prop_get_params(asicp_prop *prop, float *params);
 
-/* Raw mixture outputs out [B][P][16][9] and centroids [B][3] (may be NULL) of B
+/* Raw mixture outputs out [B][P][16][10] and centroids [B][3] (may be NULL) of B
  * object clouds clouds [B][n_points][3]. */
 asicp_status asicp_prop_forward(asicp_prop *prop, const float *clouds, int B, float *out, float *centroids);
 
@@ -69,11 +69,12 @@ asicp_status asicp_prop_loss_grad(asicp_prop *prop, const float *clouds, const f
  * gradient of the last asicp_prop_loss_grad; the bfloat16 weights follow. */
 asicp_status asicp_prop_adam_step(asicp_prop *prop, float lr);
 
-/* Initial poses theta [B][P][K][7] sampled from the mixtures out [B][P][16][9]
+/* Initial poses theta [B][P][K][7] sampled from the mixtures out [B][P][16][10]
  * around centroids [B][3] (both from asicp_prop_forward), with caller-drawn
  * random numbers draws [B][P][K][8] = (u uniform in [0, 1) choosing the component
  * by cumulative weight, then 7 standard normals): t = centroid + mu_c + sigma_c
- * (n1, n2, n3), q = normalise(nu_c + (n4..n7) / 4).  theta may feed asicp_run. */
+ * (n1, n2, n3), q = normalise(nu_c + (n4..n7) / sqrt(2 kappa_c)).  theta may feed
+ * asicp_run. */
 asicp_status asicp_prop_sample(asicp_prop *prop, const float *out, const float *centroids, int B, int K,
                                const float *draws, float *theta);
 

@@ -20,15 +20,19 @@ Weights, the centred input and the stored activations (h1, h2, h3, g, z) are
 bfloat16 values (round to nearest even); products and sums are exact here and
 float32 on the GPU.
 
-Mixture (per preshape p, component c; raw outputs o[p, c, 0..8]):
+Mixture (per preshape p, component c; raw outputs o[p, c, 0..9]):
     pi_c    = softmax_c(o0)
     mu_c    = 0.1 (o1, o2, o3)                     translation relative to the centroid
     sigma_c = 0.1 exp(clip(o4, -4, 1))             isotropic translation spread
     nu_c    = (o5..o8) / max(|o5..o8|, 1e-6)       rotation mean (unit quaternion)
+    kappa_c = 4 exp(clip(o9, -2, 3))               rotational concentration
     log p(t, q) = LSE_c [log pi_c - |t' - mu_c|^2 / (2 sigma_c^2) - 3 log sigma_c
-                         + kappa ((nu_c . q)^2 - 1)] - 1.5 log(2 pi)
-with t' = t - centroid and a fixed concentration kappa (a Watson density on
-the quaternion sphere, so q and -q score alike; its normaliser is constant).
+                         + kappa_c (nu_c . q)^2 - log M(1/2, 2, kappa_c)]
+                  - 1.5 log(2 pi) - log(2 pi^2)
+with t' = t - centroid: a Gaussian in translation times a Watson density on the
+quaternion sphere S^3 (so q and -q score alike), M = Kummer's confluent
+hypergeometric function 1F1 (the Watson normaliser; d/dk log M(1/2, 2, k) =
+M(3/2, 3, k) / (4 M(1/2, 2, k))) and 2 pi^2 the area of S^3.
 Loss of one object: L = -(1 / (P T)) sum_p sum_j log p_p(t_pj, q_pj) over T
 target poses per preshape.
 """
@@ -37,8 +41,7 @@ from __future__ import annotations
 import numpy as np
 
 C_COMP = 16          # mixture components per preshape
-N_RAW = 9            # raw outputs per component
-KAPPA = 8.0          # rotational concentration
+N_RAW = 10           # raw outputs per component
 HIDDEN = (64, 128, 256)
 HEAD = 256
 
@@ -76,18 +79,6 @@ def bf16(x: np.ndarray) -> np.ndarray:
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def init_params(P: int, seed: int) -> np.ndarray:
-    """He-style initialisation (float32 master values)."""
-    g = np.random.default_rng(seed)
-    layers = []
-    for o, i in layer_shapes(P):
-        W = g.normal(0.0, np.sqrt(2.0 / i), (o, i))
-        layers.append((W, np.zeros(o)))
-    W5, b5 = layers[-1]
-    layers[-1] = (W5 * 0.1, b5)
-    return flatten(layers).astype(np.float32)
-
-
 def forward(flat: np.ndarray, cloud: np.ndarray, P: int, round_bf16: bool = True):
     """One object: returns (o [P, C, 9], cache for backward, centroid).  round_bf16=False
     keeps every value in float64 (for finite-difference checks of the backward pass)."""
@@ -108,8 +99,15 @@ def forward(flat: np.ndarray, cloud: np.ndarray, P: int, round_bf16: bool = True
     return o.reshape(P, C_COMP, N_RAW), cache, cen
 
 
+def log_kummer(k):
+    """log M(1/2, 2, k) and its derivative (scipy's 1F1)."""
+    from scipy.special import hyp1f1
+    m = hyp1f1(0.5, 2.0, k)
+    return np.log(m), 0.25 * hyp1f1(1.5, 3.0, k) / m
+
+
 def mixture(o: np.ndarray):
-    """Mixture parameters of one preshape from its raw outputs o [C, 9]."""
+    """Mixture parameters of one preshape from its raw outputs o [C, 10]."""
     a = o[:, 0]
     logpi = a - (a.max() + np.log(np.exp(a - a.max()).sum()))
     mu = 0.1 * o[:, 1:4]
@@ -118,17 +116,22 @@ def mixture(o: np.ndarray):
     v = o[:, 5:9]
     nv = np.maximum(np.linalg.norm(v, axis=1), 1e-6)
     nu = v / nv[:, None]
-    return logpi, mu, sigma, nu
+    kappa = 4.0 * np.exp(np.clip(o[:, 9], -2.0, 3.0))
+    return logpi, mu, sigma, nu, kappa
+
+
+CONST = -1.5 * np.log(2 * np.pi) - np.log(2 * np.pi ** 2)
 
 
 def log_density(o: np.ndarray, t_rel: np.ndarray, q: np.ndarray) -> np.ndarray:
     """log p(t, q) of one preshape's mixture at poses (t relative to the centroid)."""
-    logpi, mu, sigma, nu = mixture(o)
+    logpi, mu, sigma, nu, kappa = mixture(o)
+    lm, _ = log_kummer(kappa)
     d2 = ((t_rel[:, None, :] - mu[None, :, :]) ** 2).sum(-1)
     dot = q @ nu.T
-    ell = logpi[None, :] - d2 / (2 * sigma[None, :] ** 2) - 3 * np.log(sigma)[None, :] + KAPPA * (dot ** 2 - 1.0)
+    ell = logpi[None, :] - d2 / (2 * sigma[None, :] ** 2) - 3 * np.log(sigma)[None, :] + kappa * dot ** 2 - lm
     m = ell.max(1, keepdims=True)
-    return (m + np.log(np.exp(ell - m).sum(1, keepdims=True)))[:, 0] - 1.5 * np.log(2 * np.pi)
+    return (m + np.log(np.exp(ell - m).sum(1, keepdims=True)))[:, 0] + CONST
 
 
 def loss_and_grad_o(o: np.ndarray, targets: np.ndarray, cen: np.ndarray):
@@ -141,14 +144,15 @@ def loss_and_grad_o(o: np.ndarray, targets: np.ndarray, cen: np.ndarray):
     for p in range(P):
         t = targets[p, :, :3] - cen
         q = targets[p, :, 3:7]
-        logpi, mu, sigma, nu = mixture(o[p])
+        logpi, mu, sigma, nu, kappa = mixture(o[p])
+        lm, dlm = log_kummer(kappa)
         diff = t[:, None, :] - mu[None, :, :]                          # [T, C, 3]
         d2 = (diff ** 2).sum(-1)
         dot = q @ nu.T
-        ell = logpi[None, :] - d2 / (2 * sigma ** 2) - 3 * np.log(sigma) + KAPPA * (dot ** 2 - 1.0)
+        ell = logpi[None, :] - d2 / (2 * sigma ** 2) - 3 * np.log(sigma) + kappa * dot ** 2 - lm
         m = ell.max(1, keepdims=True)
         lse = m[:, 0] + np.log(np.exp(ell - m).sum(1))
-        loss -= (lse - 1.5 * np.log(2 * np.pi)).sum()
+        loss -= (lse + CONST).sum()
         r = np.exp(ell - lse[:, None])                                  # responsibilities [T, C]
         pi = np.exp(logpi)
         w = -1.0 / (P * T)
@@ -159,11 +163,14 @@ def loss_and_grad_o(o: np.ndarray, targets: np.ndarray, cen: np.ndarray):
         dsig = (r * (d2 / sigma ** 3 - 3.0 / sigma)).sum(0)
         inside = (o[p, :, 4] > -4.0) & (o[p, :, 4] < 1.0)
         go[p, :, 4] += w * np.where(inside, dsig * sigma, 0.0)
-        dnu = (r[:, :, None] * (2 * KAPPA * dot[:, :, None]) * q[:, None, :]).sum(0)   # [C, 4]
+        dnu = (r[:, :, None] * (2 * kappa[None, :, None] * dot[:, :, None]) * q[:, None, :]).sum(0)   # [C, 4]
         v = o[p, :, 5:9]
         nv = np.maximum(np.linalg.norm(v, axis=1), 1e-6)
         proj = dnu - (dnu * nu).sum(1, keepdims=True) * nu
         go[p, :, 5:9] += w * proj / nv[:, None]
+        dkap = (r * (dot ** 2 - dlm[None, :])).sum(0)
+        kin = (o[p, :, 9] > -2.0) & (o[p, :, 9] < 3.0)
+        go[p, :, 9] += w * np.where(kin, dkap * kappa, 0.0)
     return loss / (P * T), go
 
 
@@ -212,15 +219,16 @@ def adam(flat, grad, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
 def sample(o: np.ndarray, cen: np.ndarray, draws: np.ndarray) -> np.ndarray:
     """Initial poses from one preshape's mixture: draws [K, 8] = (u, n1..n7) with u uniform in
     [0, 1) picking the component by its cumulative weight, n standard normal.
-    t = centroid + mu_c + sigma_c (n1, n2, n3); q = normalise(nu_c + (n4..n7) / sqrt(2 kappa))."""
-    logpi, mu, sigma, nu = mixture(o)
+    t = centroid + mu_c + sigma_c (n1, n2, n3); q = normalise(nu_c + (n4..n7) / sqrt(2 kappa_c))
+    (a Gaussian perturbation of the mean axis: close to the Watson density for large kappa)."""
+    logpi, mu, sigma, nu, kappa = mixture(o)
     cdf = np.cumsum(np.exp(logpi))
     out = np.zeros((draws.shape[0], 7))
     for k, d in enumerate(draws):
         c = int(np.searchsorted(cdf, d[0] * cdf[-1], side="right"))
         c = min(c, C_COMP - 1)
         t = cen + mu[c] + sigma[c] * d[1:4]
-        q = nu[c] + d[4:8] / np.sqrt(2 * KAPPA)
+        q = nu[c] + d[4:8] / np.sqrt(2 * kappa[c])
         out[k, :3] = t
         out[k, 3:] = q / np.linalg.norm(q)
     return out

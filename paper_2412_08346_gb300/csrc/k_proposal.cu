@@ -9,12 +9,14 @@
 // Network (x_i = r_i - centroid; W row-major [out][in]):
 //   h1 = relu(W1 x + b1) 3->64, h2 = relu(W2 h1 + b2) 64->128,
 //   h3 = relu(W3 h2 + b3) 128->256, g = max over points (ties: lowest point),
-//   z = relu(W4 g + b4) 256->256, o = W5 z + b5 256->P*16*9.
-// Mixture per preshape p, component c (raw o[0..8]): pi = softmax(o0),
-// mu = 0.1 (o1, o2, o3), sigma = 0.1 exp(clip(o4, -4, 1)), nu = (o5..o8)/|.|;
-// log p(t, q) = LSE_c[log pi_c - |t' - mu_c|^2 / (2 sigma_c^2) - 3 log sigma_c
-// + kappa ((nu_c.q)^2 - 1)] - 1.5 log 2 pi, kappa = 8 (a Watson density: q and -q
-// score alike).  Loss of one object: -(1 / (P T)) sum over preshapes and targets.
+//   z = relu(W4 g + b4) 256->256, o = W5 z + b5 256->P*16*10.
+// Mixture per preshape p, component c (raw o[0..9]): pi = softmax(o0),
+// mu = 0.1 (o1, o2, o3), sigma = 0.1 exp(clip(o4, -4, 1)), nu = (o5..o8)/|.|,
+// kappa = 4 exp(clip(o9, -2, 3)); log p(t, q) = LSE_c[log pi_c - |t' - mu_c|^2 /
+// (2 sigma_c^2) - 3 log sigma_c + kappa_c (nu_c.q)^2 - log M(1/2, 2, kappa_c)]
+// - 1.5 log 2 pi - log 2 pi^2: a Gaussian in translation times a Watson density on
+// the quaternion sphere (q and -q score alike; M = Kummer's 1F1, summed as its
+// series).  Loss of one object: -(1 / (P T)) sum over preshapes and targets.
 //
 // Backward: the per-object gradients are written to per-object slices and
 // summed in object order, so a training step is deterministic.
@@ -35,7 +37,6 @@ namespace {
 typedef __nv_bfloat16 bf16;
 constexpr int kC = ASICP_PROP_COMPONENTS, kRaw = ASICP_PROP_RAW;
 constexpr int kH1 = 64, kH2 = 128, kH3 = 256, kHead = 256;
-constexpr float kKappa = 8.f;
 constexpr int kMaxPre = 16, kMaxPoints = 65536, kMaxBatch = 256;
 
 struct Layer {
@@ -219,27 +220,45 @@ __global__ void maxpool_kernel(const bf16 *h3, int npts, bf16 *g, int *arg)
 }
 
 struct Mix {
-    float logpi[kC], mu[kC][3], sigma[kC], nu[kC][4], nv[kC];
-    int inside[kC];
+    float logpi[kC], mu[kC][3], sigma[kC], nu[kC][4], nv[kC], kappa[kC], logm[kC], dlogm[kC];
+    int inside[kC], kin[kC];
 };
 
-__device__ void mixture_params(const float *o, Mix &m)
+// Kummer's 1F1(a; b; k) by its series (k <= 80 here: under 200 terms)
+__device__ double kummer(double a, double b, double k)
 {
-    float amax = -INFINITY;
-    for (int c = 0; c < kC; ++c) amax = fmaxf(amax, o[c * kRaw]);
-    float se = 0.f;
-    for (int c = 0; c < kC; ++c) se += expf(o[c * kRaw] - amax);
-    const float lse = amax + logf(se);
-    for (int c = 0; c < kC; ++c) {
-        const float *oc = o + c * kRaw;
-        m.logpi[c] = oc[0] - lse;
-        for (int k = 0; k < 3; ++k) m.mu[c][k] = 0.1f * oc[1 + k];
-        m.inside[c] = oc[4] > -4.f && oc[4] < 1.f;
-        m.sigma[c] = 0.1f * expf(fminf(fmaxf(oc[4], -4.f), 1.f));
-        const float n = fmaxf(sqrtf(oc[5] * oc[5] + oc[6] * oc[6] + oc[7] * oc[7] + oc[8] * oc[8]), 1e-6f);
-        m.nv[c] = n;
-        for (int k = 0; k < 4; ++k) m.nu[c][k] = oc[5 + k] / n;
+    double t = 1.0, s = 1.0;
+    for (int n = 0; n < 400; ++n) {
+        t *= (a + n) / (b + n) * k / (n + 1);
+        s += t;
+        if (t < 1e-17 * s) break;
     }
+    return s;
+}
+
+// Mixture parameters of one preshape from its raw outputs; thread c < kC fills
+// component c (call with at least kC threads, then synchronise).
+__device__ void mixture_params(const float *o, Mix &m, int c)
+{
+    if (c >= kC) return;
+    float amax = -INFINITY;
+    for (int e = 0; e < kC; ++e) amax = fmaxf(amax, o[e * kRaw]);
+    float se = 0.f;
+    for (int e = 0; e < kC; ++e) se += expf(o[e * kRaw] - amax);
+    const float *oc = o + c * kRaw;
+    m.logpi[c] = oc[0] - (amax + logf(se));
+    for (int k = 0; k < 3; ++k) m.mu[c][k] = 0.1f * oc[1 + k];
+    m.inside[c] = oc[4] > -4.f && oc[4] < 1.f;
+    m.sigma[c] = 0.1f * expf(fminf(fmaxf(oc[4], -4.f), 1.f));
+    const float n = fmaxf(sqrtf(oc[5] * oc[5] + oc[6] * oc[6] + oc[7] * oc[7] + oc[8] * oc[8]), 1e-6f);
+    m.nv[c] = n;
+    for (int k = 0; k < 4; ++k) m.nu[c][k] = oc[5 + k] / n;
+    m.kin[c] = oc[9] > -2.f && oc[9] < 3.f;
+    const float kap = 4.f * expf(fminf(fmaxf(oc[9], -2.f), 3.f));
+    m.kappa[c] = kap;
+    const double m0 = kummer(0.5, 2.0, kap), m1 = kummer(1.5, 3.0, kap);
+    m.logm[c] = (float)log(m0);
+    m.dlogm[c] = (float)(0.25 * m1 / m0);
 }
 
 // Loss of preshape p of object b and its gradient with respect to the raw outputs.
@@ -255,7 +274,7 @@ __global__ void __launch_bounds__(kLossThreads) loss_kernel(const float *out, co
     __shared__ float lpart[kLossThreads / 32];
     const int p = blockIdx.x, b = blockIdx.y, j = threadIdx.x, lane = j & 31, warp = j >> 5;
     const float *o = out + ((size_t)b * P + p) * kC * kRaw;
-    if (j == 0) mixture_params(o, mx);
+    mixture_params(o, mx, j);
     __syncthreads();
     const bool live = j < T;
     float t[3] = {0.f, 0.f, 0.f}, q[4] = {1.f, 0.f, 0.f, 0.f};
@@ -274,13 +293,14 @@ __global__ void __launch_bounds__(kLossThreads) loss_kernel(const float *out, co
         d2[c] = dd;
         dot[c] = dq;
         const float s = mx.sigma[c];
-        ell[c] = mx.logpi[c] - dd / (2.f * s * s) - 3.f * logf(s) + kKappa * (dq * dq - 1.f);
+        ell[c] = mx.logpi[c] - dd / (2.f * s * s) - 3.f * logf(s) + mx.kappa[c] * dq * dq - mx.logm[c];
         emax = fmaxf(emax, ell[c]);
     }
     float se = 0.f;
     for (int c = 0; c < kC; ++c) se += expf(ell[c] - emax);
     const float lse = emax + logf(se);
-    float nll = live ? -(lse - 1.5f * logf(2.f * 3.14159265358979f)) : 0.f;
+    // constant: -1.5 log(2 pi) - log(2 pi^2)
+    float nll = live ? -(lse - 2.75681559961402f - 2.98260695225875f) : 0.f;
     const float w = -1.f / (float)(P * T);
     for (int c = 0; c < kC; ++c) {
         const float r = live ? expf(ell[c] - lse) : 0.f;
@@ -290,8 +310,9 @@ __global__ void __launch_bounds__(kLossThreads) loss_kernel(const float *out, co
         for (int k = 0; k < 3; ++k) v[1 + k] = w * 0.1f * r * (t[k] - mx.mu[c][k]) / (s * s);
         v[4] = mx.inside[c] ? w * r * (d2[c] / (s * s * s) - 3.f / s) * s : 0.f;
         float dn[4], pr = 0.f;
-        for (int k = 0; k < 4; ++k) { dn[k] = r * 2.f * kKappa * dot[c] * q[k]; pr = fmaf(dn[k], mx.nu[c][k], pr); }
+        for (int k = 0; k < 4; ++k) { dn[k] = r * 2.f * mx.kappa[c] * dot[c] * q[k]; pr = fmaf(dn[k], mx.nu[c][k], pr); }
         for (int k = 0; k < 4; ++k) v[5 + k] = w * (dn[k] - pr * mx.nu[c][k]) / mx.nv[c];
+        v[9] = mx.kin[c] ? w * r * (dot[c] * dot[c] - mx.dlogm[c]) * mx.kappa[c] : 0.f;
         for (int k = 0; k < kRaw; ++k) {
             float x = v[k];
             for (int o2 = 16; o2 > 0; o2 >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o2);
@@ -384,8 +405,10 @@ __global__ void sample_kernel(const float *out, const float *cen, const float *d
     float *th = theta + e * 7;
     for (int k = 0; k < 3; ++k) th[k] = cen[b * 3 + k] + 0.1f * oc[1 + k] + sigma * d[1 + k];
     const float n = fmaxf(sqrtf(oc[5] * oc[5] + oc[6] * oc[6] + oc[7] * oc[7] + oc[8] * oc[8]), 1e-6f);
+    const float kap = 4.f * expf(fminf(fmaxf(oc[9], -2.f), 3.f));
+    const float spread = rsqrtf(2.f * kap);
     float qv[4], qq = 0.f;
-    for (int k = 0; k < 4; ++k) { qv[k] = oc[5 + k] / n + d[4 + k] * 0.25f; qq = fmaf(qv[k], qv[k], qq); }
+    for (int k = 0; k < 4; ++k) { qv[k] = oc[5 + k] / n + d[4 + k] * spread; qq = fmaf(qv[k], qv[k], qq); }
     const float inv = 1.f / sqrtf(qq);
     for (int k = 0; k < 4; ++k) th[3 + k] = qv[k] * inv;
 }

@@ -16,7 +16,7 @@ PROP_EXPORTED = ("asicp_prop_num_params", "asicp_prop_create", "asicp_prop_destr
                  "asicp_prop_get_params", "asicp_prop_forward", "asicp_prop_loss_grad", "asicp_prop_adam_step",
                  "asicp_prop_sample")
 COMPONENTS = 16
-RAW = 9
+RAW = 10
 MAX_TARGETS = 128
 
 _ready = False
@@ -80,7 +80,7 @@ class Proposal:
         return out
 
     def forward(self, clouds, B: int, out=None, centroids=None):
-        """Raw mixture outputs [B, P, 16, 9] and centroids [B, 3] (numpy unless buffers are given)."""
+        """Raw mixture outputs [B, P, 16, 10] and centroids [B, 3] (numpy unless buffers are given)."""
         if out is None:
             out = np.zeros((B, self.P, COMPONENTS, RAW), np.float32)
         if centroids is None:

@@ -327,3 +327,15 @@ def batched_case(n_objects: int = 64, seed: int = BASE_SEED + 3, k_max: int = 10
     w = Workload(f"batched-{n_objects}obj-M1k-32k-K128-512-P3-N2048-sdf64-it{k_max}", pre, objs, K=int(K.max()),
                  k_max=k_max, k_stein=k_stein_for(k_max), schedule=0)
     return w, K
+
+
+def proposal_params(P: int, seed: int) -> np.ndarray:
+    """Seeded initial weights of the proposal network (flat float32, layout of
+    include/asicp_proposal.h): He-normal matrices, zero biases, the output layer scaled by 0.1."""
+    g = rng(seed)
+    dims = [(64, 3), (128, 64), (256, 128), (256, 256), (P * 16 * 10, 256)]
+    parts = []
+    for li, (o, i) in enumerate(dims):
+        W = g.normal(0.0, np.sqrt(2.0 / i), (o, i)) * (0.1 if li == 4 else 1.0)
+        parts += [W.ravel(), np.zeros(o)]
+    return np.concatenate(parts).astype(np.float32)

@@ -45,8 +45,8 @@ def net():
 
 
 def test_forward_matches_oracle(net):
-    params = orc.init_params(P, 11)
-    params[orc.num_params(P) - P * 144:] = np.random.default_rng(3).normal(0, 0.5, P * 144)   # non-zero b5
+    params = synth.proposal_params(P, 11)
+    params[orc.num_params(P) - P * 160:] = np.random.default_rng(3).normal(0, 0.5, P * 160)   # non-zero b5
     net.set_params(params)
     clouds, _ = _batch(4, 21)
     out, cen = net.forward(clouds, 4)
@@ -57,7 +57,7 @@ def test_forward_matches_oracle(net):
 
 
 def test_loss_and_gradient_match_oracle(net):
-    params = orc.init_params(P, 12)
+    params = synth.proposal_params(P, 12)
     net.set_params(params)
     clouds, tg = _batch(4, 31)
     loss, grad = net.loss_grad(clouds, tg, 4, T, want_grad=True)
@@ -73,7 +73,7 @@ def test_loss_and_gradient_match_oracle(net):
 
 
 def test_adam_step_matches_oracle(net):
-    params = orc.init_params(P, 13)
+    params = synth.proposal_params(P, 13)
     net.set_params(params)
     clouds, tg = _batch(2, 41)
     _, grad = net.loss_grad(clouds, tg, 2, T, want_grad=True)
@@ -85,8 +85,8 @@ def test_adam_step_matches_oracle(net):
 
 
 def test_sampling_matches_oracle(net):
-    params = orc.init_params(P, 14)
-    params[orc.num_params(P) - P * 144:] = np.random.default_rng(5).normal(0, 1.0, P * 144)
+    params = synth.proposal_params(P, 14)
+    params[orc.num_params(P) - P * 160:] = np.random.default_rng(5).normal(0, 1.0, P * 160)
     net.set_params(params)
     clouds, _ = _batch(2, 51)
     out, cen = net.forward(clouds, 2)
@@ -105,7 +105,7 @@ def test_sampling_matches_oracle(net):
 
 
 def test_training_reduces_the_loss(net):
-    net.set_params(orc.init_params(P, 15))
+    net.set_params(synth.proposal_params(P, 15))
     clouds, tg = _batch(8, 61)
     first, _ = net.loss_grad(clouds, tg, 8, T)
     for _ in range(60):
@@ -113,3 +113,30 @@ def test_training_reduces_the_loss(net):
         net.adam_step(3e-3)
     last, _ = net.loss_grad(clouds, tg, 8, T)
     assert last < first - 0.5, (first, last)
+
+
+def test_trained_proposal_generalises_to_held_out_objects():
+    """Targets from the plain method on procedural objects; after training, the loss on held-out
+    objects is well below the untrained network's (the network has learned where good grasps of
+    unseen objects lie), and its samples feed asicp_run."""
+    from paper_2412_08346_gb300 import asicp, learned_init
+    stream = torch.cuda.current_stream().cuda_stream
+    npts = 1024
+    pre = synth.make_preshapes(3, 512, 32, synth.BASE_SEED + 9)
+    train_c = learned_init.object_clouds(160, npts, synth.BASE_SEED + 70_000)
+    test_c = learned_init.object_clouds(32, npts, synth.BASE_SEED + 80_000)
+    tg_train, _ = learned_init.converged_targets(train_c, pre, K=96, k_max=40, stream=stream)
+    tg_test, _ = learned_init.converged_targets(test_c, pre, K=96, k_max=40, stream=stream)
+    net = proposal.Proposal(3, npts, 32, stream)
+    try:
+        net.set_params(synth.proposal_params(3, 17))
+        before, _ = net.loss_grad(test_c, tg_test, 32, tg_test.shape[2])
+        hist = learned_init.train(net, train_c, tg_train, epochs=40, batch=32, lr=1e-3, seed=3)
+        after, _ = net.loss_grad(test_c, tg_test, 32, tg_test.shape[2])
+        print(f"held-out loss {before:.3f} -> {after:.3f}; training {hist[0]:.3f} -> {hist[-1]:.3f}")
+        assert after < before - 1.0
+        th0, _ = learned_init.propose(net, test_c[:4], 32, seed=1)
+        best, _ = learned_init.run_grasp_sets(test_c[:4], pre, 32, 10, stream, theta0=th0, batch=4)
+        assert np.all(np.isfinite(best))
+    finally:
+        net.close()

@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 from oracle import proposal as pr
+from paper_2412_08346_gb300 import synth
 
 
 def _rand_targets(g, P, T):
@@ -23,17 +24,33 @@ def test_bf16_rounding_known_values():
 
 
 def test_single_component_density_is_gaussian_times_watson():
-    """With one logit dominating, log p = log N(t; mu, sigma^2 I) + kappa((nu.q)^2 - 1)."""
+    """With one logit dominating, p = N(t; mu, sigma^2 I) x Watson(q; nu, kappa) on S^3."""
+    from scipy.special import hyp1f1
     from scipy.stats import multivariate_normal
     g = np.random.default_rng(1)
     o = g.normal(size=(pr.C_COMP, pr.N_RAW))
     o[:, 0] = -80.0
     o[3, 0] = 80.0
-    logpi, mu, sigma, nu = pr.mixture(o)
+    logpi, mu, sigma, nu, kappa = pr.mixture(o)
     t = g.normal(0, 0.05, (5, 3))
     q = g.normal(size=(5, 4)); q /= np.linalg.norm(q, axis=1, keepdims=True)
-    ref = multivariate_normal(mu[3], sigma[3] ** 2 * np.eye(3)).logpdf(t) + pr.KAPPA * ((q @ nu[3]) ** 2 - 1)
+    watson = np.exp(kappa[3] * (q @ nu[3]) ** 2) / (hyp1f1(0.5, 2.0, kappa[3]) * 2 * np.pi ** 2)
+    ref = multivariate_normal(mu[3], sigma[3] ** 2 * np.eye(3)).logpdf(t) + np.log(watson)
     assert np.allclose(pr.log_density(o, t, q), ref, rtol=0, atol=1e-9)
+
+
+def test_rotation_factor_integrates_to_one_on_s3():
+    """Monte Carlo over uniform unit quaternions: E[exp(kappa (nu.q)^2) / M(1/2, 2, kappa)] = 1."""
+    g = np.random.default_rng(11)
+    q = g.normal(size=(400000, 4)); q /= np.linalg.norm(q, axis=1, keepdims=True)
+    nu = np.array([0.5, -0.5, 0.5, 0.5])
+    for kappa in (0.6, 4.0, 15.0):
+        lm, dlm = pr.log_kummer(np.array([kappa]))
+        mean = np.exp(kappa * (q @ nu) ** 2 - lm[0]).mean()
+        assert abs(mean - 1.0) < 0.02 * max(1.0, np.sqrt(kappa)), (kappa, mean)
+        h = 1e-5    # the derivative of log M against central differences
+        fd = (pr.log_kummer(np.array([kappa + h]))[0][0] - pr.log_kummer(np.array([kappa - h]))[0][0]) / (2 * h)
+        assert abs(fd - dlm[0]) < 1e-7
 
 
 def test_density_is_antipodal_invariant():
@@ -48,12 +65,13 @@ def test_output_gradient_matches_finite_differences():
     g = np.random.default_rng(3)
     P, T = 2, 5
     o = g.normal(size=(P, pr.C_COMP, pr.N_RAW))
-    o[..., 4] = g.uniform(-3.5, 0.5, (P, pr.C_COMP))          # inside the clip range
+    o[..., 4] = g.uniform(-3.5, 0.5, (P, pr.C_COMP))          # inside the clip ranges
+    o[..., 9] = g.uniform(-1.5, 2.5, (P, pr.C_COMP))
     tg = _rand_targets(g, P, T)
     cen = g.normal(0, 0.01, 3)
     _, go = pr.loss_and_grad_o(o, tg, cen)
     h = 1e-6
-    for idx in [(0, 0, 0), (1, 5, 2), (0, 7, 4), (1, 3, 6), (0, 15, 8), (1, 9, 1)]:
+    for idx in [(0, 0, 0), (1, 5, 2), (0, 7, 4), (1, 3, 6), (0, 15, 8), (1, 9, 1), (0, 4, 9), (1, 12, 9)]:
         op, om = o.copy(), o.copy()
         op[idx] += h; om[idx] -= h
         fd = (pr.loss_and_grad_o(op, tg, cen)[0] - pr.loss_and_grad_o(om, tg, cen)[0]) / (2 * h)
@@ -64,7 +82,7 @@ def test_parameter_gradient_matches_finite_differences():
     """Backward pass of the whole network (float64, no bf16 rounding) against central differences."""
     g = np.random.default_rng(4)
     P = 1
-    flat = pr.init_params(P, 5).astype(np.float64)
+    flat = synth.proposal_params(P, 5).astype(np.float64)
     clouds = [g.normal(0, 0.05, (40, 3)) + 0.2, g.normal(0, 0.04, (40, 3))]
     tgs = [_rand_targets(g, P, 4), _rand_targets(g, P, 4)]
     _, grad = pr.loss_and_grad(flat, clouds, tgs, P, round_bf16=False)
@@ -82,7 +100,7 @@ def test_parameter_gradient_matches_finite_differences():
 
 def test_maxpool_ties_go_to_the_lowest_point():
     P = 1
-    flat = pr.init_params(P, 6).astype(np.float64)
+    flat = synth.proposal_params(P, 6).astype(np.float64)
     cloud = np.zeros((8, 3))          # every point identical: every channel ties across points
     cloud[:, 0] = 0.1
     _, cache, _ = pr.forward(flat, cloud, P)
