@@ -12,5 +12,5 @@ this module builds it with gcc and wraps it with ctypes.
 """
 from .oracle import (  # noqa: F401
     Oracle, build, rotation, rot_jacobian, nn, trilinear, gamma, bandwidth,
-    stein_direction, fibonacci_init, select, centroid,
+    stein_direction, fibonacci_init, quarter_init, select, centroid,
 )

@@ -376,6 +376,35 @@ void orc_fibonacci_init(int K, const double com[3], double radius, double *theta
     }
 }
 
+/* Variant of the initialisation used in the paper's experiments (Section VI-A,
+ * Fig. 3 (b)): Fibonacci points on the quarter of the sphere facing the robot,
+ * plus six initialisations directly above the object.  Readings: the quarter is
+ * z >= 0 and x >= 0 relative to the CoM (robot along +x); the lattice is the
+ * spiral z_j = 1 - (j + 1/2)/n, azimuth (j * golden angle mod pi) - pi/2, which is
+ * uniform in area on that quarter; the last min(6, K) particles sit at
+ * CoM + radius e_z, approach axis -e_z, yawed by 0, 60, ..., 300 degrees. */
+void orc_quarter_init(int K, const double com[3], double radius, double *theta)
+{
+    const double ga = M_PI * (3.0 - sqrt(5.0));
+    const int n_above = K < 6 ? K : 6, nq = K - n_above;
+    for (int j = 0; j < K; ++j) {
+        double *th = theta + j * 7;
+        if (j < nq) {
+            double z = 1.0 - (j + 0.5) / nq;
+            double rho = sqrt(fmax(0.0, 1.0 - z * z));
+            double phi = fmod(j * ga, M_PI) - 0.5 * M_PI;
+            double u[3] = {rho * cos(phi), rho * sin(phi), z};
+            for (int a = 0; a < 3; ++a) th[a] = com[a] + radius * u[a];
+            th[3] = 1.0 - u[2]; th[4] = u[1]; th[5] = -u[0]; th[6] = 0.0;   /* +z -> -u */
+            normalize_q(th + 3);
+        } else {
+            double half = (j - nq) * M_PI / 6.0;     /* half of the yaw angle */
+            th[0] = com[0]; th[1] = com[1]; th[2] = com[2] + radius;
+            th[3] = 0.0; th[4] = cos(half); th[5] = sin(half); th[6] = 0.0;  /* yaw about z after pi about x */
+        }
+    }
+}
+
 static void particle_cost_grad(const orc_problem *pb, const orc_state *st, int p, int j,
                                double *cost, double g[7], int *ncol)
 {

@@ -72,6 +72,7 @@ double orc_bandwidth(const double *theta, int K, const orc_schedule *sc);
 void orc_stein_direction(const double *theta, const double *grad, int K, int N,
                          double gamma, double h, double *phi);
 void orc_fibonacci_init(int K, const double com[3], double radius, double *theta);
+void orc_quarter_init(int K, const double com[3], double radius, double *theta);
 void orc_centroid(const double *X, int n, double c[3]);
 void orc_step(const orc_problem *pb, const orc_schedule *sc, orc_state *st, int k, int nthreads);
 void orc_evaluate(const orc_problem *pb, orc_state *st, int nthreads);

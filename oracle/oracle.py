@@ -73,6 +73,7 @@ def _load():
         lib.orc_bandwidth.restype = C.c_double
         lib.orc_stein_direction.argtypes = [_dp, _dp, C.c_int, C.c_int, C.c_double, C.c_double, _dp]
         lib.orc_fibonacci_init.argtypes = [C.c_int, _dp, C.c_double, _dp]
+        lib.orc_quarter_init.argtypes = [C.c_int, _dp, C.c_double, _dp]
         lib.orc_centroid.argtypes = [_dp, C.c_int, _dp]
         lib.orc_step.argtypes = [C.POINTER(_Problem), C.POINTER(_Schedule), C.POINTER(_State), C.c_int, C.c_int]
         lib.orc_evaluate.argtypes = [C.POINTER(_Problem), C.POINTER(_State), C.c_int]
@@ -156,6 +157,14 @@ def fibonacci_init(K, com, radius):
     c, cp = _d(com)
     out = np.zeros((K, 7))
     _load().orc_fibonacci_init(int(K), cp, float(radius), out.ctypes.data_as(_dp))
+    return out
+
+
+def quarter_init(K, com, radius):
+    """Quarter-sphere Fibonacci initialisation plus six poses above the object (see the C source)."""
+    c, cp = _d(com)
+    out = np.zeros((K, 7))
+    _load().orc_quarter_init(int(K), cp, float(radius), out.ctypes.data_as(_dp))
     return out
 
 

@@ -339,3 +339,16 @@ def proposal_params(P: int, seed: int) -> np.ndarray:
         W = g.normal(0.0, np.sqrt(2.0 / i), (o, i)) * (0.1 if li == 4 else 1.0)
         parts += [W.ravel(), np.zeros(o)]
     return np.concatenate(parts).astype(np.float32)
+
+
+def table_points(n: int, obj_points: np.ndarray, seed: int, extent: float = 0.30, gap: float = 0.002,
+                 noise: float = 0.001) -> np.ndarray:
+    """A table under the object (the collision cloud C of Section IV-C holds the object and the
+    table): n points uniform on a square of side `extent` centred under the object's centroid,
+    `gap` below its lowest point, with normal noise."""
+    g = rng(seed)
+    c = obj_points.mean(0)
+    z = obj_points[:, 2].min() - gap
+    xy = c[:2] + g.uniform(-extent / 2, extent / 2, (n, 2))
+    pts = np.concatenate([xy, np.full((n, 1), z)], 1) + g.normal(0.0, noise, (n, 3))
+    return pts.astype(np.float32)

@@ -495,3 +495,38 @@ def test_tensor_core_matching_equals_float32_matching(stream):
             assert rel.max() <= tl.NEAR_TIE_REL, f"non-tie mismatch, relative gap {rel.max():.3e}"
             assert n_diff <= 1e-4 * a["nn_idx"].size
         assert np.allclose(a["cost"], b["cost"], rtol=1e-6, atol=0)
+
+
+def test_separate_collision_cloud_with_a_table(stream):
+    """Matching against the object R, collision test against C = R + a table under the object
+    (Section IV-C): poses close enough that fingers reach into the table; teacher-forced steps in
+    both phases, every output compared with the oracle built with the same C."""
+    import oracle
+    w = synth.custom_case(P=2, K=16, N=600, M=3000, grid=32, k_max=8, seed=23, k_stein=3)
+    R = w.objects[0].points
+    C = np.concatenate([R, synth.table_points(2000, R, seed=5)]).astype(np.float32)
+    orc = oracle.Oracle(np.stack([pre.S for pre in w.preshapes]),
+                        [(pre.sdf, pre.origin, pre.voxel) for pre in w.preshapes], R, Cc=C, K=w.K)
+    P, K, N, Mc = 2, w.K, 600, len(C)
+    ctx = _ctx(w, stream)
+    rep = {}
+    table_hits = 0
+    try:
+        keep = tl.upload(ctx, w)
+        Rt, Ct = torch.from_numpy(R).cuda(), torch.from_numpy(C).cuda()
+        asicp.asicp_set_object(ctx, Rt, Ct)
+        com = R.astype(np.float64).mean(0)
+        theta0 = np.tile(oracle.fibonacci_init(K, com, 0.05), (P, 1)).astype(np.float32)
+        asicp.asicp_set_state(ctx, theta0, 0)
+        for k in (0, 1, 3, 4, 6):
+            asicp.asicp_set_state(ctx, tl.read_theta(ctx, P * K), k)
+            before = tl.read_theta(ctx, P * K)
+            asicp.asicp_step(ctx, k)
+            st = tl.read_state(ctx, P, K, N, Mc)
+            tl.check_step(orc, w, before, st, k, rep)
+            table_hits += sum(int((st["col_list"][pk, :n] >= len(R)).sum()) for pk, n in enumerate(st["ncol"]))
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
+    print("table:", rep, "table points in collision:", table_hits)
+    assert rep.get("colliding_particles", 0) > 0 and table_hits > 0, "the table is meant to be hit"

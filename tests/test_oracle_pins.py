@@ -511,3 +511,27 @@ def test_table1_golden_parameters_are_the_defaults(oracle_mod):
     assert t1["svgd_iterations"] / (t1["svgd_iterations"] + t1["sgd_iterations"]) == 0.375
     assert synth.k_stein_for(40) == t1["svgd_iterations"]
     assert synth.k_stein_for(100) == 38
+
+
+def test_quarter_sphere_initialisation():
+    """Quarter-sphere Fibonacci poses face the CoM from z >= 0, x >= 0 at the given radius, the
+    last six sit directly above with the approach axis pointing down, yawed 60 degrees apart."""
+    import oracle
+    com = np.array([0.01, -0.02, 0.03])
+    K, r = 40, 0.15
+    th = oracle.quarter_init(K, com, r)
+    t, q = th[:, :3] - com, th[:, 3:]
+    assert np.allclose(np.linalg.norm(t, axis=1), r, atol=1e-12)
+    assert np.allclose(np.linalg.norm(q, axis=1), 1.0, atol=1e-12)
+    R = Rotation.from_quat(q[:, [1, 2, 3, 0]]).as_matrix()
+    approach = R[:, :, 2]
+    quarter, above = slice(0, K - 6), slice(K - 6, K)
+    assert np.all(t[quarter, 2] > 0) and np.all(t[quarter, 0] >= -1e-12)
+    assert np.allclose(approach[quarter], -t[quarter] / r, atol=1e-12)          # facing the CoM
+    assert np.allclose(t[above], [0, 0, r], atol=1e-12)
+    assert np.allclose(approach[above], [0, 0, -1], atol=1e-12)
+    yaw = np.degrees(np.arctan2(R[above, 1, 0], R[above, 0, 0]))
+    assert np.allclose(np.diff(np.unwrap(np.radians(yaw))), np.radians(60.0), atol=1e-9)
+    # area-uniform lattice: the z coordinates are the midpoints of n equal bands
+    n = K - 6
+    assert np.allclose(np.sort(t[quarter, 2] / r)[::-1], 1 - (np.arange(n) + 0.5) / n, atol=1e-12)
