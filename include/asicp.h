@@ -70,6 +70,13 @@ typedef enum {
  *                  workload and keeps the fastest (see asicp_autotune); 0: use fwd_shape
  *   fwd_shape     forward-matching kernel shape, 0 .. ASICP_FWD_SHAPES-1 (0 = default;
  *                  the shapes differ in speed only, never in results)
+ *   init_mode     initial poses when asicp_run gets none: 0 = Fibonacci sphere of radius
+ *                  init_radius around the CoM, approach axis towards the CoM; 1 = the
+ *                  variant of the paper's experiments (Section VI-A, Fig. 3 (b)):
+ *                  Fibonacci points on the quarter of the sphere facing the robot (z >= 0,
+ *                  x >= 0 relative to the CoM; spiral z_j = 1 - (j + 1/2)/n, azimuth
+ *                  (j golden angle mod pi) - pi/2) plus min(6, K_g) poses directly above
+ *                  the object, approach axis -z, yawed 0, 60, ..., 300 degrees
  * Particles are numbered object by object, preshape by preshape: the group
  * g = object * P + preshape holds K_g particles (K_g = K unless set with
  * asicp_set_particle_counts); T = sum of K_g is the particle count of every
@@ -93,6 +100,7 @@ typedef struct {
     int n_objects;
     int autotune;
     int fwd_shape;
+    int init_mode;
 } asicp_config;
 
 /* Host pointers (or device pointers) the library fills in asicp_get_state; any

@@ -319,23 +319,44 @@ double orc_bandwidth(const double *theta, int K, const orc_schedule *sc)
  * sign is q_j.q_i) so that q_j and -q_j, one rotation, push q_i the same way.
  * phi_q is projected onto the tangent space at q_i, which removes the radial
  * rotational repulsion entirely. */
-void orc_stein_direction(const double *theta, const double *grad, int K, int N,
-                         double gamma, double h, double *phi)
+/* Eq. 8 with the priors of Section IV-A (reading R10b): the drive of particle j is
+ * gamma (-N g_j + grad log p(theta_j)), the annealing factor scaling both as Eq. 8
+ * groups them, with a Gaussian prior on t, grad = -(t - CoM) / sigma^2, and a von
+ * Mises prior on the rotation, log p = kappa |mu.q| (q and -q alike), grad = kappa
+ * sign(mu.q) mu for the unit mean mu.  prior = {sigma, kappa, mu (4), CoM (3)} or
+ * NULL; sigma <= 0 or kappa <= 0 switches a prior off. */
+void orc_stein_direction_prior(const double *theta, const double *grad, int K, int N,
+                               double gamma, double h, const double *prior, double *phi)
 {
+    const double sig = prior ? prior[0] : 0.0, kap = prior ? prior[1] : 0.0;
+    double mu[4] = {1.0, 0.0, 0.0, 0.0};
+    if (prior && kap > 0.0) {
+        double n = sqrt(prior[2] * prior[2] + prior[3] * prior[3] + prior[4] * prior[4] + prior[5] * prior[5]);
+        for (int a = 0; a < 4; ++a) mu[a] = prior[2 + a] / n;
+    }
     for (int i = 0; i < K; ++i) {
         const double *ti = theta + i * 7, *qi = theta + i * 7 + 3;
         double ft[3] = {0, 0, 0}, fq[4] = {0, 0, 0, 0};
         for (int j = 0; j < K; ++j) {
             const double *tj = theta + j * 7, *qj = theta + j * 7 + 3;
             const double *gj = grad + j * 7;
+            double drive[7];
+            for (int a = 0; a < 7; ++a) drive[a] = -N * gj[a];
+            if (sig > 0.0)
+                for (int a = 0; a < 3; ++a) drive[a] -= (tj[a] - prior[6 + a]) / (sig * sig);
+            if (kap > 0.0) {
+                double m = mu[0] * qj[0] + mu[1] * qj[1] + mu[2] * qj[2] + mu[3] * qj[3];
+                double sm = m < 0.0 ? -1.0 : 1.0;
+                for (int a = 0; a < 4; ++a) drive[3 + a] += kap * sm * mu[a];
+            }
             double dt[3] = {ti[0] - tj[0], ti[1] - tj[1], ti[2] - tj[2]};
             double kt = exp(-(dt[0] * dt[0] + dt[1] * dt[1] + dt[2] * dt[2]) / h);
             for (int a = 0; a < 3; ++a)
-                ft[a] += kt * (-gamma * N * gj[a]) + (2.0 / h) * dt[a] * kt;
+                ft[a] += kt * (gamma * drive[a]) + (2.0 / h) * dt[a] * kt;
             double c = qj[0] * qi[0] + qj[1] * qi[1] + qj[2] * qi[2] + qj[3] * qi[3];
             double sg = c < 0.0 ? -1.0 : 1.0;
             for (int a = 0; a < 4; ++a)
-                fq[a] += c * (-gamma * N * gj[3 + a]) + sg * qi[a];
+                fq[a] += c * (gamma * drive[3 + a]) + sg * qi[a];
         }
         for (int a = 0; a < 3; ++a) ft[a] /= K;
         for (int a = 0; a < 4; ++a) fq[a] /= K;
@@ -343,6 +364,12 @@ void orc_stein_direction(const double *theta, const double *grad, int K, int N,
         for (int a = 0; a < 3; ++a) phi[i * 7 + a] = ft[a];
         for (int a = 0; a < 4; ++a) phi[i * 7 + 3 + a] = fq[a];
     }
+}
+
+void orc_stein_direction(const double *theta, const double *grad, int K, int N,
+                         double gamma, double h, double *phi)
+{
+    orc_stein_direction_prior(theta, grad, K, N, gamma, h, NULL, phi);
 }
 
 static void normalize_q(double *q)
@@ -355,7 +382,7 @@ static void normalize_q(double *q)
  * z = 1 - (2j+1)/K and golden-angle azimuth j*pi*(3 - sqrt 5); t_j = CoM +
  * radius * u_j; q_j the smallest rotation taking the approach axis +z to -u_j
  * (half-vector form), pi about x when -u_j = -z.  Reading: the full sphere is
- * used; the paper's quarter sphere and six extra poses are a variant. */
+ * the default; the paper's quarter sphere and six extra poses are orc_quarter_init. */
 void orc_fibonacci_init(int K, const double com[3], double radius, double *theta)
 {
     const double ga = M_PI * (3.0 - sqrt(5.0));
@@ -452,7 +479,10 @@ void orc_step(const orc_problem *pb, const orc_schedule *sc, orc_state *st, int 
             double h = orc_bandwidth(th, K, sc);
             st->h[p] = h;
             double *phi = st->phi + (size_t)p * K * 7;
-            orc_stein_direction(th, gr, K, pb->N, gamma, h, phi);
+            double prior[9] = {sc->prior_t_sigma, sc->prior_q_kappa, sc->prior_q_mean[0], sc->prior_q_mean[1],
+                               sc->prior_q_mean[2], sc->prior_q_mean[3], 0.0, 0.0, 0.0};
+            orc_centroid(pb->R, pb->M, prior + 6);
+            orc_stein_direction_prior(th, gr, K, pb->N, gamma, h, prior, phi);
             for (int j = 0; j < K; ++j) {           /* Eq. 7 */
                 for (int a = 0; a < 7; ++a) th[j * 7 + a] += sc->eta_svgd * phi[j * 7 + a];
                 normalize_q(th + j * 7 + 3);

@@ -35,6 +35,9 @@ typedef struct {
     int bandwidth_mode;       /* 0: median heuristic, 1: h_fixed                 */
     double h_fixed;
     double conv_tol;          /* < 0 disables freezing                            */
+    double prior_t_sigma;     /* Gaussian prior on t around the CoM (<= 0: off)   */
+    double prior_q_kappa;     /* von Mises prior on q (<= 0: off)                 */
+    double prior_q_mean[4];   /* its mean rotation (normalised)                   */
 } orc_schedule;
 
 typedef struct {
@@ -71,6 +74,8 @@ double orc_gamma(const orc_schedule *sc, int k);
 double orc_bandwidth(const double *theta, int K, const orc_schedule *sc);
 void orc_stein_direction(const double *theta, const double *grad, int K, int N,
                          double gamma, double h, double *phi);
+void orc_stein_direction_prior(const double *theta, const double *grad, int K, int N,
+                               double gamma, double h, const double *prior, double *phi);
 void orc_fibonacci_init(int K, const double com[3], double radius, double *theta);
 void orc_quarter_init(int K, const double com[3], double radius, double *theta);
 void orc_centroid(const double *X, int n, double c[3]);

@@ -42,7 +42,8 @@ class _Schedule(C.Structure):
     _fields_ = [("k_max", C.c_int), ("k_stein", C.c_int), ("schedule", C.c_int),
                 ("C_cycles", C.c_double), ("p_exp", C.c_double), ("g0", C.c_double), ("g1", C.c_double),
                 ("eta_sgd", C.c_double), ("eta_svgd", C.c_double), ("bandwidth_mode", C.c_int),
-                ("h_fixed", C.c_double), ("conv_tol", C.c_double)]
+                ("h_fixed", C.c_double), ("conv_tol", C.c_double), ("prior_t_sigma", C.c_double),
+                ("prior_q_kappa", C.c_double), ("prior_q_mean", C.c_double * 4)]
 
 
 class _State(C.Structure):
@@ -72,6 +73,7 @@ def _load():
         lib.orc_bandwidth.argtypes = [_dp, C.c_int, C.POINTER(_Schedule)]
         lib.orc_bandwidth.restype = C.c_double
         lib.orc_stein_direction.argtypes = [_dp, _dp, C.c_int, C.c_int, C.c_double, C.c_double, _dp]
+        lib.orc_stein_direction_prior.argtypes = [_dp, _dp, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
         lib.orc_fibonacci_init.argtypes = [C.c_int, _dp, C.c_double, _dp]
         lib.orc_quarter_init.argtypes = [C.c_int, _dp, C.c_double, _dp]
         lib.orc_centroid.argtypes = [_dp, C.c_int, _dp]
@@ -145,11 +147,17 @@ def bandwidth(theta, bandwidth_mode=0, h_fixed=1.0):
     return _load().orc_bandwidth(tp, len(th), C.byref(sc))
 
 
-def stein_direction(theta, grad, N, gamma_, h):
+def stein_direction(theta, grad, N, gamma_, h, prior=None):
+    """prior: None or (sigma_t, kappa_q, mean_q (4), CoM (3))."""
     th, tp = _d(np.asarray(theta).reshape(-1, 7))
     g, gp = _d(np.asarray(grad).reshape(-1, 7))
     phi = np.zeros_like(th)
-    _load().orc_stein_direction(tp, gp, len(th), int(N), float(gamma_), float(h), phi.ctypes.data_as(_dp))
+    if prior is None:
+        pp = None
+    else:
+        pr, pp = _d(np.concatenate([[prior[0], prior[1]], prior[2], prior[3]]).astype(np.float64))
+    _load().orc_stein_direction_prior(tp, gp, len(th), int(N), float(gamma_), float(h), pp,
+                                      phi.ctypes.data_as(_dp))
     return phi
 
 
@@ -287,11 +295,13 @@ class Oracle:
 
     @staticmethod
     def schedule(k_max, k_stein, schedule=0, C_cycles=5.0, p_exp=2.0, g0=0.1, g1=1.0, eta_sgd=1.0,
-                 eta_svgd=None, N=1, bandwidth_mode=0, h_fixed=1.0, conv_tol=-1.0):
+                 eta_svgd=None, N=1, bandwidth_mode=0, h_fixed=1.0, conv_tol=-1.0, prior_t_sigma=0.0,
+                 prior_q_kappa=0.0, prior_q_mean=(1.0, 0.0, 0.0, 0.0)):
         if eta_svgd is None:
             eta_svgd = 1.0 / N
         return _Schedule(int(k_max), int(k_stein), int(schedule), C_cycles, p_exp, g0, g1, eta_sgd, eta_svgd,
-                         int(bandwidth_mode), h_fixed, conv_tol)
+                         int(bandwidth_mode), h_fixed, conv_tol, prior_t_sigma, prior_q_kappa,
+                         (C.c_double * 4)(*prior_q_mean))
 
     def step(self, st, sched, k, nthreads=1):
         cs = self._cstate(st)

@@ -682,7 +682,7 @@ asicp_status asicp_create(const asicp_config *cfg, asicp_ctx **out)
         (cfg->schedule == 0 && !(cfg->C_cycles > 0.f)) || !(cfg->eta_sgd >= 0.f) ||
         (cfg->bandwidth_mode == 1 && !(cfg->h_fixed > 0.f)) || !std::isfinite(cfg->w_com) ||
         !(cfg->init_radius >= 0.f) || cfg->n_objects < 1 || cfg->n_objects > 4096 ||
-        cfg->fwd_shape < 0 || cfg->fwd_shape >= kFwdVariants)
+        cfg->fwd_shape < 0 || cfg->fwd_shape >= kFwdVariants || cfg->init_mode < 0 || cfg->init_mode > 1)
         return ASICP_ERR_INVALID_ARG;
     asicp_ctx *c = new (std::nothrow) asicp_ctx();
     if (!c) return ASICP_ERR_OOM;
@@ -859,7 +859,9 @@ asicp_status asicp_run(asicp_ctx *ctx, const float *theta0)
                "set theta0");
             sync_and_check_err(ctx, "run");
         } else {
-            ck(launch_fibonacci(ctx->layout(), ctx->cfg.init_radius, ctx->theta.as<float>(), ctx->st), "fibonacci init");
+            ck(launch_fibonacci(ctx->layout(), ctx->cfg.init_radius, ctx->cfg.init_mode, ctx->theta.as<float>(),
+                                ctx->st),
+               "initial poses");
         }
         ctx->theta_set = true;
         if (ctx->cfg.autotune && !ctx->tuned) autotune_impl(ctx, nullptr);
@@ -952,7 +954,9 @@ asicp_status asicp_autotune(asicp_ctx *ctx, int *chosen, float *ms)
         if (!ctx->inputs_ready()) fail(ASICP_ERR_STATE, "autotune: objects and every preshape must be set first");
         build_layout(ctx);
         if (!ctx->theta_set) {
-            ck(launch_fibonacci(ctx->layout(), ctx->cfg.init_radius, ctx->theta.as<float>(), ctx->st), "fibonacci init");
+            ck(launch_fibonacci(ctx->layout(), ctx->cfg.init_radius, ctx->cfg.init_mode, ctx->theta.as<float>(),
+                                ctx->st),
+               "initial poses");
             ctx->theta_set = true;
             ctx->stepped = false;
         }

@@ -473,8 +473,9 @@ cudaError_t launch_preshape_consts(const float4 *S, int N, double *out12, cudaSt
 // Fibonacci sphere of K directions around the CoM (Section V); the same set for
 // every preshape.  u_j: z = 1 - (2j+1)/K, azimuth j * pi * (3 - sqrt 5);
 // t_j = CoM + radius u_j; q_j the smallest rotation taking +z (the approach
-// axis) to -u_j, pi about x when -u_j = -z.
-__global__ void fibonacci_kernel(const Layout L, float radius, float *theta)
+// axis) to -u_j, pi about x when -u_j = -z.  mode 1: the quarter-sphere lattice
+// facing +x (upper half) plus min(6, K) poses above the object (see asicp.h).
+__global__ void fibonacci_kernel(const Layout L, float radius, int mode, float *theta)
 {
     const int pk = blockIdx.x * blockDim.x + threadIdx.x;
     if (pk >= L.T) return;
@@ -482,12 +483,33 @@ __global__ void fibonacci_kernel(const Layout L, float radius, float *theta)
     const int j = pk - L.grp_off[grp], K = L.grp_off[grp + 1] - L.grp_off[grp];
     const double *com = L.com + 3 * (grp / L.P);
     const double ga = 3.14159265358979323846 * (3.0 - sqrt(5.0));
-    const double z = 1.0 - (2.0 * j + 1.0) / K;
-    const double rho = sqrt(fmax(0.0, 1.0 - z * z));
-    double sa, ca;
-    sincos(j * ga, &sa, &ca);
-    const double u[3] = {rho * ca, rho * sa, z};
     float *th = theta + (size_t)pk * 8;
+    th[7] = 0.f;
+    double u[3];
+    const int n_above = mode == 1 ? min(6, K) : 0, nq = K - n_above;
+    if (j >= nq) {
+        // above the object, approach axis -z (pi about x), yawed by (j - nq) * 60 degrees
+        double sh, ch;
+        sincos((j - nq) * (3.14159265358979323846 / 6.0), &sh, &ch);
+        th[0] = (float)com[0];
+        th[1] = (float)com[1];
+        th[2] = (float)(com[2] + (double)radius);
+        th[3] = 0.f; th[4] = (float)ch; th[5] = (float)sh; th[6] = 0.f;
+        return;
+    }
+    if (mode == 1) {   // quarter sphere facing +x, upper half
+        const double z = 1.0 - (j + 0.5) / nq;
+        const double rho = sqrt(fmax(0.0, 1.0 - z * z));
+        double sa, ca;
+        sincos(fmod(j * ga, 3.14159265358979323846) - 0.5 * 3.14159265358979323846, &sa, &ca);
+        u[0] = rho * ca; u[1] = rho * sa; u[2] = z;
+    } else {
+        const double z = 1.0 - (2.0 * j + 1.0) / K;
+        const double rho = sqrt(fmax(0.0, 1.0 - z * z));
+        double sa, ca;
+        sincos(j * ga, &sa, &ca);
+        u[0] = rho * ca; u[1] = rho * sa; u[2] = z;
+    }
     for (int a = 0; a < 3; ++a) th[a] = (float)(com[a] + (double)radius * u[a]);
     const double w = 1.0 - u[2];
     if (w < 1e-12) {
@@ -497,12 +519,11 @@ __global__ void fibonacci_kernel(const Layout L, float radius, float *theta)
         const double n = sqrt(qv[0] * qv[0] + qv[1] * qv[1] + qv[2] * qv[2]);
         for (int a = 0; a < 4; ++a) th[3 + a] = (float)(qv[a] / n);
     }
-    th[7] = 0.f;
 }
 
-cudaError_t launch_fibonacci(const Layout &L, float radius, float *theta, cudaStream_t st)
+cudaError_t launch_fibonacci(const Layout &L, float radius, int mode, float *theta, cudaStream_t st)
 {
-    fibonacci_kernel<<<(L.T + 255) / 256, 256, 0, st>>>(L, radius, theta);
+    fibonacci_kernel<<<(L.T + 255) / 256, 256, 0, st>>>(L, radius, mode, theta);
     return cudaGetLastError();
 }
 

@@ -530,3 +530,24 @@ def test_separate_collision_cloud_with_a_table(stream):
         asicp.asicp_destroy(ctx)
     print("table:", rep, "table points in collision:", table_hits)
     assert rep.get("colliding_particles", 0) > 0 and table_hits > 0, "the table is meant to be hit"
+
+
+def test_quarter_sphere_initialisation_matches_oracle(stream):
+    """config.init_mode = 1: the quarter-sphere lattice plus six poses above, per preshape group,
+    against the oracle's (float32 poses vs float64)."""
+    import oracle
+    w = synth.custom_case(P=2, K=40, N=200, M=1000, grid=24, k_max=0, seed=29, k_stein=0)
+    ctx = _ctx(w, stream, init_mode=1, k_max=0, k_stein=0)
+    try:
+        keep = tl.upload(ctx, w)
+        asicp.asicp_run(ctx)
+        th = tl.read_theta(ctx, 2 * w.K)
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
+    ref = oracle.quarter_init(w.K, w.objects[0].points.astype(np.float64).mean(0), 0.15)
+    for p in range(2):
+        got = th[p * w.K:(p + 1) * w.K].astype(np.float64)
+        assert np.allclose(got[:, :3], ref[:, :3], rtol=0, atol=2e-7)
+        dots = np.abs((got[:, 3:] * ref[:, 3:]).sum(1))          # q and -q are the same rotation
+        assert np.all(dots > 1 - 1e-6)

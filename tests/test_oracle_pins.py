@@ -535,3 +535,25 @@ def test_quarter_sphere_initialisation():
     # area-uniform lattice: the z coordinates are the midpoints of n equal bands
     n = K - 6
     assert np.allclose(np.sort(t[quarter, 2] / r)[::-1], 1 - (np.arange(n) + 0.5) / n, atol=1e-12)
+
+
+def test_priors_in_the_stein_direction_closed_form():
+    """K = 1, no cost gradient: phi = gamma grad log p = gamma (-(t - CoM)/sigma^2, kappa sign(mu.q)
+    projected mu) (plus the self-repulsion, radial in q, which the projection removes)."""
+    import oracle
+    g = np.random.default_rng(21)
+    com = np.array([0.02, -0.01, 0.05])
+    mu = np.array([0.3, -0.4, 0.5, 0.7]); mu /= np.linalg.norm(mu)
+    th = np.zeros((1, 7)); th[0, :3] = com + g.normal(0, 0.05, 3)
+    q = g.normal(size=4); q /= np.linalg.norm(q); th[0, 3:] = -q if q @ mu > 0 else q   # mu.q < 0
+    sigma, kappa, gam = 0.07, 3.0, 0.6
+    phi = oracle.stein_direction(th, np.zeros((1, 7)), 100, gam, 1.0, prior=(sigma, kappa, mu, com))[0]
+    qq = th[0, 3:]
+    assert np.allclose(phi[:3], -gam * (th[0, :3] - com) / sigma ** 2, rtol=1e-12, atol=0)
+    d = -kappa * mu                                     # sign(mu.q) = -1
+    assert np.allclose(phi[3:], gam * (d - (d @ qq) * qq), rtol=1e-12, atol=1e-15)
+    # switched off, the priors change nothing
+    grad = g.normal(size=(5, 7)); th5 = np.tile(th, (5, 1)); th5[:, :3] += g.normal(0, 0.03, (5, 3))
+    a = oracle.stein_direction(th5, grad, 100, gam, 0.01)
+    b = oracle.stein_direction(th5, grad, 100, gam, 0.01, prior=(0.0, 0.0, mu, com))
+    assert np.array_equal(a, b)
