@@ -77,6 +77,13 @@ typedef enum {
  *                  x >= 0 relative to the CoM; spiral z_j = 1 - (j + 1/2)/n, azimuth
  *                  (j golden angle mod pi) - pi/2) plus min(6, K_g) poses directly above
  *                  the object, approach axis -z, yawed 0, 60, ..., 300 degrees
+ *   prior_t_sigma, prior_q_kappa, prior_q_mean
+ *                 the priors of Eq. 8 (Section IV-A: Gaussian on translations, von Mises on
+ *                  rotations), used in the SVGD phase: the drive of particle j becomes
+ *                  gamma (-N g_j + grad log p(theta_j)) with grad_t log p = -(t - CoM) /
+ *                  prior_t_sigma^2 and grad_q log p = prior_q_kappa sign(mu.q) mu, mu =
+ *                  prior_q_mean normalised (q and -q alike); 0 switches a prior off (the
+ *                  default: the paper gives no parameters)
  * Particles are numbered object by object, preshape by preshape: the group
  * g = object * P + preshape holds K_g particles (K_g = K unless set with
  * asicp_set_particle_counts); T = sum of K_g is the particle count of every
@@ -101,6 +108,8 @@ typedef struct {
     int autotune;
     int fwd_shape;
     int init_mode;
+    float prior_t_sigma, prior_q_kappa;
+    float prior_q_mean[4];
 } asicp_config;
 
 /* Host pointers (or device pointers) the library fills in asicp_get_state; any

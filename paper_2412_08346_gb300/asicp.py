@@ -42,7 +42,8 @@ class asicp_config(C.Structure):
                 ("g1", C.c_float), ("eta_sgd", C.c_float), ("eta_svgd", C.c_float), ("w_com", C.c_float),
                 ("bandwidth_mode", C.c_int), ("h_fixed", C.c_float), ("conv_tol", C.c_float),
                 ("init_radius", C.c_float), ("debug", C.c_int), ("profile", C.c_int),
-                ("cuda_stream", C.c_void_p), ("n_objects", C.c_int), ("autotune", C.c_int), ("fwd_shape", C.c_int), ("init_mode", C.c_int)]
+                ("cuda_stream", C.c_void_p), ("n_objects", C.c_int), ("autotune", C.c_int), ("fwd_shape", C.c_int), ("init_mode", C.c_int),
+                ("prior_t_sigma", C.c_float), ("prior_q_kappa", C.c_float), ("prior_q_mean", C.c_float * 4)]
 
 
 class asicp_state_view(C.Structure):

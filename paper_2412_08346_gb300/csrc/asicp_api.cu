@@ -462,6 +462,14 @@ void iterate(asicp_ctx *c, int mode, float gamma)
     ua.phi = c->phi.as<float>();
     ua.h = c->h.as<float>();
     ua.col_items = c->colitems.as<int>();
+    ua.prior_t_sigma = c->cfg.prior_t_sigma;
+    ua.prior_q_kappa = c->cfg.prior_q_kappa;
+    {
+        const float *m = c->cfg.prior_q_mean;
+        const double n =
+            std::sqrt((double)m[0] * m[0] + (double)m[1] * m[1] + (double)m[2] * m[2] + (double)m[3] * m[3]);
+        for (int a = 0; a < 4; ++a) ua.prior_q_mean[a] = n > 0.0 ? (float)(m[a] / n) : (a == 0 ? 1.f : 0.f);
+    }
     timed(c, kTimeFinalize, [&](cudaStream_t st) { return launch_finalize(ua, st); }, "finalize kernel");
     if (mode == 1)
         timed(c, kTimeStein, [&](cudaStream_t st) { return launch_stein(ua, st); }, "Stein kernel");
@@ -682,7 +690,10 @@ asicp_status asicp_create(const asicp_config *cfg, asicp_ctx **out)
         (cfg->schedule == 0 && !(cfg->C_cycles > 0.f)) || !(cfg->eta_sgd >= 0.f) ||
         (cfg->bandwidth_mode == 1 && !(cfg->h_fixed > 0.f)) || !std::isfinite(cfg->w_com) ||
         !(cfg->init_radius >= 0.f) || cfg->n_objects < 1 || cfg->n_objects > 4096 ||
-        cfg->fwd_shape < 0 || cfg->fwd_shape >= kFwdVariants || cfg->init_mode < 0 || cfg->init_mode > 1)
+        cfg->fwd_shape < 0 || cfg->fwd_shape >= kFwdVariants || cfg->init_mode < 0 || cfg->init_mode > 1 ||
+        !std::isfinite(cfg->prior_t_sigma) || !std::isfinite(cfg->prior_q_kappa) ||
+        (cfg->prior_q_kappa > 0.f && !(std::fabs(cfg->prior_q_mean[0]) + std::fabs(cfg->prior_q_mean[1]) +
+                                       std::fabs(cfg->prior_q_mean[2]) + std::fabs(cfg->prior_q_mean[3]) > 0.f)))
         return ASICP_ERR_INVALID_ARG;
     asicp_ctx *c = new (std::nothrow) asicp_ctx();
     if (!c) return ASICP_ERR_OOM;

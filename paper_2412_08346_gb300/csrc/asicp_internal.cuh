@@ -245,6 +245,9 @@ struct UpdateArgs {
     float *phi;               // [T][8]
     float *h;                 // [G]
     int *col_items;           // collision work-list counters (count, next), cleared for the next pass
+    float prior_t_sigma;      // Gaussian prior on t around the object's CoM (<= 0: off)
+    float prior_q_kappa;      // von Mises prior on q (<= 0: off)
+    float prior_q_mean[4];    // its unit mean
 };
 cudaError_t launch_finalize(const UpdateArgs &a, cudaStream_t st);   // cost/gradient, convergence, SGD step
 cudaError_t launch_stein(const UpdateArgs &a, cudaStream_t st);      // SVGD step (mode 1)

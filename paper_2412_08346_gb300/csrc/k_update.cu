@@ -194,14 +194,24 @@ __global__ void __launch_bounds__(kSteinThreads) stein_kernel(const UpdateArgs a
     const int i = threadIdx.x / T, sub = threadIdx.x % T;
     const bool active = i < K;
     const float gN = -a.gamma * (float)a.L.N;
+    const double *com = a.L.com + 3 * (grp / a.L.P);
+    const float cx = (float)com[0], cy = (float)com[1], cz = (float)com[2];
+    const float pt = a.prior_t_sigma > 0.f ? -a.gamma / (a.prior_t_sigma * a.prior_t_sigma) : 0.f;
+    const float pq = a.prior_q_kappa > 0.f ? a.gamma * a.prior_q_kappa : 0.f;
+    const float *mu = a.prior_q_mean;
     for (int j = threadIdx.x; j < K; j += blockDim.x) {
         const size_t pj = (size_t)base + j;
         const float *th = a.theta + pj * 8;
         const double *g = a.grad + pj * 8;
         sT[j] = make_float4(th[0], th[1], th[2], 0.f);
         sQ[j] = make_float4(th[3], th[4], th[5], th[6]);
-        sDt[j] = make_float4(gN * (float)g[0], gN * (float)g[1], gN * (float)g[2], 0.f);
-        sDq[j] = make_float4(gN * (float)g[3], gN * (float)g[4], gN * (float)g[5], gN * (float)g[6]);
+        // drive gamma (-N g + grad log p): Gaussian prior on t, von Mises on q (both off at 0)
+        const float m = mu[0] * th[3] + mu[1] * th[4] + mu[2] * th[5] + mu[3] * th[6];
+        const float sq = m < 0.f ? -pq : pq;
+        sDt[j] = make_float4(gN * (float)g[0] + pt * (th[0] - cx), gN * (float)g[1] + pt * (th[1] - cy),
+                             gN * (float)g[2] + pt * (th[2] - cz), 0.f);
+        sDq[j] = make_float4(gN * (float)g[3] + sq * mu[0], gN * (float)g[4] + sq * mu[1],
+                             gN * (float)g[5] + sq * mu[2], gN * (float)g[6] + sq * mu[3]);
     }
     __syncthreads();
 

@@ -109,8 +109,9 @@ def rel_err(a, b, floor=0.0):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), floor)
 
 
-def check_step(orc, w, before_theta, st, k, report, check_update=True, sample=None):
-    """Teacher-forced comparison of one GPU step against the oracle, particle by particle."""
+def check_step(orc, w, before_theta, st, k, report, check_update=True, sample=None, prior=None):
+    """Teacher-forced comparison of one GPU step against the oracle, particle by particle.
+    prior: None or (sigma_t, kappa_q, mean_q, CoM) of the Stein direction's priors."""
     import oracle
     P, K, N = orc.P, orc.K, orc.N
     Mc = len(orc.Cc)
@@ -159,8 +160,8 @@ def check_step(orc, w, before_theta, st, k, report, check_update=True, sample=No
             gam = oracle.gamma(k, w.k_max, w.schedule, w.C_cycles, w.p_exp, w.g0, w.g1)
             h = oracle.bandwidth(th)
             assert abs(st["h"][p] - h) <= 1e-5 * h, f"bandwidth {st['h'][p]} vs {h}"
-            phi = oracle.stein_direction(th, st["grad"][sl], N, gam, h)
-            scale = stein_term_scale(th, st["grad"][sl], N, gam, h)
+            phi = oracle.stein_direction(th, st["grad"][sl], N, gam, h, prior=prior)
+            scale = stein_term_scale(th, st["grad"][sl], N, gam, h, prior)
             for j in range(K):
                 for b, blk in enumerate((slice(0, 3), slice(3, 7))):
                     e = np.linalg.norm(st["phi"][sl][j, blk] - phi[j, blk])
@@ -182,15 +183,17 @@ def check_step(orc, w, before_theta, st, k, report, check_update=True, sample=No
 STEIN_ABS_REL = 1e-5
 
 
-def stein_term_scale(theta, grad, N, gam, h):
+def stein_term_scale(theta, grad, N, gam, h, prior=None):
     """Mean magnitude of the terms the Stein direction of each particle sums (per block)."""
     t, q = theta[:, :3], theta[:, 3:]
     dt = t[:, None, :] - t[None, :, :]                       # [i, j]
     kt = np.exp(-(dt ** 2).sum(-1) / h)
     c = np.abs(q @ q.T)
-    st = (kt * (gam * N * np.linalg.norm(grad[None, :, :3], axis=-1) +
+    pt = np.zeros(len(t)) if prior is None or prior[0] <= 0 else np.linalg.norm(t - prior[3], axis=1) / prior[0] ** 2
+    pq = 0.0 if prior is None or prior[1] <= 0 else prior[1]
+    st = (kt * (gam * N * np.linalg.norm(grad[None, :, :3], axis=-1) + gam * pt[None, :] +
                 (2 / h) * np.linalg.norm(dt, axis=-1))).mean(1)
-    sq = (c * gam * N * np.linalg.norm(grad[None, :, 3:], axis=-1) + 1.0).mean(1)
+    sq = (c * (gam * N * np.linalg.norm(grad[None, :, 3:], axis=-1) + gam * pq) + 1.0).mean(1)
     return np.stack([st, sq], 1)
 
 

@@ -551,3 +551,33 @@ def test_quarter_sphere_initialisation_matches_oracle(stream):
         assert np.allclose(got[:, :3], ref[:, :3], rtol=0, atol=2e-7)
         dots = np.abs((got[:, 3:] * ref[:, 3:]).sum(1))          # q and -q are the same rotation
         assert np.all(dots > 1 - 1e-6)
+
+
+def test_stein_priors_match_oracle(stream):
+    """Gaussian translation prior and von Mises rotation prior in the SVGD drive (Section IV-A):
+    teacher-forced SVGD steps against the oracle with the same priors."""
+    import ctypes
+    import oracle
+    w = synth.custom_case(P=2, K=16, N=400, M=2000, grid=24, k_max=6, seed=37, k_stein=6, schedule=1)
+    mu = np.array([0.5, 0.5, -0.5, 0.5])
+    prior = (0.05, 2.0, mu, w.objects[0].points.astype(np.float64).mean(0))
+    orc = tl.make_oracle(w)
+    P, K, N, Mc = 2, w.K, 400, len(w.objects[0].points)
+    cfg = tl.make_config(w, stream=stream, prior_t_sigma=prior[0], prior_q_kappa=prior[1])
+    cfg.prior_q_mean = (ctypes.c_float * 4)(*mu)
+    ctx = asicp.asicp_create(cfg)
+    rep = {}
+    try:
+        keep = tl.upload(ctx, w)
+        theta0 = np.tile(oracle.fibonacci_init(K, prior[3], 0.1), (P, 1)).astype(np.float32)
+        asicp.asicp_set_state(ctx, theta0, 0)
+        for k in (0, 2, 4):
+            asicp.asicp_set_state(ctx, tl.read_theta(ctx, P * K), k)
+            before = tl.read_theta(ctx, P * K)
+            asicp.asicp_step(ctx, k)
+            st = tl.read_state(ctx, P, K, N, Mc)
+            tl.check_step(orc, w, before, st, k, rep, prior=prior)
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
+    print("priors:", rep)
