@@ -83,6 +83,15 @@ void orc_centroid(const double *X, int n, double c[3])
     for (int a = 0; a < 3; ++a) c[a] /= (double)n;
 }
 
+/* The problem's CoM: given, or the centroid of its object cloud R. */
+static void problem_com(const orc_problem *pb, double com[3])
+{
+    if (pb->com)
+        for (int a = 0; a < 3; ++a) com[a] = pb->com[a];
+    else
+        orc_centroid(pb->R, pb->M, com);
+}
+
 /* Trilinear interpolation of a node-centred grid (x fastest).  A point outside
  * the grid's node box is reported with *inside = 0 (reading: the grid covers
  * the gripper, so such a point cannot be inside it). */
@@ -136,7 +145,7 @@ void orc_match_terms(const orc_problem *pb, int p, const double theta[7], const 
     double Rm[9], tcp[3], com[3];
     orc_rotation(q, Rm);
     orc_centroid(S, N, tcp);            /* TCP: centre of the contact cloud */
-    orc_centroid(pb->R, pb->M, com);    /* CoM: centroid of the object cloud */
+    problem_com(pb, com);               /* CoM: centroid of the object cloud */
     double se = 0.0, ge[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0};
     for (int i = 0; i < N; ++i) {
         double sp[3], J[12];
@@ -481,7 +490,7 @@ void orc_step(const orc_problem *pb, const orc_schedule *sc, orc_state *st, int 
             double *phi = st->phi + (size_t)p * K * 7;
             double prior[9] = {sc->prior_t_sigma, sc->prior_q_kappa, sc->prior_q_mean[0], sc->prior_q_mean[1],
                                sc->prior_q_mean[2], sc->prior_q_mean[3], 0.0, 0.0, 0.0};
-            orc_centroid(pb->R, pb->M, prior + 6);
+            problem_com(pb, prior + 6);
             orc_stein_direction_prior(th, gr, K, pb->N, gamma, h, prior, phi);
             for (int j = 0; j < K; ++j) {           /* Eq. 7 */
                 for (int a = 0; a < 7; ++a) th[j * 7 + a] += sc->eta_svgd * phi[j * 7 + a];

@@ -25,6 +25,8 @@ typedef struct {
     const double *sdf_origin; /* P*3 position of node (0,0,0)                    */
     const double *sdf_voxel;  /* P   node spacing                                */
     double w_com;             /* weight of the TCP-CoM term inside 1/N (Eqs. 16-17) */
+    const double *com;        /* 3: CoM, or NULL for the centroid of R (a mini-batch
+                                 of R keeps the whole object's CoM)                */
 } orc_problem;
 
 typedef struct {

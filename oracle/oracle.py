@@ -35,7 +35,8 @@ def build(force: bool = False) -> str:
 class _Problem(C.Structure):
     _fields_ = [("P", C.c_int), ("K", C.c_int), ("N", C.c_int), ("M", C.c_int), ("Mc", C.c_int),
                 ("S", _dp), ("R", _dp), ("C", _dp), ("sdf", _dp), ("sdf_off", C.POINTER(C.c_longlong)),
-                ("sdf_dims", _ip), ("sdf_origin", _dp), ("sdf_voxel", _dp), ("w_com", C.c_double)]
+                ("sdf_dims", _ip), ("sdf_origin", _dp), ("sdf_voxel", _dp), ("w_com", C.c_double),
+                ("com", _dp)]
 
 
 class _Schedule(C.Structure):
@@ -192,7 +193,7 @@ class Oracle:
     ``R`` is (M, 3); ``Cc`` the collision cloud (defaults to ``R``).
     """
 
-    def __init__(self, S, sdfs, R, Cc=None, K=1, w_com=1.0):
+    def __init__(self, S, sdfs, R, Cc=None, K=1, w_com=1.0, com=None):
         self.S = np.ascontiguousarray(np.asarray(S, dtype=np.float64).reshape(len(S), -1, 3))
         self.P, self.N = self.S.shape[0], self.S.shape[1]
         self.R = np.ascontiguousarray(np.asarray(R, dtype=np.float64).reshape(-1, 3))
@@ -214,11 +215,13 @@ class Oracle:
         self.sdf_origin = np.ascontiguousarray(np.array(orgs, np.float64))
         self.sdf_voxel = np.ascontiguousarray(np.array(vox, np.float64))
         self.w_com = float(w_com)
+        self._com = None if com is None else np.ascontiguousarray(np.asarray(com, dtype=np.float64).reshape(3))
         self._pb = _Problem(self.P, self.K, self.N, len(self.R), len(self.Cc),
                             self.S.ctypes.data_as(_dp), self.R.ctypes.data_as(_dp), self.Cc.ctypes.data_as(_dp),
                             self.sdf.ctypes.data_as(_dp), self.sdf_off.ctypes.data_as(C.POINTER(C.c_longlong)),
                             self.sdf_dims.ctypes.data_as(_ip), self.sdf_origin.ctypes.data_as(_dp),
-                            self.sdf_voxel.ctypes.data_as(_dp), self.w_com)
+                            self.sdf_voxel.ctypes.data_as(_dp), self.w_com,
+                            None if com is None else self._com.ctypes.data_as(_dp))
 
     # ---- per particle
     def match_cost_grad(self, p, theta):

@@ -352,3 +352,19 @@ def table_points(n: int, obj_points: np.ndarray, seed: int, extent: float = 0.30
     xy = c[:2] + g.uniform(-extent / 2, extent / 2, (n, 2))
     pts = np.concatenate([xy, np.full((n, 1), z)], 1) + g.normal(0.0, noise, (n, 3))
     return pts.astype(np.float32)
+
+
+def minibatch_ramp(M: int, k_max: int, seed: int):
+    """Mini-batches of the object cloud per iteration (Table I's ramp): m_k = ceil(M min(k, 2 k_max/3)
+    / (2 k_max/3)), at least 1, drawn without replacement (seeded) and sorted ascending.
+    Returns (offsets [k_max + 1], indices [offsets[-1]]) int32."""
+    g = rng(seed)
+    ramp = 2.0 * k_max / 3.0
+    offs, idx = [0], []
+    for k in range(k_max):
+        m = int(np.ceil(M * min(k, ramp) / ramp)) if ramp > 0 else M
+        m = min(max(m, 1), M)
+        sel = np.sort(g.choice(M, m, replace=False)) if m < M else np.arange(M)
+        idx.append(sel)
+        offs.append(offs[-1] + m)
+    return np.asarray(offs, np.int32), np.concatenate(idx).astype(np.int32)

@@ -557,3 +557,39 @@ def test_priors_in_the_stein_direction_closed_form():
     a = oracle.stein_direction(th5, grad, 100, gam, 0.01)
     b = oracle.stein_direction(th5, grad, 100, gam, 0.01, prior=(0.0, 0.0, mu, com))
     assert np.array_equal(a, b)
+
+
+def test_minibatch_ramp_follows_table1():
+    """m_k = ceil(M min(k, 2 k_max/3) / (2 k_max/3)), at least one point, ascending unique indices."""
+    from paper_2412_08346_gb300 import synth
+    M, k_max = 1000, 30
+    off, idx = synth.minibatch_ramp(M, k_max, 3)
+    sizes = np.diff(off)
+    ramp = 2 * k_max / 3
+    want = [min(max(int(np.ceil(M * min(k, ramp) / ramp)), 1), M) for k in range(k_max)]
+    assert list(sizes) == want and sizes[0] == 1 and sizes[-1] == M
+    for k in range(k_max):
+        sub = idx[off[k]:off[k + 1]]
+        assert np.all(np.diff(sub) > 0) and sub[0] >= 0 and sub[-1] < M
+
+
+def test_match_cost_with_a_given_com():
+    """A mini-batch of R keeps the whole object's CoM: the cost with an explicit CoM equals the
+    formula of Eqs. 13-15 written out with brute-force correspondences into the mini-batch."""
+    import oracle
+    g = np.random.default_rng(31)
+    S = g.normal(0, 0.03, (1, 30, 3))
+    R = g.normal(0, 0.05, (200, 3))
+    sub = R[::3]
+    com = R.mean(0)
+    grid = np.zeros((4, 4, 4))
+    o = oracle.Oracle(S, [(grid, np.array([-1.0, -1, -1]), 0.5)], sub, Cc=R, K=1, com=com)
+    th = np.array([0.01, -0.02, 0.03, 0.9, 0.1, -0.2, 0.3]); th[3:] /= np.linalg.norm(th[3:])
+    Rm = Rotation.from_quat(th[[4, 5, 6, 3]]).as_matrix()
+    sp = S[0] @ Rm.T + th[:3]
+    d2 = ((sp[:, None, :] - sub[None]) ** 2).sum(-1)
+    nn = d2.argmin(1)
+    tcp = S[0].mean(0)
+    ref = (d2[np.arange(30), nn].sum() + ((Rm @ tcp + th[:3] - com) ** 2).sum()) / 30
+    cost, _ = o.match_terms(0, th, nn.astype(np.int32))
+    assert abs(cost - ref) <= 1e-12 * ref
