@@ -250,6 +250,20 @@ asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[5], long long launches
 asicp_status asicp_match_noalloc(const float *theta, int P, int K, const float *S_xyz, int N,
                                  const float *R_xyz, int M, int *nn_idx, void *cuda_stream);
 
+/* Mini-batches of the object cloud for the matching (Eq. 14 and Table I: iteration
+ * k matches the gripper points against a mini-batch of R whose size ramps up, N
+ * min(k, 2 k_max/3) / (2 k_max/3) in Table I).  offsets [iters + 1] (offsets[0] = 0)
+ * and indices [offsets[iters]] give per iteration k < iters the mini-batch as
+ * ascending indices into R; iterations k >= iters, and the final evaluation of
+ * asicp_run, use the whole cloud.  The collision test, the CoM and the cost
+ * normalisation (by N) keep the whole object; with debug = 1 the correspondences
+ * read back are positions within the mini-batch.  Host or device pointers, copied;
+ * NULL offsets switch mini-batches off; asicp_set_object switches them off too.
+ * One object per context; not with the tensor-core kernel shape (7), which the
+ * autotuner then skips.  Errors: INVALID_ARG (sizes, ranges, order, n_objects > 1),
+ * STATE (no object), CUDA. */
+asicp_status asicp_set_minibatch(asicp_ctx *ctx, const int *offsets, const int *indices, int iters);
+
 /* Time every shape of the forward-matching kernel (queries per thread, screening
  * chunk, threads per CTA, shared-memory tile size) on the context's current
  * objects and poses (the Fibonacci initial poses when none are set) and keep the

@@ -27,7 +27,8 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "STATE", 3: "CUDA", 4: "OOM", 5: "
 EXPORTED = ("asicp_config_default", "asicp_create", "asicp_destroy", "asicp_set_object",
             "asicp_set_gripper_sdf", "asicp_set_state", "asicp_step", "asicp_run", "asicp_best_grasps",
             "asicp_get_state", "asicp_kernel_times", "asicp_last_error", "asicp_match_noalloc",
-            "asicp_set_object_at", "asicp_set_particle_counts", "asicp_best_grasps_at", "asicp_autotune")
+            "asicp_set_object_at", "asicp_set_particle_counts", "asicp_best_grasps_at", "asicp_autotune",
+            "asicp_set_minibatch")
 
 
 class AsicpError(RuntimeError):
@@ -86,6 +87,7 @@ def load(build_if_missing: bool = True):
     lib.asicp_match_noalloc.argtypes = [vp, ip, ip, vp, ip, vp, ip, vp, vp]
     lib.asicp_set_object_at.argtypes = [vp, ip, vp, ip, vp, ip]
     lib.asicp_autotune.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_float)]
+    lib.asicp_set_minibatch.argtypes = [vp, vp, vp, C.c_int]
     lib.asicp_set_particle_counts.argtypes = [vp, vp, ip]
     lib.asicp_best_grasps_at.argtypes = [vp, ip, ip, vp, vp, vp, C.POINTER(C.c_int)]
     lib.asicp_last_error.argtypes = [vp]
@@ -155,6 +157,17 @@ def asicp_set_particle_counts(ctx, K) -> None:
     """``K`` int32 array of n_objects * P particle counts (object-major)."""
     K = np.ascontiguousarray(np.asarray(K, dtype=np.int32))
     _check(ctx, load().asicp_set_particle_counts(ctx, _ptr(K), int(K.size)))
+
+
+def asicp_set_minibatch(ctx, offsets, indices) -> None:
+    """Per-iteration mini-batches of the object cloud: int32 offsets [iters + 1] and ascending
+    indices (None switches them off)."""
+    if offsets is None:
+        _check(ctx, load().asicp_set_minibatch(ctx, None, None, 0))
+        return
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    idx = np.ascontiguousarray(np.asarray(indices, dtype=np.int32))
+    _check(ctx, load().asicp_set_minibatch(ctx, _ptr(off), _ptr(idx), int(off.size) - 1))
 
 
 def asicp_set_gripper_sdf(ctx, preshape, S_xyz, sdf_zyx, origin, voxel) -> None:

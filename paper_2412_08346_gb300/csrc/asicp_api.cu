@@ -93,6 +93,11 @@ struct asicp_ctx {
     std::vector<DevMem> grids;
     int k_next = 0;
 
+    // mini-batches of the object cloud per iteration (Table I), one object only
+    std::vector<int> mb_off;          // [iters + 1] on the host (sizes are fixed at capture)
+    long long mb_version = 0;         // bumped by every asicp_set_minibatch
+    DevMem mb_idx, mb_R, mb_Rx, mb_rmax;
+
     int fwd_variant = 0;              // forward-matching kernel shape (autotuner's choice)
     bool tuned = false;
 
@@ -405,8 +410,30 @@ void accumulate_graph_events(asicp_ctx *c)
 }
 
 // One pass of cost/gradient evaluation (+ update for mode 1/2).
-void iterate(asicp_ctx *c, int mode, float gamma)
+// Object 0's table points at the mini-batch of iteration k (k < the number of
+// mini-batches) or back at the whole cloud (otherwise), on the work stream.
+void select_minibatch(asicp_ctx *c, int k)
 {
+    if (c->mb_off.empty()) return;
+    cudaStream_t st = work_stream(c);
+    ObjMeta m = c->objmeta_h[0];
+    if (k >= 0 && k + 1 < (int)c->mb_off.size()) {
+        const int first = c->mb_off[k], cnt = c->mb_off[k + 1] - first;
+        const int Mpad = (cnt + kRefTilePts - 1) / kRefTilePts * kRefTilePts;
+        ck(launch_gather_points(c->objs[0].R.as<float4>(), c->mb_idx.as<int>() + first, cnt, c->mb_R.as<float4>(), st),
+           "mini-batch gather");
+        ck(launch_ref_prep(c->mb_R.as<float4>(), cnt, Mpad, c->mb_Rx.p, c->mb_rmax.as<float>(), st), "mini-batch prep");
+        m.R = c->mb_R.as<float4>();
+        m.Rx = c->mb_Rx.as<ulonglong2>();
+        m.M = cnt;
+        m.Mpad = Mpad;
+    }
+    ck(launch_store_meta(c->objmeta.as<ObjMeta>(), m, st), "object table");
+}
+
+void iterate(asicp_ctx *c, int mode, float gamma, int k)
+{
+    select_minibatch(c, k);
     const Layout L = c->layout();
     FwdArgs fa{};
     fa.L = L;
@@ -478,7 +505,7 @@ void iterate(asicp_ctx *c, int mode, float gamma)
 void step_impl(asicp_ctx *c, int k)
 {
     const int mode = k < c->cfg.k_stein ? 1 : 2;
-    iterate(c, mode, (float)gamma_of(c->cfg, k));
+    iterate(c, mode, (float)gamma_of(c->cfg, k), k);
     c->k_next = k + 1;
     c->stepped = true;
 }
@@ -489,7 +516,7 @@ void run_loop(asicp_ctx *c)
 {
     reset_convergence(c);
     for (int k = 0; k < c->cfg.k_max; ++k) step_impl(c, k);
-    iterate(c, 0, 0.f);   // final evaluation at the last poses
+    iterate(c, 0, 0.f, -1);   // final evaluation at the last poses (whole object cloud)
     ck(launch_select(c->layout(), c->cost.as<double>(), c->ncol.as<int>(), c->order.as<int>(), work_stream(c)),
        "select");
 }
@@ -501,7 +528,8 @@ std::vector<const void *> loop_key(const asicp_ctx *c)
     return {c->partgrp.p, c->grpoff.p, c->objmeta.p, c->items.p, c->ctaoff.p, c->com.p, c->rmax.p, c->colitems.p, c->collist.p,
             c->S.p, c->pconst.p, c->dmeta.p, c->theta.p, c->fsums.p, c->csums.p, c->ncol.p, c->colidx.p, c->cost.p,
             c->grad.p, c->prev.p, c->frozen.p, c->phi.p, c->h.p, c->order.p, c->errw.p, c->nnidx.p, c->dbg_d2.p,
-            c->dbg_sp.p, c->dbg_colnn.p, reinterpret_cast<const void *>((size_t)c->T),
+            c->dbg_sp.p, c->dbg_colnn.p, c->mb_idx.p, c->mb_R.p, c->mb_Rx.p,
+            reinterpret_cast<const void *>((size_t)c->mb_version), reinterpret_cast<const void *>((size_t)c->T),
             reinterpret_cast<const void *>((size_t)c->G), reinterpret_cast<const void *>((size_t)c->n_items),
             reinterpret_cast<const void *>((size_t)c->N), reinterpret_cast<const void *>((size_t)c->fwd_variant)};
 }
@@ -584,6 +612,10 @@ void autotune_impl(asicp_ctx *c, float *ms_out)
     float best = 0.f;
     int best_v = 0;
     for (int v = 0; v < kFwdVariants; ++v) {
+        if (v == 7 && !c->mb_off.empty()) {   // the tensor-core kernel has no mini-batch tiles
+            if (ms_out) ms_out[v] = 0.f;
+            continue;
+        }
         plan_fwd_items(c, v);
         FwdArgs fa{};
         fa.L = c->layout();
@@ -621,6 +653,8 @@ void set_object_impl(asicp_ctx *ctx, int o, const float *R_xyz, int M, const flo
     if (C_xyz && Mc < 1) fail(ASICP_ERR_INVALID_ARG, "set_object: Mc must be >= 1 when C is given");
     ObjBufs &b = ctx->objs[o];
     const int mc = C_xyz ? Mc : M;
+    ctx->mb_off.clear();          // mini-batches index the previous cloud
+    ++ctx->mb_version;
     b.set = false;
     ctx->run_done = false;
     ctx->stage.ensure(sizeof(float) * 3 * (size_t)(M > mc ? M : mc), "staging");
@@ -757,6 +791,42 @@ asicp_status asicp_set_particle_counts(asicp_ctx *ctx, const int *K, int n)
         ctx->Kg = k;
         ctx->layout_dirty = true;
         ctx->theta_set = false;
+        ctx->run_done = false;
+    });
+}
+
+asicp_status asicp_set_minibatch(asicp_ctx *ctx, const int *offsets, const int *indices, int iters)
+{
+    return guarded(ctx, [&] {
+        ++ctx->mb_version;
+        if (!offsets) {
+            ctx->mb_off.clear();
+            return;
+        }
+        if (ctx->nobj != 1) fail(ASICP_ERR_INVALID_ARG, "set_minibatch: one object per context");
+        if (!ctx->objs[0].set) fail(ASICP_ERR_STATE, "set_minibatch: set the object first");
+        if (!indices || iters < 1) fail(ASICP_ERR_INVALID_ARG, "set_minibatch: NULL indices or iters < 1");
+        if (ctx->fwd_variant == 7) fail(ASICP_ERR_INVALID_ARG, "set_minibatch: not with the tensor-core kernel shape");
+        const int M = ctx->objs[0].M;
+        std::vector<int> off(iters + 1);
+        ck(cudaMemcpy(off.data(), offsets, sizeof(int) * (iters + 1), cudaMemcpyDefault), "copy mini-batch offsets");
+        if (off[0] != 0) fail(ASICP_ERR_INVALID_ARG, "set_minibatch: offsets must start at 0");
+        for (int k = 0; k < iters; ++k)
+            if (off[k + 1] - off[k] < 1 || off[k + 1] - off[k] > M)
+                fail(ASICP_ERR_INVALID_ARG, "set_minibatch: every mini-batch needs 1..M points");
+        std::vector<int> idx(off[iters]);
+        ck(cudaMemcpy(idx.data(), indices, sizeof(int) * idx.size(), cudaMemcpyDefault), "copy mini-batch indices");
+        for (int k = 0; k < iters; ++k)
+            for (int i = off[k]; i < off[k + 1]; ++i)
+                if (idx[i] < 0 || idx[i] >= M || (i > off[k] && idx[i] <= idx[i - 1]))
+                    fail(ASICP_ERR_INVALID_ARG, "set_minibatch: indices must be ascending within [0, M)");
+        const int Mpad = (M + kRefTilePts - 1) / kRefTilePts * kRefTilePts;
+        ctx->mb_idx.ensure(sizeof(int) * idx.size(), "mini-batch indices");
+        ctx->mb_R.ensure(sizeof(float4) * M, "mini-batch points");
+        ctx->mb_Rx.ensure(sizeof(float4) * Mpad, "mini-batch screening layout");
+        ctx->mb_rmax.ensure(sizeof(float), "mini-batch rmax");
+        ck(cudaMemcpy(ctx->mb_idx.p, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice), "upload indices");
+        ctx->mb_off = off;
         ctx->run_done = false;
     });
 }

@@ -257,6 +257,8 @@ cudaError_t launch_check_finite(const float *v, long long n, int *err, cudaStrea
 cudaError_t launch_centroid(const float4 *X, int n, double *out3, cudaStream_t st);
 cudaError_t launch_preshape_consts(const float4 *S, int N, double *out12, cudaStream_t st);
 cudaError_t launch_fibonacci(const Layout &L, float radius, int mode, float *theta, cudaStream_t st);
+cudaError_t launch_gather_points(const float4 *R, const int *idx, int n, float4 *out, cudaStream_t st);
+cudaError_t launch_store_meta(ObjMeta *dst, const ObjMeta &v, cudaStream_t st);
 cudaError_t launch_set_theta(const float *theta7, int T, float *theta8, int *err, cudaStream_t st);
 cudaError_t launch_sdf_box(const float *grid, int nx, int ny, int nz, int *box6, cudaStream_t st);
 cudaError_t launch_select(const Layout &L, const double *cost, const int *ncol, int *order, cudaStream_t st);

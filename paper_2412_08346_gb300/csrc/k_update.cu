@@ -537,6 +537,27 @@ cudaError_t launch_fibonacci(const Layout &L, float radius, int mode, float *the
     return cudaGetLastError();
 }
 
+// out[i] = R[idx[i]], i < n (a mini-batch of the object cloud)
+__global__ void gather_points_kernel(const float4 *R, const int *idx, int n, float4 *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = R[idx[i]];
+}
+
+cudaError_t launch_gather_points(const float4 *R, const int *idx, int n, float4 *out, cudaStream_t st)
+{
+    gather_points_kernel<<<(n + 255) / 256, 256, 0, st>>>(R, idx, n, out);
+    return cudaGetLastError();
+}
+
+__global__ void store_meta_kernel(ObjMeta *dst, const ObjMeta v) { *dst = v; }
+
+cudaError_t launch_store_meta(ObjMeta *dst, const ObjMeta &v, cudaStream_t st)
+{
+    store_meta_kernel<<<1, 1, 0, st>>>(dst, v);
+    return cudaGetLastError();
+}
+
 // Particle -> group map and group offsets for P groups of K particles (one object).
 __global__ void uniform_groups_kernel(int *part_grp, int *grp_off, int P, int K)
 {

@@ -581,3 +581,42 @@ def test_stein_priors_match_oracle(stream):
     finally:
         asicp.asicp_destroy(ctx)
     print("priors:", rep)
+
+
+def test_minibatch_ramp_matches_oracle(stream):
+    """Table I's mini-batch ramp: iteration k matches against a seeded ascending subset of R (one
+    point at k = 0, the whole cloud from 2 k_max / 3 on); the collision test and the CoM keep the
+    whole object.  Teacher-forced steps against an oracle built on the same subset."""
+    import oracle
+    w = synth.custom_case(P=2, K=16, N=400, M=3000, grid=24, k_max=12, seed=41, k_stein=4)
+    R = w.objects[0].points
+    off, idx = synth.minibatch_ramp(len(R), w.k_max, seed=7)
+    com = R.astype(np.float64).mean(0)
+    S = np.stack([pre.S for pre in w.preshapes])
+    sdfs = [(pre.sdf, pre.origin, pre.voxel) for pre in w.preshapes]
+    P, K, N = 2, w.K, 400
+    ctx = _ctx(w, stream)
+    rep = {}
+    try:
+        keep = tl.upload(ctx, w)
+        asicp.asicp_set_minibatch(ctx, off, idx)
+        theta0 = np.tile(oracle.fibonacci_init(K, com, 0.08), (P, 1)).astype(np.float32)
+        asicp.asicp_set_state(ctx, theta0, 0)
+        for k in (0, 1, 5, 9):
+            sub = R[idx[off[k]:off[k + 1]]]
+            orc = oracle.Oracle(S, sdfs, sub, Cc=R, K=K, com=com)
+            asicp.asicp_set_state(ctx, tl.read_theta(ctx, P * K), k)
+            before = tl.read_theta(ctx, P * K)
+            asicp.asicp_step(ctx, k)
+            st = tl.read_state(ctx, P, K, N, len(R))
+            assert st["nn_idx"].max() < len(sub)
+            tl.check_step(orc, w, before, st, k, rep)
+        # switching the mini-batches off restores whole-cloud matching
+        asicp.asicp_set_minibatch(ctx, None, None)
+        asicp.asicp_step(ctx, 3)
+        st = tl.read_state(ctx, P, K, N, len(R))
+        assert st["nn_idx"].max() > len(R) // 2
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
+    print("mini-batch:", rep)
