@@ -368,3 +368,12 @@ def minibatch_ramp(M: int, k_max: int, seed: int):
         idx.append(sel)
         offs.append(offs[-1] + m)
     return np.asarray(offs, np.int32), np.concatenate(idx).astype(np.int32)
+
+
+def large_case(seed: int = BASE_SEED + 4, k_max: int = 10) -> Workload:
+    """The largest single-object workload: 3 preshapes x 1024 particles, N=4096, M=65536 points of a
+    superquadric partial view, 128^3 SDF."""
+    pre = make_preshapes(3, 4096, 128, seed)
+    obj = partial_object(65536, seed + 1000, kind="superquadric")
+    return Workload(f"partial-P3-K1024-N4096-M65536-sdf128-it{k_max}", pre, [obj], K=1024, k_max=k_max,
+                    k_stein=k_stein_for(k_max), schedule=0)

@@ -620,3 +620,30 @@ def test_minibatch_ramp_matches_oracle(stream):
     finally:
         asicp.asicp_destroy(ctx)
     print("mini-batch:", rep)
+
+
+def test_largest_workload_sampled_steps_and_tensor_core_agreement(stream):
+    """3 x 1024 particles, N=4096, M=65536 (superquadric partial view), SDF 128^3 -- the maximum
+    particle count per preshape and the largest clouds: sampled particles of an SVGD and an SGD step
+    against the oracle, and the tensor-core kernel's correspondences against the float32 kernel's
+    on every query (identical except near-ties)."""
+    import oracle
+    w = synth.large_case()
+    g = np.random.default_rng(4)
+    sample = sorted(g.choice(w.K * 3, 6, replace=False).tolist())
+    rep = _teacher_forced_run(w, stream, [0, 7], {}, sample=sample)
+    print("largest workload sampled:", rep)
+    com = w.objects[0].points.astype(np.float64).mean(0)
+    th = np.tile(oracle.fibonacci_init(w.K, com, 0.15), (3, 1)).astype(np.float32)
+    a = _step_indices(w, stream, th, 0)
+    b = _step_indices(w, stream, th, asicp.FWD_VARIANTS.index("tc-tf32x3-m128-n128"))
+    diff = np.nonzero(a["nn_idx"] != b["nn_idx"])
+    n_diff = len(diff[0])
+    print(f"tensor-core vs float32: {n_diff} of {a['nn_idx'].size} indices differ")
+    if n_diff:
+        R = w.objects[0].points.astype(np.float64)
+        sp = a["s_prime"][diff].astype(np.float64)
+        da = ((sp - R[a["nn_idx"][diff]]) ** 2).sum(-1)
+        db = ((sp - R[b["nn_idx"][diff]]) ** 2).sum(-1)
+        assert (np.abs(da - db) / np.maximum(np.minimum(da, db), 1e-300)).max() <= tl.NEAR_TIE_REL
+        assert n_diff <= 1e-4 * a["nn_idx"].size
