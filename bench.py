@@ -39,7 +39,7 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
 # DRAM bytes (read + write) of one forward-matching launch from the committed ncu capture
 # (profiles/fwd_match_kernel_profile-case-P1-K256-N2048-M8192.md); null once the kernel changes
-FWD_DRAM_BYTES_PER_LAUNCH = 406528
+FWD_DRAM_BYTES_PER_LAUNCH = None
 OPS_PER_PAIR = 4          # algorithmic FP32-lane work per particle*point pair: 3 FMA + 1 compare
 FMA_PER_PAIR = 3          # of which FMA-pipe work (the compare runs as half a 3-input min on the ALU pipe)
 TOPK = 16

@@ -79,6 +79,29 @@ __device__ __forceinline__ void exact_scan(const float4 *__restrict__ R, int lo,
     }
 }
 
+// Exact-form nearest point of query (qx, qy, qz) among all M object points, found by
+// the whole warp together (lane l takes points l, l + 32, ...; ties to the lower
+// index); every lane receives the result.  Call with all 32 lanes.
+__device__ __forceinline__ void warp_exact_all(const float4 *__restrict__ R, int M, float qx, float qy, float qz,
+                                               float &best, int &bi)
+{
+    float wb = __int_as_float(0x7f800000);
+    int wi = 0x7fffffff;
+    for (int r = (int)(threadIdx.x & 31); r < M; r += 32) {
+        const float4 v = __ldg(R + r);
+        const float d = dist2_f32(qx, qy, qz, v.x, v.y, v.z);
+        if (d < wb) { wb = d; wi = r; }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, wb, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, wi, off);
+        if (ob < wb || (ob == wb && oi < wi)) { wb = ob; wi = oi; }
+    }
+    best = wb;
+    bi = wi < M ? wi : 0;    // no finite distance at all (not reached with finite inputs)
+}
+
 // Double-float accumulation (hi + lo, ~48-bit significand) from float32 error-free
 // transformations: products are split exactly by an FMA, sums by two-sum.  Used
 // for the per-particle sums, where float64 arithmetic would dominate the run time

@@ -19,8 +19,8 @@
 //     excluded.  If only chunk c1 (and c2 when b2 <= b1 + 2 delta) can hold r*,
 //     their points are re-evaluated with the exact-form distance
 //     (dx^2 + dy^2 + dz^2 in float32) in index order; if a third chunk could
-//     (b3 <= b1 + 2 delta, rare), the query falls back to an exact scan of the
-//     whole cloud.  The result is the lowest-index minimum of the exact-form
+//     (b3 <= b1 + 2 delta, rare), the warp scans the whole cloud for that query
+//     together.  The result is the lowest-index minimum of the exact-form
 //     float32 distance among all points that can be nearest.
 //
 // Object tiles are staged in shared memory by 1D bulk (TMA) copies into two
@@ -170,20 +170,32 @@ __device__ __forceinline__ bool match_pass(const FwdArgs &a, const ObjMeta &om, 
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int li = q * kThreads + threadIdx.x;
-        if (li >= nq) continue;
-        const long long g = q0 + li;
+        const bool valid = li < nq;
         const float thr = b1[q] + win[q];
+        // a third candidate chunk: the whole cloud, scanned by the warp together (one such
+        // query at a time) rather than by its thread alone
+        const bool whole = valid && b3[q] <= thr;
         float best = __int_as_float(0x7f800000);
         int bi = 0;
-        if (b3[q] <= thr) {
-            exact_scan(om.R, 0, om.M, sx[q], sy[q], sz[q], best, bi);
-        } else {
+        if (valid && !whole) {
             int ca = c1[q], cb = c2[q];
             const bool two = b2[q] <= thr && cb != ca;
             if (two && cb < ca) { const int x = ca; ca = cb; cb = x; }
             exact_scan(om.R, ca * kChunk, min((ca + 1) * kChunk, om.M), sx[q], sy[q], sz[q], best, bi);
             if (two) exact_scan(om.R, cb * kChunk, min((cb + 1) * kChunk, om.M), sx[q], sy[q], sz[q], best, bi);
         }
+        unsigned pending = __ballot_sync(0xffffffffu, whole);
+        while (pending) {
+            const int src = __ffs(pending) - 1;
+            pending &= pending - 1;
+            float wb;
+            int wi;
+            warp_exact_all(om.R, om.M, __shfl_sync(0xffffffffu, sx[q], src), __shfl_sync(0xffffffffu, sy[q], src),
+                           __shfl_sync(0xffffffffu, sz[q], src), wb, wi);
+            if ((int)(threadIdx.x & 31) == src) { best = wb; bi = wi; }
+        }
+        if (!valid) continue;
+        const long long g = q0 + li;
         a.nn_idx[g] = bi;
         if (a.dbg_d2) a.dbg_d2[g] = best;
         if (a.dbg_sp) {

@@ -383,21 +383,10 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
             while (pending) {
                 const int src = __ffs(pending) - 1;
                 pending &= pending - 1;
-                const float qx = __shfl_sync(0xffffffffu, o.x, src), qy = __shfl_sync(0xffffffffu, o.y, src),
-                            qz = __shfl_sync(0xffffffffu, o.z, src);
-                float wb = __int_as_float(0x7f800000);
-                int wi = 0x7fffffff;
-                for (int r = lane; r < om.M; r += 32) {
-                    const float4 v = __ldg(om.R + r);
-                    const float d = dist2_f32(qx, qy, qz, v.x, v.y, v.z);
-                    if (d < wb) { wb = d; wi = r; }
-                }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    const float ob = __shfl_xor_sync(0xffffffffu, wb, off);
-                    const int oi = __shfl_xor_sync(0xffffffffu, wi, off);
-                    if (ob < wb || (ob == wb && oi < wi)) { wb = ob; wi = oi; }
-                }
+                float wb;
+                int wi;
+                warp_exact_all(om.R, om.M, __shfl_sync(0xffffffffu, o.x, src), __shfl_sync(0xffffffffu, o.y, src),
+                               __shfl_sync(0xffffffffu, o.z, src), wb, wi);
                 if (lane == src) { best = wb; bi = wi; }
             }
             if (valid) {
