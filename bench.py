@@ -43,6 +43,7 @@ FWD_DRAM_BYTES_PER_LAUNCH = None
 OPS_PER_PAIR = 4          # algorithmic FP32-lane work per particle*point pair: 3 FMA + 1 compare
 FMA_PER_PAIR = 3          # of which FMA-pipe work (the compare runs as half a 3-input min on the ALU pipe)
 TOPK = 16
+METRIC = "AS-ICP particle*point pairs/s (forward matching) and ms per grasp set"
 
 
 def parse():
@@ -184,7 +185,7 @@ def run_reference(args, rank, world):
     sample = (f"{info['particles_per_preshape']} particles per preshape x {len(w.preshapes)} preshapes, "
               f"whole iterations (N={w.preshapes[0].S.shape[0]}, M={len(w.objects[0].points)}), "
               f"~{per_step:.0f} s per step")
-    line = {"impl": "reference", "metric": "AS-ICP particle*point pairs/s (forward matching)", "value": value,
+    line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -287,7 +288,7 @@ def run_gpu(args, rank, world, local_rank):
     asicp.asicp_destroy(ctx)
     if rank == 0:
         line = {
-            "metric": "AS-ICP particle*point pairs/s (forward matching) and ms per grasp set",
+            "metric": METRIC,
             "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
