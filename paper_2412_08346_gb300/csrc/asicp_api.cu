@@ -222,7 +222,7 @@ double gamma_of(const asicp_config &c, int k)
 // every CTA gets a contiguous range of the item table.
 void plan_fwd_items(asicp_ctx *c, int v)
 {
-    constexpr int kPlanRounds = 4;
+    constexpr int kPlanRounds = 3;
     const int grid = fwd_shape_grid(v), threads = fwd_shape_threads(v), qmax = fwd_shape_queries(v), N = c->N;
     const std::vector<ObjMeta> &om = c->objmeta_h;
     double W = 0.0;

@@ -8,7 +8,7 @@
 //     A row    = [a_h, a_h, a_l, 1, 1, 1, 0, 0, 0, 0]          (K = 16)
 //     B column = [r_h, r_l, r_h, w_1, w_2, w_3, 0, 0, 0, 0]
 // gives A.B = w + a_h.r_h + a_h.r_l + a_l.r_h: two kind::tf32 MMAs (K = 8 each),
-// 128 queries x 128 object points, accumulated in float32 in tensor memory.
+// 128 queries x 256 object points, accumulated in float32 in tensor memory.
 //
 // Error bound, u = 2^-24: the dropped a_l.r_l and the rounding of the low parts
 // are at most 3 * 2^-22 |a_k| |r_k| per coordinate, i.e. 24 u |s'| |r| in all;
@@ -26,14 +26,18 @@
 // the float32 kernel.
 //
 // Per CTA: one block of 128 queries (one per reduction thread, TMEM lane =
-// query); object tiles of 128 points (8 KB, already in the MMA's shared-memory
+// query); object tiles of 256 points (16 KB, already in the MMA's shared-memory
 // layout) stream through a ring of kStages buffers by 1D bulk copies.  One
-// thread issues the copies and MMAs (tile t + 1 while the reduction warps read
-// tile t from the other accumulator); a tcgen05.ld.red per 64 columns returns
-// a chunk minimum directly.  Two CTAs per SM (256 TMEM columns each) overlap
-// one another's per-item prologue and exact stage.  Every wait is bounded: on expiry the kernel reports ASICP_ERR_TIMEOUT
-// through the error word, drains its own copies and MMAs (bounded), frees its
-// tensor memory and returns.
+// thread issues the copies and another the MMAs: every mbarrier, copy or MMA
+// operation of a single thread costs on the order of a hundred cycles (measured
+// with clock64 stamps on GB300), so one thread doing both set the pace, and a
+// wide tile amortises those operations over more pairs.  A tcgen05.ld.red per
+// 64 columns returns a chunk minimum directly.  Each CTA has one 256-column
+// accumulator; the two CTAs of an SM (256 TMEM columns each) take turns on the
+// tensor pipe, and overlap one another's per-item prologue and exact stage.
+// Every wait is bounded: on expiry the kernel reports ASICP_ERR_TIMEOUT through
+// the error word, drains its own copies and MMAs (bounded), frees its tensor
+// memory and returns.
 #include "asicp_internal.cuh"
 #include "async_copy.cuh"
 
@@ -46,21 +50,23 @@ namespace {
 constexpr int kRows = 128;                 // queries per block = MMA M
 constexpr int kBlocks = 1;                 // query blocks per CTA
 constexpr int kQueries = kRows * kBlocks;  // queries per item = reduction threads
-constexpr int kThreadsTc = kQueries + 32;  // + one warp for the copies and MMAs
-constexpr int kCols = 128;                 // object points per tile = MMA N
+constexpr int kThreadsTc = kQueries + 64;  // + one warp for the copies, one for the MMAs
+constexpr int kCols = 256;                 // object points per tile = MMA N
+constexpr int kBufs = 1;                   // accumulators per query block (a power of two)
 constexpr int kAug = 16;                   // augmented length (two K = 8 MMAs)
-constexpr int kStages = 10;                // object tiles in flight
+constexpr int kStages = 5;                 // object tiles in flight
 constexpr int kChunk = 64;                 // screening chunk = columns per tcgen05.ld.red
 constexpr int kTop = 4;                    // chunks per query the exact stage rescans at most
-constexpr unsigned kTileBytes = kCols * kAug * 4;       // 4 KB
+constexpr unsigned kTileBytes = kCols * kAug * 4;       // 16 KB
 constexpr unsigned kABlockBytes = kRows * kAug * 4;     // 8 KB
 constexpr unsigned kABytes = kBlocks * kABlockBytes;
 constexpr unsigned kLBO = 128, kSBO = 512; // core matrices (8 rows x 16 B): K-adjacent 128 B, row groups 512 B
-constexpr int kTmemCols = kBlocks * 2 * kCols;          // two accumulators per block
+constexpr int kTmemCols = kBlocks * kBufs * kCols;      // kBufs accumulators per block
 constexpr size_t kSmemBytes = kABytes + (size_t)kStages * kTileBytes;
 static_assert(kRefTilePts % kCols == 0, "object padding must be whole tiles");
 static_assert(kTmemCols == 256, "two CTAs per SM share the 512 tensor-memory columns");
 static_assert(kCols % kChunk == 0, "whole chunks per tile");
+static_assert((kBufs & (kBufs - 1)) == 0, "accumulator count");
 
 // instruction descriptor: D f32, A and B tf32, both K-major, N = kCols, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kCols >> 3) << 17) |
@@ -119,15 +125,20 @@ __device__ __forceinline__ float ld_min64(uint32_t taddr)
     return m;
 }
 
-// Exact-form nearest point among object points [lo, hi), merged into (best, bi)
-// with ties to the lower index.
-__device__ __forceinline__ void exact_scan_tie(const float4 *__restrict__ R, int lo, int hi, float3 q, float &best,
-                                               int &bi)
+// Exact-form nearest point among the object points of chunk [lo, lo + kChunk) below
+// M, merged into (best, bi) with ties to the lower index.  A fixed trip count with
+// clamped addresses lets sixteen loads be in flight at once: with most of shared
+// memory given to the tile ring, the object cloud is not L1-resident and each load
+// pays the L2 latency.
+__device__ __forceinline__ void exact_chunk_tie(const float4 *__restrict__ R, int lo, int M, float3 q, float &best,
+                                                int &bi)
 {
-    for (int r = lo; r < hi; ++r) {
-        const float4 v = __ldg(R + r);
+#pragma unroll 16
+    for (int k = 0; k < kChunk; ++k) {
+        const int r = lo + k;
+        const float4 v = __ldg(R + min(r, M - 1));
         const float d = dist2_f32(q.x, q.y, q.z, v.x, v.y, v.z);
-        if (d < best || (d == best && r < bi)) { best = d; bi = r; }
+        if (r < M && (d < best || (d == best && r < bi))) { best = d; bi = r; }
     }
 }
 
@@ -171,7 +182,7 @@ size_t tc_ref_bytes(int Mpad) { return (size_t)Mpad / kCols * kTileBytes; }
 // Warp roles: warps 0-3 (one query per thread; warp w reads TMEM lanes
 // 32 w .. 32 w + 31) build the
 // augmented query rows, reduce the accumulators and make the exact choice;
-// lane 0 of warp 4 streams the object tiles and issues the MMAs.  They meet on
+// lane 0 of warp 4 streams the object tiles, lane 0 of warp 5 issues the MMAs.  They meet on
 // mbarriers only (no CTA-wide barrier inside the loop):
 //   bfull[s]  tile in stage s has landed          (copy -> MMA)
 //   bempty[s] the MMAs reading stage s are done    (MMA commit -> copy)
@@ -183,7 +194,7 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     unsigned char *sA = smem_tc;
     unsigned char *sB = smem_tc + kABytes;
-    __shared__ __align__(8) unsigned long long bfull[kStages], bempty[kStages], accf[2], acce[2], afull;
+    __shared__ __align__(8) unsigned long long bfull[kStages], bempty[kStages], accf[kBufs], acce[kBufs], afull;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -211,7 +222,7 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
     if (tid == 0) {
         s_abort = 0;
         for (int s = 0; s < kStages; ++s) { mbar_init(&bfull[s], 1); mbar_init(&bempty[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], kQueries); }
+        for (int b = 0; b < kBufs; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], kQueries); }
         mbar_init(&afull, kQueries);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -227,45 +238,49 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
     const uint32_t tmem = s_tmem;
 
     if (warp == kQueries / 32) {
-        // ------------------------------------------------ copies and MMAs (one thread)
+        // ------------------------------------------------ object-tile copies (one thread)
         if (lane == 0) {
-            int p_it = it0, p_tile = 0, p_ntiles = 0;
-            const unsigned char *p_src = nullptr;
-            long long p_seq = 0, seq = 0;
-            auto producer_item = [&]() {
-                if (p_it >= it1) return;
-                const ObjMeta &om = a.L.obj[item_at(p_it).obj];
-                p_src = reinterpret_cast<const unsigned char *>(om.Rt);
-                p_ntiles = om.Mpad / kCols;
-            };
-            // copy the next tile into its stage once the MMAs that last read the stage are done
-            auto issue_load = [&]() -> bool {
-                const int stage = (int)(p_seq % kStages);
-                if (!mbar_wait(&bempty[stage], (unsigned)(((p_seq / kStages) & 1) ^ 1))) return false;
-                mbar_arrive_tx(&bfull[stage], kTileBytes);
-                bulk_load(sB + (size_t)stage * kTileBytes, p_src + (size_t)p_tile * kTileBytes, kTileBytes,
-                          &bfull[stage]);
-                ++p_seq;
-                if (++p_tile == p_ntiles) {
-                    p_tile = 0;
-                    p_it += step;
-                    producer_item();
+            // copies issued so far, the stage of the next one and the parity of the ring's lap
+            int p_seq = 0, p_stage = 0;
+            unsigned p_lap = 0u;
+            bool ok = true;
+            for (int it = it0; it < it1 && ok; it += step) {
+                const ObjMeta &om = a.L.obj[item_at(it).obj];
+                const unsigned char *src = reinterpret_cast<const unsigned char *>(om.Rt);
+                const int ntiles = om.Mpad / kCols;
+                for (int t = 0; t < ntiles; ++t) {
+                    // the stage is free once the MMAs of its previous tile are done
+                    if (s_abort || !mbar_wait(&bempty[p_stage], p_lap ^ 1u)) { ok = false; break; }
+                    mbar_arrive_tx(&bfull[p_stage], kTileBytes);
+                    bulk_load(sB + (size_t)p_stage * kTileBytes, src + (size_t)t * kTileBytes, kTileBytes,
+                              &bfull[p_stage]);
+                    ++p_seq;
+                    if (++p_stage == kStages) { p_stage = 0; p_lap ^= 1u; }
                 }
-                return true;
-            };
-            producer_item();
+            }
+            if (!ok) {
+                fail();
+                // drain (bounded): the last copy issued into each stage
+                for (int q = p_seq > kStages ? p_seq - kStages : 0; q < p_seq; ++q)
+                    mbar_wait(&bfull[q % kStages], (unsigned)((q / kStages) & 1));
+            }
+        }
+    } else if (warp == kQueries / 32 + 1) {
+        // ------------------------------------------------ MMAs (one thread)
+        if (lane == 0) {
+            // tiles consumed so far, their stage and the parity of the ring's lap (kept
+            // incrementally: no division on this thread's path)
+            int seq = 0, c_stage = 0;
+            unsigned c_lap = 0u;
             int ia = 0;
             for (int it = it0; it < it1 && !s_abort; it += step, ++ia) {
                 const int ntiles = a.L.obj[item_at(it).obj].Mpad / kCols;
                 if (!mbar_wait(&afull, (unsigned)(ia & 1))) { fail(); break; }
                 tc_fence_after();
                 for (int t = 0; t < ntiles; ++t, ++seq) {
-                    // copies run kStages - 2 tiles ahead: the stage they reuse was read by MMA(seq - 2)
-                    while (p_it < it1 && p_seq <= seq + kStages - 2)
-                        if (!issue_load()) { fail(); break; }
-                    const int stage = (int)(seq % kStages), buf = (int)(seq & 1);
-                    if (s_abort || !mbar_wait(&bfull[stage], (unsigned)((seq / kStages) & 1)) ||
-                        !mbar_wait(&acce[buf], (unsigned)(((seq >> 1) & 1) ^ 1))) {
+                    const int stage = c_stage, buf = (int)((unsigned)seq % kBufs);
+                    if (s_abort || !mbar_wait(&bfull[stage], c_lap) ||
+                        !mbar_wait(&acce[buf], (((unsigned)seq / kBufs) & 1u) ^ 1u)) {
                         fail();
                         break;
                     }
@@ -273,20 +288,19 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
                     const unsigned b0 = smem_u32(sB + (size_t)stage * kTileBytes);
 #pragma unroll
                     for (int blk = 0; blk < kBlocks; ++blk) {
-                        const uint32_t d = tmem + (uint32_t)(blk * 2 + buf) * kCols;
+                        const uint32_t d = tmem + (uint32_t)(blk * kBufs + buf) * kCols;
                         const unsigned a0 = smem_u32(sA + blk * kABlockBytes);
                         mma_tf32(d, smem_desc(a0), smem_desc(b0), 0u);
                         mma_tf32(d, smem_desc(a0 + 256), smem_desc(b0 + 256), 1u);
                     }
                     mma_commit(&bempty[stage]);
                     mma_commit(&accf[buf]);
+                    if (++c_stage == kStages) { c_stage = 0; c_lap ^= 1u; }
                 }
             }
-            if (s_abort) {
-                // drain (bounded): the MMAs issued, then the copies no MMA consumed
-                if (seq > 0) mbar_wait(&accf[(seq - 1) & 1], (unsigned)(((seq - 1) >> 1) & 1));
-                for (long long q = seq; q < p_seq; ++q) mbar_wait(&bfull[q % kStages], (unsigned)((q / kStages) & 1));
-            }
+            // drain (bounded): the MMAs issued
+            if (s_abort && seq > 0)
+                mbar_wait(&accf[(unsigned)(seq - 1) % kBufs], ((unsigned)(seq - 1) / kBufs) & 1u);
         }
     } else {
         // ------------------------------------------------ query rows, reduction, exact choice
@@ -336,14 +350,14 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
             for (int k = 0; k < kTop; ++k) { bk[k] = __int_as_float(0x7f800000); ck[k] = 0; }
             bool good = true;
             for (int t = 0; t < ntiles; ++t, ++seq) {
-                const int buf = (int)(seq & 1);
-                good = mbar_wait_warp(&accf[buf], (unsigned)((seq >> 1) & 1));
+                const int buf = (int)((unsigned long long)seq % kBufs);
+                good = mbar_wait_warp(&accf[buf], (unsigned)(((unsigned long long)seq / kBufs) & 1u));
                 if (!__all_sync(0xffffffffu, good && !s_abort)) { good = false; break; }
                 tc_fence_after();
                 float mv[kCols / kChunk];
 #pragma unroll
                 for (int h = 0; h < kCols / kChunk; ++h)
-                    mv[h] = ld_min64(tmem + lane_base + (uint32_t)(blk * 2 + buf) * kCols + (uint32_t)(h * kChunk));
+                    mv[h] = ld_min64(tmem + lane_base + (uint32_t)(blk * kBufs + buf) * kCols + (uint32_t)(h * kChunk));
                 tc_fence_before();
                 mbar_arrive(&acce[buf]);
 #pragma unroll
@@ -377,7 +391,7 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
 #pragma unroll
                 for (int k = 0; k < kTop; ++k)
                     if (bk[k] <= thr)
-                        exact_scan_tie(om.R, ck[k] * kChunk, min((ck[k] + 1) * kChunk, om.M), o, best, bi);
+                        exact_chunk_tie(om.R, ck[k] * kChunk, om.M, o, best, bi);
             }
             unsigned pending = __ballot_sync(0xffffffffu, whole);
             while (pending) {
