@@ -232,7 +232,7 @@ def asicp_match_noalloc(theta, S_xyz, R_xyz, nn_idx, P: int, K: int, stream=None
 
 FWD_VARIANTS = ("qpt8-chunk64-t128-tile2048", "qpt8-chunk32-t128-tile2048", "qpt4-chunk64-t256-tile2048",
                 "qpt4-chunk32-t256-tile2048", "qpt4-chunk64-t128-tile1024", "qpt8-chunk64-t128-tile1024",
-                "qpt6-chunk64-t128-tile1024", "tc-tf32x3-m128-n256")
+                "qpt6-chunk64-t128-tile1024", "tc-f16x3-m128-n256")
 FWD_SHAPES = len(FWD_VARIANTS)          # ASICP_FWD_SHAPES
 
 

@@ -673,7 +673,7 @@ void set_object_impl(asicp_ctx *ctx, int o, const float *R_xyz, int M, const flo
     b.Rx.ensure(sizeof(float4) * (size_t)Mpad, "screening layout");
     ck(launch_ref_prep(b.R.as<float4>(), M, Mpad, b.Rx.p, ctx->rmax.as<float>() + o, ctx->st), "ref prep");
     b.Rt.ensure(tc_ref_bytes(Mpad), "tensor-core object tiles");
-    ck(launch_tc_ref_prep(b.R.as<float4>(), M, Mpad, b.Rt.as<float>(), ctx->st), "tensor-core ref prep");
+    ck(launch_tc_ref_prep(b.R.as<float4>(), M, Mpad, ctx->rmax.as<float>() + o, b.Rt.p, ctx->st), "tensor-core ref prep");
     sync_and_check_err(ctx, "set_object");
     b.M = M;
     b.Mpad = Mpad;

@@ -223,7 +223,7 @@ const char *fwd_variant_name(int v);
 cudaError_t init_collision_attributes();
 cudaError_t init_update_attributes();
 cudaError_t launch_ref_prep(const float4 *R, int M, int Mpad, void *Rx, float *rmax, cudaStream_t st);
-cudaError_t launch_tc_ref_prep(const float4 *R, int M, int Mpad, float *Rt, cudaStream_t st);
+cudaError_t launch_tc_ref_prep(const float4 *R, int M, int Mpad, const float *rmax, void *Rt, cudaStream_t st);
 size_t tc_ref_bytes(int Mpad);         // bytes of the tensor-core object tiles
 cudaError_t launch_fwd_match_tc(const FwdArgs &a, cudaStream_t st);
 int fwd_tc_grid();

@@ -344,7 +344,7 @@ const char *fwd_variant_name(int v)
     static const char *names[kFwdVariants] = {"qpt8-chunk64-t128-tile2048", "qpt8-chunk32-t128-tile2048",
                                               "qpt4-chunk64-t256-tile2048", "qpt4-chunk32-t256-tile2048",
                                               "qpt4-chunk64-t128-tile1024", "qpt8-chunk64-t128-tile1024",
-                                              "qpt6-chunk64-t128-tile1024", "tc-tf32x3-m128-n256"};
+                                              "qpt6-chunk64-t128-tile1024", "tc-f16x3-m128-n256"};
     return (v >= 0 && v < kFwdVariants) ? names[v] : "unknown";
 }
 

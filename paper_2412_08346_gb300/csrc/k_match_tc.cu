@@ -1,47 +1,54 @@
-// Forward matching on the tensor cores: tcgen05 TF32 MMAs with split operands.
+// Forward matching on the tensor cores: tcgen05 f16 MMAs with split operands.
 //
 // The screening value of the float32 kernel, d~(r) = |r|^2 - 2 s'.r (Eq. 1 up to
 // the query's own |s'|^2), is a contraction of an augmented query row with an
-// augmented object-point column.  Every factor is split into two TF32 parts
-// (x = x_h + x_l, each exactly representable in TF32, rounded to nearest) and
-// |r|^2 into three (exact), so that with a = -2 s'
-//     A row    = [a_h, a_h, a_l, 1, 1, 1, 0, 0, 0, 0]          (K = 16)
-//     B column = [r_h, r_l, r_h, w_1, w_2, w_3, 0, 0, 0, 0]
-// gives A.B = w + a_h.r_h + a_h.r_l + a_l.r_h: two kind::tf32 MMAs (K = 8 each),
-// 128 queries x 256 object points, accumulated in float32 in tensor memory.
+// augmented object-point column.  Coordinates are scaled by a power of two lam
+// (lam Rmax in (128, 256], Rmax = max |r|), every scaled factor is split into two
+// f16 parts (x = x_h + x_l, rounded to nearest) and lam^2 |r|^2 / 4 into three,
+// so that with a = -2 lam s' and rho = lam r
+//     A row    = [a_h, a_h, a_l, 4, 4, 4, 2^15, 0, 0, 0]          (K = 16)
+//     B column = [rho_h, rho_l, rho_h, w_1, w_2, w_3, 0, 0, 0, 0]
+// gives A.B = lam^2 (|r|^2 - 2 s'.r) up to rounding: one kind::f16 MMA, 128
+// queries x 256 object points, accumulated in float32 in tensor memory.  (Slot
+// 12 is 2^15 for padding columns, which then never screen in.)
 //
-// Error bound, u = 2^-24: the dropped a_l.r_l and the rounding of the low parts
-// are at most 3 * 2^-22 |a_k| |r_k| per coordinate, i.e. 24 u |s'| |r| in all;
-// w = fl(|r|^2) is within u |r|^2; the products of TF32 values are exact, and
-// the tensor core's float32 accumulation is taken to stay within 16 u of the sum
-// of the magnitudes of its addends (<= 1.002 (|r|^2 + 2 |s'| |r|)); measured on
-// GB300: at most 3.3 u over 10^6 random rows of this form.  So
-//     delta_tc = u (18 Rmax^2 + 57 |s'| Rmax)
-// bounds |d~_tc - (|r|^2 - 2 s'.r)|.  Each query keeps its kTop best chunk
-// minima (chunks of 64 object points) and the best of the rest; the chunks
-// within 2 delta_tc of the best are rescanned with the exact-form float32
+// Error bound, u = 2^-24, in lam^2 units: the dropped a_l.rho_l and the rounding
+// of the low parts are at most 3 * 2^-22 |a_k| |rho_k| per coordinate (f16 has an
+// 11-bit significand), i.e. 24 u |s'| |r| in all; w = fl(lam^2 |r|^2) is within
+// u lam^2 |r|^2; products of f16 values are exact in float32, and the tensor
+// core's float32 accumulation is taken to stay within 16 u of the sum of the
+// magnitudes of its addends (<= 1.002 (|r|^2 + 2 |s'| |r|)); measured on GB300:
+// at most 2.9 u over 10^6 random rows of this form.  Low parts below the f16
+// normal range (2^-14) add at most 2^-14 * 1.74 lam (2 |s'| + |r|) even if
+// flushed, and the last part of w / 4 at most 2^-12.  So
+//     delta_tc = u lam^2 (18 Rmax^2 + 57 |s'| Rmax) + 2^-14 * 1.74 lam (2 |s'| + Rmax) + 2^-12
+// bounds |d~_tc - lam^2 (|r|^2 - 2 s'.r)|.  A query whose scaled coordinates
+// would leave the f16 range takes the whole-cloud scan.  Each query keeps its kTop
+// best chunk minima (chunks of 64 object points) and the best of the rest; the
+// chunks within 2 delta_tc of the best are rescanned with the exact-form float32
 // distance (ties to the lower index) by the query's thread, or, when more than
 // kTop qualify, the warp scans the whole cloud for that query together.  The
 // result is the exact-form argmin over every point that can be nearest, as in
 // the float32 kernel.
 //
 // Per CTA: one block of 128 queries (one per reduction thread, TMEM lane =
-// query); object tiles of 256 points (16 KB, already in the MMA's shared-memory
+// query); object tiles of 256 points (8 KB, already in the MMA's shared-memory
 // layout) stream through a ring of kStages buffers by 1D bulk copies.  One
 // thread issues the copies and another the MMAs: every mbarrier, copy or MMA
 // operation of a single thread costs on the order of a hundred cycles (measured
 // with clock64 stamps on GB300), so one thread doing both set the pace, and a
-// wide tile amortises those operations over more pairs.  A tcgen05.ld.red per
-// 64 columns returns a chunk minimum directly.  Each CTA has one 256-column
-// accumulator; the two CTAs of an SM (256 TMEM columns each) take turns on the
-// tensor pipe, and overlap one another's per-item prologue and exact stage.
-// Every wait is bounded: on expiry the kernel reports ASICP_ERR_TIMEOUT through
-// the error word, drains its own copies and MMAs (bounded), frees its tensor
-// memory and returns.
+// wide tile with a single MMA and a single commit amortises those operations
+// over more pairs.  A tcgen05.ld.red per 64 columns returns a chunk minimum
+// directly.  Each CTA has one 256-column accumulator; the two CTAs of an SM (256
+// TMEM columns each) take turns on the tensor pipe, and overlap one another's
+// per-item prologue and exact stage.  Every wait is bounded: on expiry the kernel
+// reports ASICP_ERR_TIMEOUT through the error word, drains its own copies and
+// MMAs (bounded), frees its tensor memory and returns.
 #include "asicp_internal.cuh"
 #include "async_copy.cuh"
 
 #include <cstdint>
+#include <cuda_fp16.h>
 
 namespace asicp {
 
@@ -53,14 +60,14 @@ constexpr int kQueries = kRows * kBlocks;  // queries per item = reduction threa
 constexpr int kThreadsTc = kQueries + 64;  // + one warp for the copies, one for the MMAs
 constexpr int kCols = 256;                 // object points per tile = MMA N
 constexpr int kBufs = 1;                   // accumulators per query block (a power of two)
-constexpr int kAug = 16;                   // augmented length (two K = 8 MMAs)
-constexpr int kStages = 5;                 // object tiles in flight
+constexpr int kAug = 16;                   // augmented length (one K = 16 MMA)
+constexpr int kStages = 10;                // object tiles in flight
 constexpr int kChunk = 64;                 // screening chunk = columns per tcgen05.ld.red
 constexpr int kTop = 4;                    // chunks per query the exact stage rescans at most
-constexpr unsigned kTileBytes = kCols * kAug * 4;       // 16 KB
-constexpr unsigned kABlockBytes = kRows * kAug * 4;     // 8 KB
+constexpr unsigned kTileBytes = kCols * kAug * 2;       // 8 KB
+constexpr unsigned kABlockBytes = kRows * kAug * 2;     // 4 KB
 constexpr unsigned kABytes = kBlocks * kABlockBytes;
-constexpr unsigned kLBO = 128, kSBO = 512; // core matrices (8 rows x 16 B): K-adjacent 128 B, row groups 512 B
+constexpr unsigned kLBO = 128, kSBO = 256; // core matrices (8 rows x 16 B): K-adjacent 128 B, row groups 256 B
 constexpr int kTmemCols = kBlocks * kBufs * kCols;      // kBufs accumulators per block
 constexpr size_t kSmemBytes = kABytes + (size_t)kStages * kTileBytes;
 static_assert(kRefTilePts % kCols == 0, "object padding must be whole tiles");
@@ -68,14 +75,14 @@ static_assert(kTmemCols == 256, "two CTAs per SM share the 512 tensor-memory col
 static_assert(kCols % kChunk == 0, "whole chunks per tile");
 static_assert((kBufs & (kBufs - 1)) == 0, "accumulator count");
 
-// instruction descriptor: D f32, A and B tf32, both K-major, N = kCols, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kCols >> 3) << 17) |
+// instruction descriptor: D f32, A and B f16, both K-major, N = kCols, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(kCols >> 3) << 17) |
                             ((uint32_t)(kRows >> 4) << 24);
 
 // byte offset of element (row, k) in the no-swizzle K-major layout
 __host__ __device__ constexpr unsigned core_offset(int row, int k)
 {
-    return (unsigned)(row / 8) * kSBO + (unsigned)(k / 4) * kLBO + (unsigned)(row % 8) * 16u + (unsigned)(k % 4) * 4u;
+    return (unsigned)(row / 8) * kSBO + (unsigned)(k / 8) * kLBO + (unsigned)(row % 8) * 16u + (unsigned)(k % 8) * 2u;
 }
 
 __device__ __forceinline__ uint64_t smem_desc(unsigned addr)
@@ -84,19 +91,22 @@ __device__ __forceinline__ uint64_t smem_desc(unsigned addr)
            (1ull << 46);
 }
 
-// round to the nearest TF32 value (ties to even); finite inputs of moderate size
-__device__ __forceinline__ float tf32_rn(float x)
+// Power-of-two scale lam with lam Rmax in (128, 256] (Rmax clamped below at 2^-30),
+// so that scaled coordinates and |r|^2 / 4 fit the f16 range.
+__device__ __forceinline__ float tc_scale(float rmax)
 {
-    const unsigned u = __float_as_uint(x);
-    return __uint_as_float((u + 0x0FFFu + ((u >> 13) & 1u)) & 0xFFFFE000u);
+    int ex;
+    frexpf(fmaxf(rmax, 9.3132257e-10f), &ex);
+    return ldexpf(1.f, 8 - ex);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t ad, uint64_t bd, uint32_t accumulate)
+// One K = 16 MMA into a fresh accumulator.
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t ad, uint64_t bd)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(ad), "l"(bd), "r"(kIdesc), "r"(accumulate)
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(ad), "l"(bd), "r"(kIdesc), "r"(0u)
         : "memory");
 }
 
@@ -145,35 +155,41 @@ __device__ __forceinline__ void exact_chunk_tie(const float4 *__restrict__ R, in
 }  // namespace
 
 // Augmented object tiles for the tensor-core kernel: point r goes to tile
-// r / 128, row r % 128 of that tile's MMA layout; padding points (r >= M) get
-// r = 0 and |r|^2 = 1e30, so they never screen in.
-__global__ void tc_ref_prep_kernel(const float4 *R, int M, int Mpad, float *Rt)
+// r / kCols, row r % kCols of that tile's MMA layout, as f16 parts of lam r and
+// lam^2 |r|^2 / 4 (lam from the object's Rmax); padding points (r >= M) carry
+// only 2^15 in slot 12, which meets 2^15 in every query row: + 2^30, so they never
+// screen in.
+__global__ void tc_ref_prep_kernel(const float4 *R, int M, int Mpad, const float *rmax, __half *Rt)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= Mpad) return;
-    float x = 0.f, y = 0.f, z = 0.f, w = 1e30f;
+    const float lam = tc_scale(*rmax);
+    __half v[kAug];
+    for (int k = 0; k < kAug; ++k) v[k] = __float2half_rn(0.f);
     if (r < M) {
         const float4 p = R[r];
-        x = p.x; y = p.y; z = p.z;
-        w = (float)((double)x * x + (double)y * y + (double)z * z);
+        const float c[3] = {lam * p.x, lam * p.y, lam * p.z};
+        for (int k = 0; k < 3; ++k) {
+            const __half h = __float2half_rn(c[k]);
+            const __half l = __float2half_rn(c[k] - __half2float(h));
+            v[k] = h; v[3 + k] = l; v[6 + k] = h;
+        }
+        // w = fl(lam^2 |r|^2) / 4, split into three f16 parts (exact to 2^-33 relative)
+        const double w = (double)(float)((double)c[0] * c[0] + (double)c[1] * c[1] + (double)c[2] * c[2]) * 0.25;
+        const __half w1 = __float2half_rn((float)w);
+        const __half w2 = __float2half_rn((float)(w - (double)__half2float(w1)));
+        const __half w3 = __float2half_rn((float)(w - (double)__half2float(w1) - (double)__half2float(w2)));
+        v[9] = w1; v[10] = w2; v[11] = w3;
+    } else {
+        v[12] = __float2half_rn(32768.f);
     }
-    const float c[3] = {x, y, z};
-    float v[kAug];
-    for (int k = 0; k < 3; ++k) {
-        const float h = tf32_rn(c[k]);
-        const float l = tf32_rn(c[k] - h);
-        v[k] = h; v[3 + k] = l; v[6 + k] = h;
-    }
-    const float w1 = tf32_rn(w), w2 = tf32_rn(w - w1);
-    v[9] = w1; v[10] = w2; v[11] = (w - w1) - w2;
-    v[12] = v[13] = v[14] = v[15] = 0.f;
     unsigned char *tile = reinterpret_cast<unsigned char *>(Rt) + (size_t)(r / kCols) * kTileBytes;
-    for (int k = 0; k < kAug; ++k) *reinterpret_cast<float *>(tile + core_offset(r % kCols, k)) = v[k];
+    for (int k = 0; k < kAug; ++k) *reinterpret_cast<__half *>(tile + core_offset(r % kCols, k)) = v[k];
 }
 
-cudaError_t launch_tc_ref_prep(const float4 *R, int M, int Mpad, float *Rt, cudaStream_t st)
+cudaError_t launch_tc_ref_prep(const float4 *R, int M, int Mpad, const float *rmax, void *Rt, cudaStream_t st)
 {
-    tc_ref_prep_kernel<<<(Mpad + 255) / 256, 256, 0, st>>>(R, M, Mpad, Rt);
+    tc_ref_prep_kernel<<<(Mpad + 255) / 256, 256, 0, st>>>(R, M, Mpad, rmax, static_cast<__half *>(Rt));
     return cudaGetLastError();
 }
 
@@ -185,8 +201,8 @@ size_t tc_ref_bytes(int Mpad) { return (size_t)Mpad / kCols * kTileBytes; }
 // lane 0 of warp 4 streams the object tiles, lane 0 of warp 5 issues the MMAs.  They meet on
 // mbarriers only (no CTA-wide barrier inside the loop):
 //   bfull[s]  tile in stage s has landed          (copy -> MMA)
-//   bempty[s] the MMAs reading stage s are done    (MMA commit -> copy)
-//   accf[b]   accumulator b holds a finished tile  (MMA commit -> reduction)
+//   bempty[s] the MMA reading stage s is done:     (MMA commit -> copy, and -> reduction:
+//             the accumulator holds that tile     its next phase needs the reduction's acce)
 //   acce[b]   accumulator b has been read          (reduction -> MMA, 128 arrivals)
 //   afull     the item's query rows are written    (reduction warps -> MMA, 128 arrivals)
 __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdArgs a)
@@ -194,7 +210,7 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     unsigned char *sA = smem_tc;
     unsigned char *sB = smem_tc + kABytes;
-    __shared__ __align__(8) unsigned long long bfull[kStages], bempty[kStages], accf[kBufs], acce[kBufs], afull;
+    __shared__ __align__(8) unsigned long long bfull[kStages], bempty[kStages], acce[kBufs], afull;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -222,7 +238,7 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
     if (tid == 0) {
         s_abort = 0;
         for (int s = 0; s < kStages; ++s) { mbar_init(&bfull[s], 1); mbar_init(&bempty[s], 1); }
-        for (int b = 0; b < kBufs; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], kQueries); }
+        for (int b = 0; b < kBufs; ++b) mbar_init(&acce[b], kQueries);
         mbar_init(&afull, kQueries);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -270,8 +286,8 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
         if (lane == 0) {
             // tiles consumed so far, their stage and the parity of the ring's lap (kept
             // incrementally: no division on this thread's path)
-            int seq = 0, c_stage = 0;
-            unsigned c_lap = 0u;
+            int seq = 0, c_stage = 0, last_stage = -1;
+            unsigned c_lap = 0u, last_lap = 0u;
             int ia = 0;
             for (int it = it0; it < it1 && !s_abort; it += step, ++ia) {
                 const int ntiles = a.L.obj[item_at(it).obj].Mpad / kCols;
@@ -290,23 +306,26 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
                     for (int blk = 0; blk < kBlocks; ++blk) {
                         const uint32_t d = tmem + (uint32_t)(blk * kBufs + buf) * kCols;
                         const unsigned a0 = smem_u32(sA + blk * kABlockBytes);
-                        mma_tf32(d, smem_desc(a0), smem_desc(b0), 0u);
-                        mma_tf32(d, smem_desc(a0 + 256), smem_desc(b0 + 256), 1u);
+                        mma_f16(d, smem_desc(a0), smem_desc(b0));
                     }
+                    // one commit per tile: its completion frees the stage for the copy thread and
+                    // hands the accumulator to the reduction warps
                     mma_commit(&bempty[stage]);
-                    mma_commit(&accf[buf]);
+                    last_stage = stage;
+                    last_lap = c_lap;
                     if (++c_stage == kStages) { c_stage = 0; c_lap ^= 1u; }
                 }
             }
             // drain (bounded): the MMAs issued
-            if (s_abort && seq > 0)
-                mbar_wait(&accf[(unsigned)(seq - 1) % kBufs], ((unsigned)(seq - 1) / kBufs) & 1u);
+            if (s_abort && last_stage >= 0) mbar_wait(&bempty[last_stage], last_lap);
         }
     } else {
         // ------------------------------------------------ query rows, reduction, exact choice
         const int blk = warp / 4, row = tid % kRows;      // query block; row = TMEM lane
         const uint32_t lane_base = (uint32_t)((warp % 4) * 32) << 16;
         long long seq = 0;
+        int r_stage = 0;          // stage and lap of the next tile, as on the MMA thread
+        unsigned r_lap = 0u;
         for (int it = it0; it < it1; it += step) {
             if (__any_sync(0xffffffffu, s_abort)) break;
             const FwdItem item = item_at(it);
@@ -316,6 +335,7 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
             const bool valid = tid < item.nq;
             const long long g = item.q0 + tid;
             float3 o = make_float3(0.f, 0.f, 0.f);
+            bool far = false;
             if (valid) {
                 const int pk = (int)(g / a.L.N), i = (int)(g - (long long)pk * a.L.N);
                 const int pre = a.L.part_grp[pk] % a.L.P;
@@ -326,23 +346,38 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
                 o = xform_f32(Rm, th[0], th[1], th[2], s.x, s.y, s.z);
             }
             {
-                // the previous item's MMAs are complete (its last accumulator was waited for)
-                const float c[3] = {-2.f * o.x, -2.f * o.y, -2.f * o.z};
-                float v[kAug];
-                for (int k = 0; k < 3; ++k) {
-                    const float h = tf32_rn(c[k]);
-                    v[k] = h; v[3 + k] = h; v[6 + k] = tf32_rn(c[k] - h);
+                // the previous item's MMAs are complete (its last accumulator was waited for);
+                // a = -2 lam s' in two f16 parts, unless a part would leave the f16 range (such
+                // a query takes the whole-cloud scan)
+                const float lam = tc_scale(rmax);
+                const float c[3] = {-2.f * lam * o.x, -2.f * lam * o.y, -2.f * lam * o.z};
+                far = !(fabsf(c[0]) < 65000.f && fabsf(c[1]) < 65000.f && fabsf(c[2]) < 65000.f);
+                __half v[kAug];
+                for (int k = 0; k < kAug; ++k) v[k] = __float2half_rn(0.f);
+                if (!far) {
+                    for (int k = 0; k < 3; ++k) {
+                        const __half h = __float2half_rn(c[k]);
+                        v[k] = h; v[3 + k] = h; v[6 + k] = __float2half_rn(c[k] - __half2float(h));
+                    }
                 }
-                v[9] = v[10] = v[11] = 1.f;
-                v[12] = v[13] = v[14] = v[15] = 0.f;
-                for (int j = 0; j < kAug / 4; ++j)
-                    *reinterpret_cast<float4 *>(sA + blk * kABlockBytes + core_offset(row, 4 * j)) =
-                        make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                v[9] = v[10] = v[11] = __float2half_rn(4.f);
+                v[12] = __float2half_rn(32768.f);
+                for (int j = 0; j < kAug / 8; ++j) {
+                    uint4 pk;
+                    pk.x = (uint32_t)__half_as_ushort(v[8 * j + 0]) | ((uint32_t)__half_as_ushort(v[8 * j + 1]) << 16);
+                    pk.y = (uint32_t)__half_as_ushort(v[8 * j + 2]) | ((uint32_t)__half_as_ushort(v[8 * j + 3]) << 16);
+                    pk.z = (uint32_t)__half_as_ushort(v[8 * j + 4]) | ((uint32_t)__half_as_ushort(v[8 * j + 5]) << 16);
+                    pk.w = (uint32_t)__half_as_ushort(v[8 * j + 6]) | ((uint32_t)__half_as_ushort(v[8 * j + 7]) << 16);
+                    *reinterpret_cast<uint4 *>(sA + blk * kABlockBytes + core_offset(row, 8 * j)) = pk;
+                }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(&afull);
             }
             const float sn = sqrtf(o.x * o.x + o.y * o.y + o.z * o.z) * 1.001f;
-            const float win = 2.02f * 5.9604645e-8f * (18.f * rmax * rmax + 57.f * sn * rmax);
+            const float lam = tc_scale(rmax);
+            // 2 delta_tc in lam^2 units (1 % margin for evaluating the bound in float32)
+            const float win = 2.02f * (5.9604645e-8f * lam * lam * (18.f * rmax * rmax + 57.f * sn * rmax) +
+                                       6.1035156e-5f * 1.74f * lam * (2.f * sn + rmax) + 2.45e-4f);
             // the kTop best chunk minima (ascending) with their chunk ids, and the best of the rest
             float bk[kTop], brest = __int_as_float(0x7f800000);
             int ck[kTop];
@@ -351,7 +386,9 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
             bool good = true;
             for (int t = 0; t < ntiles; ++t, ++seq) {
                 const int buf = (int)((unsigned long long)seq % kBufs);
-                good = mbar_wait_warp(&accf[buf], (unsigned)(((unsigned long long)seq / kBufs) & 1u));
+                // the tile's MMA is complete once its stage barrier has flipped
+                good = mbar_wait_warp(&bempty[r_stage], r_lap);
+                if (++r_stage == kStages) { r_stage = 0; r_lap ^= 1u; }
                 if (!__all_sync(0xffffffffu, good && !s_abort)) { good = false; break; }
                 tc_fence_after();
                 float mv[kCols / kChunk];
@@ -384,7 +421,7 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
             // chunks per query by its own thread, or, when more qualify, the whole cloud
             // by the warp together (one such query at a time)
             const float thr = bk[0] + win;
-            const bool whole = valid && brest <= thr;
+            const bool whole = valid && (brest <= thr || far);
             float best = __int_as_float(0x7f800000);
             int bi = 0x7fffffff;
             if (valid && !whole) {

@@ -477,7 +477,7 @@ def test_tensor_core_matching_equals_float32_matching(stream):
     w = synth.custom_case(P=3, K=64, N=2048, M=8192, grid=32, k_max=2, seed=synth.BASE_SEED + 2)
     import oracle
     com = w.objects[0].points.astype(np.float64).mean(0)
-    tc = asicp.FWD_VARIANTS.index("tc-tf32x3-m128-n256")
+    tc = asicp.FWD_VARIANTS.index("tc-f16x3-m128-n256")
     for radius in (0.15, 0.03):          # far from the object, and fingers in contact
         th = np.tile(oracle.fibonacci_init(w.K, com, radius), (3, 1)).astype(np.float32)
         a = _step_indices(w, stream, th, 0)
@@ -636,7 +636,7 @@ def test_largest_workload_sampled_steps_and_tensor_core_agreement(stream):
     com = w.objects[0].points.astype(np.float64).mean(0)
     th = np.tile(oracle.fibonacci_init(w.K, com, 0.15), (3, 1)).astype(np.float32)
     a = _step_indices(w, stream, th, 0)
-    b = _step_indices(w, stream, th, asicp.FWD_VARIANTS.index("tc-tf32x3-m128-n256"))
+    b = _step_indices(w, stream, th, asicp.FWD_VARIANTS.index("tc-f16x3-m128-n256"))
     diff = np.nonzero(a["nn_idx"] != b["nn_idx"])
     n_diff = len(diff[0])
     print(f"tensor-core vs float32: {n_diff} of {a['nn_idx'].size} indices differ")
