@@ -109,7 +109,7 @@ struct asicp_ctx {
     std::vector<ObjMeta> objmeta_h;
 
     DevMem partgrp, grpoff, objmeta, items, ctaoff, com, rmax, colitems, collist, box, stage, S, pconst, dmeta, theta, fsums,
-        csums, ncol, colidx, cost, grad, prev, frozen, phi, h, order, errw, out7, outc, outi, nnidx, dbg_d2, dbg_sp,
+        csums, ncol, colidx, cost, grad, prev, frozen, phi, h, order, errw, out7, outc, outi, nnidx, tccand, dbg_d2, dbg_sp,
         dbg_colnn;
 
     // profiling: events recorded around launches (kind, start, stop)
@@ -326,6 +326,7 @@ void build_layout(asicp_ctx *c)
     c->colitems.ensure(sizeof(int) * 2, "collision work counters");
     c->collist.ensure(sizeof(int) * 2 * std::max<long long>(1, csum_total), "collision work list");
     c->nnidx.ensure(sizeof(int) * (size_t)T * N, "nn_idx");
+    c->tccand.ensure(sizeof(int4) * (size_t)T * N, "tensor-core candidate chunks");
     c->ncol.ensure(sizeof(int) * T, "ncol");
     c->colidx.ensure(sizeof(int) * std::max<long long>(1, colidx_total), "colidx");
     c->cost.ensure(sizeof(double) * T, "cost");
@@ -444,6 +445,7 @@ void iterate(asicp_ctx *c, int mode, float gamma, int k)
     fa.n_items = c->n_items;
     fa.err = c->errw.as<int>();
     fa.nn_idx = c->nnidx.as<int>();
+    fa.cand = c->tccand.as<int4>();
     fa.variant = c->fwd_variant;
     if (c->cfg.debug) {
         fa.dbg_d2 = c->dbg_d2.as<float>();
@@ -527,7 +529,7 @@ std::vector<const void *> loop_key(const asicp_ctx *c)
 {
     return {c->partgrp.p, c->grpoff.p, c->objmeta.p, c->items.p, c->ctaoff.p, c->com.p, c->rmax.p, c->colitems.p, c->collist.p,
             c->S.p, c->pconst.p, c->dmeta.p, c->theta.p, c->fsums.p, c->csums.p, c->ncol.p, c->colidx.p, c->cost.p,
-            c->grad.p, c->prev.p, c->frozen.p, c->phi.p, c->h.p, c->order.p, c->errw.p, c->nnidx.p, c->dbg_d2.p,
+            c->grad.p, c->prev.p, c->frozen.p, c->phi.p, c->h.p, c->order.p, c->errw.p, c->nnidx.p, c->tccand.p, c->dbg_d2.p,
             c->dbg_sp.p, c->dbg_colnn.p, c->mb_idx.p, c->mb_R.p, c->mb_Rx.p,
             reinterpret_cast<const void *>((size_t)c->mb_version), reinterpret_cast<const void *>((size_t)c->T),
             reinterpret_cast<const void *>((size_t)c->G), reinterpret_cast<const void *>((size_t)c->n_items),
@@ -626,6 +628,7 @@ void autotune_impl(asicp_ctx *c, float *ms_out)
         fa.n_items = c->n_items;
         fa.err = c->errw.as<int>();
         fa.nn_idx = c->nnidx.as<int>();
+        fa.cand = c->tccand.as<int4>();
         fa.variant = v;
         ck(launch_fwd_match(fa, c->st), "autotune warm-up");
         ck(cudaEventRecord(e0, c->st), "cudaEventRecord");

@@ -210,6 +210,7 @@ struct FwdArgs {
     int *nn_idx;             // [T][N] nearest object point per query
     float *dbg_d2;           // [T][N] or null
     float *dbg_sp;           // [T][N][3] or null
+    int4 *cand;              // [T][N] tensor-core shape only: candidate chunks per query
     int variant;             // kernel shape (0 .. kFwdVariants - 1), chosen by the autotuner
 };
 constexpr int kFwdItemQueries = 1024;  // queries per forward-matching work item

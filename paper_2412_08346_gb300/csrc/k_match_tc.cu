@@ -26,10 +26,10 @@
 // would leave the f16 range takes the whole-cloud scan.  Each query keeps its kTop
 // best chunk minima (chunks of 64 object points) and the best of the rest; the
 // chunks within 2 delta_tc of the best are rescanned with the exact-form float32
-// distance (ties to the lower index) by the query's thread, or, when more than
-// kTop qualify, the warp scans the whole cloud for that query together.  The
-// result is the exact-form argmin over every point that can be nearest, as in
-// the float32 kernel.
+// distance (ties to the lower index) by tc_exact_kernel, one thread per query, or,
+// when more than kTop qualify, by a warp scanning the whole cloud for that query
+// together.  The result is the exact-form argmin over every point that can be
+// nearest, as in the float32 kernel.
 //
 // Per CTA: one block of 128 queries (one per reduction thread, TMEM lane =
 // query); object tiles of 256 points (8 KB, already in the MMA's shared-memory
@@ -41,7 +41,7 @@
 // over more pairs.  A tcgen05.ld.red per 64 columns returns a chunk minimum
 // directly.  Each CTA has one 256-column accumulator; the two CTAs of an SM (256
 // TMEM columns each) take turns on the tensor pipe, and overlap one another's
-// per-item prologue and exact stage.  Every wait is bounded: on expiry the kernel
+// per-item prologue.  Every wait is bounded: on expiry the kernel
 // reports ASICP_ERR_TIMEOUT through the error word, drains its own copies and
 // MMAs (bounded), frees its tensor memory and returns.
 #include "asicp_internal.cuh"
@@ -417,38 +417,20 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
             }
             if (!good) { fail(); break; }
 
-            // exact choice among the chunks that can hold the nearest point: up to kTop
-            // chunks per query by its own thread, or, when more qualify, the whole cloud
-            // by the warp together (one such query at a time)
+            // the chunks that can hold the nearest point (within 2 delta_tc of the best), or
+            // the whole cloud when more than kTop qualify; tc_exact_kernel rescans them
             const float thr = bk[0] + win;
-            const bool whole = valid && (brest <= thr || far);
-            float best = __int_as_float(0x7f800000);
-            int bi = 0x7fffffff;
-            if (valid && !whole) {
-#pragma unroll
-                for (int k = 0; k < kTop; ++k)
-                    if (bk[k] <= thr)
-                        exact_chunk_tie(om.R, ck[k] * kChunk, om.M, o, best, bi);
-            }
-            unsigned pending = __ballot_sync(0xffffffffu, whole);
-            while (pending) {
-                const int src = __ffs(pending) - 1;
-                pending &= pending - 1;
-                float wb;
-                int wi;
-                warp_exact_all(om.R, om.M, __shfl_sync(0xffffffffu, o.x, src), __shfl_sync(0xffffffffu, o.y, src),
-                               __shfl_sync(0xffffffffu, o.z, src), wb, wi);
-                if (lane == src) { best = wb; bi = wi; }
-            }
             if (valid) {
-                if (bi >= om.M) bi = 0;    // no finite distance at all (not reached with finite inputs)
-                a.nn_idx[g] = bi;
-                if (a.dbg_d2) a.dbg_d2[g] = best;
-                if (a.dbg_sp) {
-                    a.dbg_sp[g * 3 + 0] = o.x;
-                    a.dbg_sp[g * 3 + 1] = o.y;
-                    a.dbg_sp[g * 3 + 2] = o.z;
+                int4 cd;
+                if (brest <= thr || far) {
+                    cd = make_int4(-2, -1, -1, -1);
+                } else {
+                    cd.x = ck[0];
+                    cd.y = bk[1] <= thr ? ck[1] : -1;
+                    cd.z = bk[2] <= thr ? ck[2] : -1;
+                    cd.w = bk[3] <= thr ? ck[3] : -1;
                 }
+                a.cand[g] = cd;
             }
         }
     }
@@ -458,6 +440,101 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+// Exact choice after the tensor-core screening.  Each warp takes 32 consecutive
+// queries and rescans their candidate chunks one query at a time, all lanes
+// together: lane l reads points l and l + 32 of a chunk (coalesced), and two
+// warp-wide integer minimum reductions give the smallest exact-form float32
+// distance (its bits order as unsigned integers, distances being non-negative) and
+// then the lowest index holding it.  A query marked for the whole cloud is scanned
+// the same way over all M points.  Separate from the screening kernel so that
+// these loads do not stall the tensor pipe between work items.  The transformed
+// point is recomputed with the same float32 operations as in the screening
+// kernel, so it is the same value.
+__device__ __forceinline__ unsigned dist_key(float d)
+{
+    return d <= 3.4028235e38f ? __float_as_uint(d) : 0x7f800000u;   // NaN -> +inf
+}
+
+// Merge this lane's (key, index) into the warp's running best (wk, wi), ties to
+// the lower index; every lane ends with the same (wk, wi).
+__device__ __forceinline__ void warp_merge_min(unsigned key, int idx, unsigned &wk, int &wi)
+{
+    const unsigned m = __reduce_min_sync(0xffffffffu, key);
+    const int mi = (int)__reduce_min_sync(0xffffffffu, key == m ? (unsigned)idx : 0x7fffffffu);
+    if (m < wk || (m == wk && mi < wi)) { wk = m; wi = mi; }
+}
+
+__global__ void __launch_bounds__(256) tc_exact_kernel(const FwdArgs a)
+{
+    const long long Qtot = (long long)a.L.T * a.L.N;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = g < Qtot;
+    const int lane = threadIdx.x & 31;
+    float3 o = make_float3(0.f, 0.f, 0.f);
+    int obj = 0;
+    int4 cd = make_int4(-1, -1, -1, -1);
+    if (valid) {
+        const int pk = (int)(g / a.L.N), i = (int)(g - (long long)pk * a.L.N);
+        const int grp = a.L.part_grp[pk];
+        obj = grp / a.L.P;
+        const float *th = a.theta + (size_t)pk * 8;
+        float Rm[9];
+        quat_rot_f32(th[3], th[4], th[5], th[6], Rm);
+        const float4 s = a.S[(size_t)(grp % a.L.P) * a.L.N + i];
+        o = xform_f32(Rm, th[0], th[1], th[2], s.x, s.y, s.z);
+        cd = a.cand[g];
+    }
+    unsigned my_key = 0x7f800000u;
+    int my_idx = 0x7fffffff;
+    unsigned todo = __ballot_sync(0xffffffffu, valid);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const float qx = __shfl_sync(0xffffffffu, o.x, src), qy = __shfl_sync(0xffffffffu, o.y, src),
+                    qz = __shfl_sync(0xffffffffu, o.z, src);
+        const int wo = __shfl_sync(0xffffffffu, obj, src);
+        const int c[4] = {__shfl_sync(0xffffffffu, cd.x, src), __shfl_sync(0xffffffffu, cd.y, src),
+                          __shfl_sync(0xffffffffu, cd.z, src), __shfl_sync(0xffffffffu, cd.w, src)};
+        const float4 *R = a.L.obj[wo].R;
+        const int M = a.L.obj[wo].M;
+        unsigned wk = 0x7f800000u;
+        int wi = 0x7fffffff;
+        if (c[0] == -2) {
+            unsigned k = 0x7f800000u;
+            int ki = 0x7fffffff;
+            for (int r = lane; r < M; r += 32) {
+                const float4 v = __ldg(R + r);
+                const unsigned dk = dist_key(dist2_f32(qx, qy, qz, v.x, v.y, v.z));
+                if (dk < k) { k = dk; ki = r; }
+            }
+            warp_merge_min(k, ki, wk, wi);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (c[j] < 0) continue;
+                const int r0 = c[j] * kChunk + lane, r1 = r0 + 32;
+                const float4 v0 = __ldg(R + min(r0, M - 1)), v1 = __ldg(R + min(r1, M - 1));
+                unsigned k0 = r0 < M ? dist_key(dist2_f32(qx, qy, qz, v0.x, v0.y, v0.z)) : 0x7f800000u;
+                const unsigned k1 = r1 < M ? dist_key(dist2_f32(qx, qy, qz, v1.x, v1.y, v1.z)) : 0x7f800000u;
+                int ki = r0;
+                if (k1 < k0) { k0 = k1; ki = r1; }
+                warp_merge_min(k0, ki, wk, wi);
+            }
+        }
+        if (lane == src) { my_key = wk; my_idx = wk < 0x7f800000u ? wi : 0x7fffffff; }
+    }
+    if (!valid) return;
+    const int M = a.L.obj[obj].M;
+    const int bi = my_idx < M ? my_idx : 0;    // no finite distance at all (not reached with finite inputs)
+    a.nn_idx[g] = bi;
+    if (a.dbg_d2) a.dbg_d2[g] = __uint_as_float(my_key);
+    if (a.dbg_sp) {
+        a.dbg_sp[g * 3 + 0] = o.x;
+        a.dbg_sp[g * 3 + 1] = o.y;
+        a.dbg_sp[g * 3 + 2] = o.z;
     }
 }
 
@@ -483,6 +560,10 @@ int fwd_tc_threads() { return kQueries; }
 cudaError_t launch_fwd_match_tc(const FwdArgs &a, cudaStream_t st)
 {
     fwd_match_tc_kernel<<<fwd_tc_grid(), kThreadsTc, kSmemBytes, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long Qtot = (long long)a.L.T * a.L.N;
+    tc_exact_kernel<<<(unsigned)((Qtot + 255) / 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
