@@ -37,11 +37,16 @@ sys.path.insert(0, ROOT)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
-# DRAM bytes (read + write) of one forward-matching launch from the committed ncu capture
-# (profiles/fwd_match_kernel_profile-case-P1-K256-N2048-M8192.md); null once the kernel changes
-FWD_DRAM_BYTES_PER_LAUNCH = None
+# DRAM bytes (read + write) of one launch of each forward-matching kernel from the committed ncu
+# captures of the profile case (profiles/fwd_match_kernel_profile-case-P1-K256-N2048-M8192.md,
+# profiles/fwd_match_tc_kernel_profile-case-P1-K256-N2048-M8192.md); every input is L2-resident, so
+# the figure holds for the paper-scale launch too.  Set to None when the kernel changes.
+FWD_DRAM_BYTES_PER_LAUNCH = 397568        # fwd_match_kernel (float32 shapes)
+TC_DRAM_BYTES_PER_LAUNCH = 393216         # fwd_match_tc_kernel (tensor-core shape)
 OPS_PER_PAIR = 4          # algorithmic FP32-lane work per particle*point pair: 3 FMA + 1 compare
 FMA_PER_PAIR = 3          # of which FMA-pipe work (the compare runs as half a 3-input min on the ALU pipe)
+TC_FLOP_PER_PAIR = 32     # tensor-core shape: one M=128 x N=256 x K=16 f16 MMA per 128 x 256 pairs (2 flop per MAC)
+TC_SHAPE = "tc-f16x3-m128-n256"
 TOPK = 16
 METRIC = "AS-ICP particle*point pairs/s (forward matching) and ms per grasp set"
 
@@ -264,13 +269,18 @@ def run_gpu(args, rank, world, local_rank):
     value = pairs * args.steps * world / (max_ms / 1e3)
 
     # dominant kernel: forward matching; algorithmic work per launch = P*K*N*M pairs
+    tc = asicp.FWD_VARIANTS[shape] == TC_SHAPE
     match_avg_s = ms[0] / max(1, launches[0]) / 1e3
+    exact_avg_s = ms[5] / max(1, launches[5]) / 1e3 if tc else 0.0
     pairs_per_launch = P * K * N * M
-    achieved = pairs_per_launch / match_avg_s / 1e9
-    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / OPS_PER_PAIR / 1e9
+    pairs_rate = pairs_per_launch / (match_avg_s + exact_avg_s) / 1e9      # whole matching stage
+    peak_alu = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / OPS_PER_PAIR / 1e9
     peak_fma = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / FMA_PER_PAIR / 1e9
-    # match, collide, collide_nn, finalize per pass, Stein per SVGD pass, + init, reset, select, gather
-    launches_per_step = 4 * (w.k_max + 1) + w.k_stein + 4
+    roofline = roofline_entry(tc, pairs_per_launch, match_avg_s, exact_avg_s, pairs_rate, peak_alu, peak_fma,
+                              ms, launches)
+    # match, collide, collide_nn, finalize per pass (+ the exact choice with the tensor-core shape),
+    # Stein per SVGD pass, + init, reset, select, gather
+    launches_per_step = (5 if tc else 4) * (w.k_max + 1) + w.k_stein + 4
 
     e2e = None
     if not args.no_e2e:
@@ -298,17 +308,7 @@ def run_gpu(args, rank, world, local_rank):
                        "parallelism": f"replicas x{world} (one object per GPU)",
                        "fwd_shape": asicp.FWD_VARIANTS[shape]},
             "ms_per_grasp_set": max_ms / args.steps,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpairs/s",
-                         "frac": achieved / peak, "traffic": FWD_DRAM_BYTES_PER_LAUNCH,
-                         "traffic_basis": "dram__bytes_read+write of one fwd_match_kernel launch (ncu, shape "
-                                          "qpt8-chunk64-t128-tile1024); every input is L2-resident, so it does not "
-                                          "grow with the launch",
-                         "kernel": "fwd_match_kernel", "peak_basis":
-                             f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz / "
-                             f"{OPS_PER_PAIR} lane operations per pair (3 FMA + 1 compare)",
-                         "frac_fma_pipe": achieved / peak_fma, "peak_fma_pipe": peak_fma,
-                         "launch_ms": match_avg_s * 1e3,
-                         "kernel_share": ms[0] / max(1e-9, sum(ms))},
+            "roofline": roofline,
             "kernel_ms_per_step": {k: v / args.steps for k, v in zip(asicp.KERNEL_KINDS, ms)},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
@@ -318,6 +318,48 @@ def run_gpu(args, rank, world, local_rank):
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
+
+
+def roofline_entry(tc, pairs_per_launch, match_avg_s, exact_avg_s, pairs_rate, peak_alu, peak_fma, ms, launches):
+    """Roofline of the dominant kernel.  Tensor-core shape: executed MMA flops of fwd_match_tc_kernel
+    against the measured dense bf16 peak (f16 has the same nominal rate); float32 shapes: pairs/s of
+    fwd_match_kernel against the FP32-lane rate at the nominal maximum clock."""
+    share = ms[0] / max(1e-9, sum(ms))
+    if tc:
+        peaks = measured_peaks()
+        peak = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops") or 1700.0
+        basis = ("MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16 loop under the power cap; f16 and bf16 "
+                 "have the same nominal dense rate)" if peaks else "fallback 1.7 PFLOP/s sustained")
+        achieved = pairs_per_launch * TC_FLOP_PER_PAIR / match_avg_s / 1e12
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": TC_DRAM_BYTES_PER_LAUNCH,
+                "traffic_basis": "dram__bytes_read+write of one fwd_match_tc_kernel launch (ncu); every input is "
+                                 "L2-resident, so it does not grow with the launch",
+                "kernel": "fwd_match_tc_kernel", "peak_basis": basis,
+                "flop_basis": f"{TC_FLOP_PER_PAIR} flop per particle*point pair (split-f16 K=16 contraction)",
+                "launch_ms": match_avg_s * 1e3, "exact_kernel_ms": exact_avg_s * 1e3,
+                "matching_pairs_per_s": pairs_rate * 1e9,
+                "matching_frac_of_fp32_alu_roofline": pairs_rate / peak_alu,
+                "kernel_share": share, "exact_kernel_share": ms[5] / max(1e-9, sum(ms))}
+    achieved = pairs_per_launch / match_avg_s / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "Gpairs/s", "frac": achieved / peak_alu,
+            "traffic": FWD_DRAM_BYTES_PER_LAUNCH,
+            "traffic_basis": "dram__bytes_read+write of one fwd_match_kernel launch (ncu); every input is "
+                             "L2-resident, so it does not grow with the launch",
+            "kernel": "fwd_match_kernel", "peak_basis":
+                f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz / "
+                f"{OPS_PER_PAIR} lane operations per pair (3 FMA + 1 compare)",
+            "frac_fma_pipe": achieved / peak_fma, "peak_fma_pipe": peak_fma,
+            "launch_ms": match_avg_s * 1e3, "kernel_share": share}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def measure_e2e(args, ctx, w, stream, best, best_c, best_p, world, dev):

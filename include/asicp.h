@@ -217,11 +217,15 @@ asicp_status asicp_best_grasps_at(asicp_ctx *ctx, int object, int topk, float *t
 asicp_status asicp_get_state(asicp_ctx *ctx, const asicp_state_view *view);
 
 /* With config.profile = 1: accumulated device time (ms) and launch count of the
- * path's kernels since the last reset.  ms[5] / launches[5] order: forward
- * matching, collision test (with the matching sums), reverse matching, finalize
- * (cost, gradient, convergence, SGD step), Stein (SVGD step).  reset = 1 clears
- * the counters after reading.  Errors: STATE (profile off). */
-asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[5], long long launches[5], int reset);
+ * path's kernels since the last reset.  ms[ASICP_KERNEL_KINDS] / launches[...]
+ * order: forward matching (screening; with the float32 shapes also the exact
+ * choice), collision test (with the matching sums), reverse matching, finalize
+ * (cost, gradient, convergence, SGD step), Stein (SVGD step), and the exact
+ * choice of the tensor-core shape (no launches with the float32 shapes).  reset = 1
+ * clears the counters after reading.  Errors: STATE (profile off). */
+#define ASICP_KERNEL_KINDS 6
+asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[ASICP_KERNEL_KINDS], long long launches[ASICP_KERNEL_KINDS],
+                                int reset);
 
 /* Forward matching without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that must not allocate device memory, such as

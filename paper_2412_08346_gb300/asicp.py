@@ -209,12 +209,12 @@ def asicp_get_state(ctx, **arrays) -> None:
     _check(ctx, load().asicp_get_state(ctx, C.byref(view)))
 
 
-KERNEL_KINDS = ("match", "collide", "collide_nn", "finalize", "stein")
+KERNEL_KINDS = ("match", "collide", "collide_nn", "finalize", "stein", "exact")
 
 
 def asicp_kernel_times(ctx, reset: bool = False):
-    ms = (C.c_double * 5)()
-    n = (C.c_longlong * 5)()
+    ms = (C.c_double * len(KERNEL_KINDS))()
+    n = (C.c_longlong * len(KERNEL_KINDS))()
     _check(ctx, load().asicp_kernel_times(ctx, ms, n, int(reset)))
     return list(ms), list(n)
 

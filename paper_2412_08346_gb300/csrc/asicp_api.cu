@@ -75,7 +75,9 @@ struct ObjBufs {
     bool set = false;
 };
 
-enum { kTimeMatch = 0, kTimeCollide = 1, kTimeCollideNN = 2, kTimeFinalize = 3, kTimeStein = 4, kTimeKinds = 5 };
+enum { kTimeMatch = 0, kTimeCollide = 1, kTimeCollideNN = 2, kTimeFinalize = 3, kTimeStein = 4, kTimeExact = 5,
+       kTimeKinds = 6 };
+static_assert(kTimeKinds == ASICP_KERNEL_KINDS, "kernel kinds");
 
 }  // namespace
 
@@ -116,8 +118,8 @@ struct asicp_ctx {
     struct Ev { int kind; cudaEvent_t a, b; };
     std::vector<Ev> events;
     std::vector<cudaEvent_t> pool;
-    double acc_ms[kTimeKinds] = {0, 0, 0, 0, 0};
-    long long acc_n[kTimeKinds] = {0, 0, 0, 0, 0};
+    double acc_ms[kTimeKinds] = {};
+    long long acc_n[kTimeKinds] = {};
 
     // CUDA graph of asicp_run's iteration loop (captured once per buffer layout)
     cudaStream_t cap_st = nullptr;
@@ -452,6 +454,8 @@ void iterate(asicp_ctx *c, int mode, float gamma, int k)
         fa.dbg_sp = c->dbg_sp.as<float>();
     }
     timed(c, kTimeMatch, [&](cudaStream_t st) { return launch_fwd_match(fa, st); }, "forward matching kernel");
+    if (fwd_has_exact_kernel(fa.variant))
+        timed(c, kTimeExact, [&](cudaStream_t st) { return launch_fwd_exact(fa, st); }, "exact choice kernel");
 
     CollideArgs ca{};
     ca.L = L;
@@ -631,8 +635,12 @@ void autotune_impl(asicp_ctx *c, float *ms_out)
         fa.cand = c->tccand.as<int4>();
         fa.variant = v;
         ck(launch_fwd_match(fa, c->st), "autotune warm-up");
+        if (fwd_has_exact_kernel(v)) ck(launch_fwd_exact(fa, c->st), "autotune warm-up");
         ck(cudaEventRecord(e0, c->st), "cudaEventRecord");
-        for (int r = 0; r < reps; ++r) ck(launch_fwd_match(fa, c->st), "autotune launch");
+        for (int r = 0; r < reps; ++r) {
+            ck(launch_fwd_match(fa, c->st), "autotune launch");
+            if (fwd_has_exact_kernel(v)) ck(launch_fwd_exact(fa, c->st), "autotune launch");
+        }
         ck(cudaEventRecord(e1, c->st), "cudaEventRecord");
         ck(cudaEventSynchronize(e1), "cudaEventSynchronize");
         float t = 0.f;
@@ -1049,7 +1057,8 @@ asicp_status asicp_autotune(asicp_ctx *ctx, int *chosen, float *ms)
     });
 }
 
-asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[5], long long launches[5], int reset)
+asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[ASICP_KERNEL_KINDS], long long launches[ASICP_KERNEL_KINDS],
+                                int reset)
 {
     return guarded(ctx, [&] {
         if (!ctx->cfg.profile) fail(ASICP_ERR_STATE, "kernel_times: config.profile is 0");

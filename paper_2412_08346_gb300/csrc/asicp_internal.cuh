@@ -216,6 +216,10 @@ struct FwdArgs {
 constexpr int kFwdItemQueries = 1024;  // queries per forward-matching work item
 constexpr int kFwdVariants = 8;        // kernel shapes of the forward matching (7: tensor cores)
 cudaError_t launch_fwd_match(const FwdArgs &a, cudaStream_t st);
+// The tensor-core shape leaves the exact choice to a second kernel (launch it after
+// launch_fwd_match on the same stream); the float32 shapes make it themselves.
+inline bool fwd_has_exact_kernel(int v) { return v == kFwdVariants - 1; }
+cudaError_t launch_fwd_exact(const FwdArgs &a, cudaStream_t st);
 int fwd_grid_size();                   // first call sets the kernels' attributes
 int fwd_shape_grid(int v);             // CTAs of kernel shape v (a whole number per SM)
 int fwd_shape_threads(int v);          // threads per CTA of kernel shape v
@@ -227,6 +231,7 @@ cudaError_t launch_ref_prep(const float4 *R, int M, int Mpad, void *Rx, float *r
 cudaError_t launch_tc_ref_prep(const float4 *R, int M, int Mpad, const float *rmax, void *Rt, cudaStream_t st);
 size_t tc_ref_bytes(int Mpad);         // bytes of the tensor-core object tiles
 cudaError_t launch_fwd_match_tc(const FwdArgs &a, cudaStream_t st);
+cudaError_t launch_tc_exact(const FwdArgs &a, cudaStream_t st);
 int fwd_tc_grid();
 int fwd_tc_threads();
 

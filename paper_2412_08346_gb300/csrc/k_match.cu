@@ -311,7 +311,7 @@ auto with_shape(int v, F &&f)
     }
 }
 constexpr int kTcVariant = 7;          // the tensor-core kernel (k_match_tc.cu)
-static_assert(kFwdVariants == 8, "shape table");
+static_assert(kFwdVariants == 8 && kTcVariant == kFwdVariants - 1, "shape table");
 static_assert(Shape0::kItem == kFwdItemQueries, "unplanned launches use shape 0's items");
 
 int fwd_shape_grid(int v)
@@ -352,6 +352,11 @@ cudaError_t launch_fwd_match(const FwdArgs &a, cudaStream_t st)
 {
     if (a.variant == kTcVariant) return launch_fwd_match_tc(a, st);
     return with_shape(a.variant, [&](auto sh) { return launch_shape<decltype(sh)>(a, st); });
+}
+
+cudaError_t launch_fwd_exact(const FwdArgs &a, cudaStream_t st)
+{
+    return a.variant == kTcVariant ? launch_tc_exact(a, st) : cudaSuccess;
 }
 
 // Reference preparation for the screening stage: pair layout of (-2 r, |r|^2)

@@ -560,9 +560,13 @@ int fwd_tc_threads() { return kQueries; }
 cudaError_t launch_fwd_match_tc(const FwdArgs &a, cudaStream_t st)
 {
     fwd_match_tc_kernel<<<fwd_tc_grid(), kThreadsTc, kSmemBytes, st>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_exact(const FwdArgs &a, cudaStream_t st)
+{
     const long long Qtot = (long long)a.L.T * a.L.N;
+    if (Qtot == 0) return cudaSuccess;
     tc_exact_kernel<<<(unsigned)((Qtot + 255) / 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }

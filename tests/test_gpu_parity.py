@@ -271,19 +271,22 @@ def test_graph_replay_equals_direct_steps(stream):
 
 
 def test_kernel_times_from_graph_replays(stream):
-    """With profiling on, asicp_run's graph replays report one timed launch per kernel and pass."""
+    """With profiling on, asicp_run's graph replays report one timed launch per kernel and pass; the
+    tensor-core shape adds one exact-choice launch per matching pass."""
     w = synth.custom_case(P=1, K=8, N=128, M=600, grid=16, k_max=3, seed=41)
-    ctx = _ctx(w, stream, debug=False, profile=True)
-    try:
-        keep = tl.upload(ctx, w)
-        for _ in range(2):
-            asicp.asicp_run(ctx)
-        ms, n = asicp.asicp_kernel_times(ctx, reset=True)
-        del keep
-    finally:
-        asicp.asicp_destroy(ctx)
-    assert n == [2 * (w.k_max + 1)] * 4 + [2 * w.k_stein]
-    assert all(t > 0 for t in ms)
+    for shape in (0, asicp.FWD_SHAPES - 1):
+        ctx = _ctx(w, stream, debug=False, profile=True, fwd_shape=shape)
+        try:
+            keep = tl.upload(ctx, w)
+            for _ in range(2):
+                asicp.asicp_run(ctx)
+            ms, n = asicp.asicp_kernel_times(ctx, reset=True)
+            del keep
+        finally:
+            asicp.asicp_destroy(ctx)
+        exact = 2 * (w.k_max + 1) if shape == asicp.FWD_SHAPES - 1 else 0
+        assert n == [2 * (w.k_max + 1)] * 4 + [2 * w.k_stein, exact]
+        assert all(t > 0 for t, c in zip(ms, n) if c)
 
 
 def _uneven_batch(seed=43):
