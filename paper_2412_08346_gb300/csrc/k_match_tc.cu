@@ -203,8 +203,8 @@ size_t tc_ref_bytes(int Mpad) { return (size_t)Mpad / kCols * kTileBytes; }
 //   bfull[s]  tile in stage s has landed          (copy -> MMA)
 //   bempty[s] the MMA reading stage s is done:     (MMA commit -> copy, and -> reduction:
 //             the accumulator holds that tile     its next phase needs the reduction's acce)
-//   acce[b]   accumulator b has been read          (reduction -> MMA, 128 arrivals)
-//   afull     the item's query rows are written    (reduction warps -> MMA, 128 arrivals)
+//   acce[b]   accumulator b has been read          (reduction -> MMA, one arrival per warp)
+//   afull     the item's query rows are written    (reduction warps -> MMA, one arrival per warp)
 __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_tc[];
@@ -238,8 +238,9 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
     if (tid == 0) {
         s_abort = 0;
         for (int s = 0; s < kStages; ++s) { mbar_init(&bfull[s], 1); mbar_init(&bempty[s], 1); }
-        for (int b = 0; b < kBufs; ++b) mbar_init(&acce[b], kQueries);
-        mbar_init(&afull, kQueries);
+        // one arrival per reduction warp (its lane 0, after the warp's loads or stores)
+        for (int b = 0; b < kBufs; ++b) mbar_init(&acce[b], kQueries / 32);
+        mbar_init(&afull, kQueries / 32);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -371,7 +372,8 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
                     *reinterpret_cast<uint4 *>(sA + blk * kABlockBytes + core_offset(row, 8 * j)) = pk;
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(&afull);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&afull);
             }
             const float sn = sqrtf(o.x * o.x + o.y * o.y + o.z * o.z) * 1.001f;
             const float lam = tc_scale(rmax);
@@ -396,7 +398,8 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
                 for (int h = 0; h < kCols / kChunk; ++h)
                     mv[h] = ld_min64(tmem + lane_base + (uint32_t)(blk * kBufs + buf) * kCols + (uint32_t)(h * kChunk));
                 tc_fence_before();
-                mbar_arrive(&acce[buf]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[buf]);
 #pragma unroll
                 for (int h = 0; h < kCols / kChunk; ++h) {
                     // insert (v, chunk gc); strict < keeps the earlier chunk first on equal minima
@@ -527,8 +530,7 @@ __global__ void __launch_bounds__(256) tc_exact_kernel(const FwdArgs a)
         if (lane == src) { my_key = wk; my_idx = wk < 0x7f800000u ? wi : 0x7fffffff; }
     }
     if (!valid) return;
-    const int M = a.L.obj[obj].M;
-    const int bi = my_idx < M ? my_idx : 0;    // no finite distance at all (not reached with finite inputs)
+    const int bi = my_idx < a.L.obj[obj].M ? my_idx : 0;   // no finite distance at all (not reached with finite inputs)
     a.nn_idx[g] = bi;
     if (a.dbg_d2) a.dbg_d2[g] = __uint_as_float(my_key);
     if (a.dbg_sp) {
