@@ -158,7 +158,7 @@ asicp_status asicp_destroy(asicp_ctx *ctx);
 
 /* Object cloud R (M x 3) used for matching (Eq. 1, the reference cloud R of
  * Section III-A) and collision cloud C (Mc x 3; object and table, Section IV-A).
- * C_xyz = NULL uses C = R.  Computes CoM = centroid of R (Algorithm 1, line 1).
+ * C_xyz = NULL uses C = R.  Computes CoM = centroid of R (Algorithm 1).
  * Errors: INVALID_ARG (NULL R, M < 1, Mc < 1 when C is given, non-finite value). */
 asicp_status asicp_set_object(asicp_ctx *ctx, const float *R_xyz, int M, const float *C_xyz, int Mc);
 
