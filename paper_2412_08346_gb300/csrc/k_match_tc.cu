@@ -447,19 +447,16 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
 }
 
 // Exact choice after the tensor-core screening.  Each warp takes 32 consecutive
-// queries and rescans their candidate chunks one query at a time, all lanes
-// together: lane l reads points l and l + 32 of a chunk (coalesced), and two
-// warp-wide integer minimum reductions give the smallest exact-form float32
-// distance (its bits order as unsigned integers, distances being non-negative) and
-// then the lowest index holding it.  A query marked for the whole cloud is scanned
-// the same way over all M points.  Separate from the screening kernel so that
-// these loads do not stall the tensor pipe between work items.  The transformed
-// point is recomputed with the same float32 operations as in the screening
-// kernel, so it is the same value.
-__device__ __forceinline__ unsigned dist_key(float d)
-{
-    return d <= 3.4028235e38f ? __float_as_uint(d) : 0x7f800000u;   // NaN -> +inf
-}
+// queries; eight lanes rescan one query's candidate chunks together (lane l of the
+// group reads points l, l + 8, ..., so every load instruction reads four whole
+// 128-byte lines), four queries at a time, and three xor-shuffle rounds inside the
+// group give the smallest exact-form float32 distance with the lowest index
+// holding it.  Distances are non-negative (or +inf), so their bits order as
+// unsigned integers; NaN (only from non-finite poses) orders above +inf and is
+// never chosen.  A query marked for the whole cloud is scanned by the warp
+// together.  Separate from the screening kernel so that these loads do not stall
+// the tensor pipe between work items.  The transformed point is recomputed with
+// the same float32 operations as in the screening kernel, so it is the same value.
 
 // Merge this lane's (key, index) into the warp's running best (wk, wi), ties to
 // the lower index; every lane ends with the same (wk, wi).
@@ -470,73 +467,119 @@ __device__ __forceinline__ void warp_merge_min(unsigned key, int idx, unsigned &
     if (m < wk || (m == wk && mi < wi)) { wk = m; wi = mi; }
 }
 
+// (key, index) of the nearest point of chunk c for this lane's share (points
+// c * kChunk + sub + 8 k), merged into (bk, bi) with ties to the lower index.
+__device__ __forceinline__ void group_chunk(const float4 *__restrict__ R, int M, int c, int sub, float qx, float qy,
+                                            float qz, unsigned &bk, int &bi)
+{
+    const int base = c * kChunk + sub;
+    unsigned ck = 0x7f800000u;
+    int ci = 0x7fffffff;
+    if ((c + 1) * kChunk <= M) {
+#pragma unroll
+        for (int k = 0; k < kChunk / 8; ++k) {
+            const float4 v = __ldg(R + base + 8 * k);
+            const unsigned kk = __float_as_uint(dist2_f32(qx, qy, qz, v.x, v.y, v.z));
+            if (kk < ck) { ck = kk; ci = base + 8 * k; }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kChunk / 8; ++k) {
+            const int r = base + 8 * k;
+            const float4 v = __ldg(R + min(r, M - 1));
+            const unsigned kk = r < M ? __float_as_uint(dist2_f32(qx, qy, qz, v.x, v.y, v.z)) : 0x7f800000u;
+            if (kk < ck) { ck = kk; ci = r; }
+        }
+    }
+    if (ck < bk || (ck == bk && ci < bi)) { bk = ck; bi = ci; }
+}
+
 __global__ void __launch_bounds__(256) tc_exact_kernel(const FwdArgs a)
 {
     const long long Qtot = (long long)a.L.T * a.L.N;
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long wq0 = g - (threadIdx.x & 31);     // first query of this warp
     const bool valid = g < Qtot;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, grp = lane >> 3, sub = lane & 7;
     float3 o = make_float3(0.f, 0.f, 0.f);
     int obj = 0;
     int4 cd = make_int4(-1, -1, -1, -1);
     if (valid) {
         const int pk = (int)(g / a.L.N), i = (int)(g - (long long)pk * a.L.N);
-        const int grp = a.L.part_grp[pk];
-        obj = grp / a.L.P;
+        const int grp_id = a.L.part_grp[pk];
+        obj = grp_id / a.L.P;
         const float *th = a.theta + (size_t)pk * 8;
         float Rm[9];
         quat_rot_f32(th[3], th[4], th[5], th[6], Rm);
-        const float4 s = a.S[(size_t)(grp % a.L.P) * a.L.N + i];
+        const float4 s = a.S[(size_t)(grp_id % a.L.P) * a.L.N + i];
         o = xform_f32(Rm, th[0], th[1], th[2], s.x, s.y, s.z);
         cd = a.cand[g];
+        if (a.dbg_sp) {
+            a.dbg_sp[g * 3 + 0] = o.x;
+            a.dbg_sp[g * 3 + 1] = o.y;
+            a.dbg_sp[g * 3 + 2] = o.z;
+        }
     }
-    unsigned my_key = 0x7f800000u;
-    int my_idx = 0x7fffffff;
-    unsigned todo = __ballot_sync(0xffffffffu, valid);
-    while (todo) {
-        const int src = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const float qx = __shfl_sync(0xffffffffu, o.x, src), qy = __shfl_sync(0xffffffffu, o.y, src),
-                    qz = __shfl_sync(0xffffffffu, o.z, src);
-        const int wo = __shfl_sync(0xffffffffu, obj, src);
-        const int c[4] = {__shfl_sync(0xffffffffu, cd.x, src), __shfl_sync(0xffffffffu, cd.y, src),
-                          __shfl_sync(0xffffffffu, cd.z, src), __shfl_sync(0xffffffffu, cd.w, src)};
-        const float4 *R = a.L.obj[wo].R;
-        const int M = a.L.obj[wo].M;
-        unsigned wk = 0x7f800000u;
-        int wi = 0x7fffffff;
-        if (c[0] == -2) {
-            unsigned k = 0x7f800000u;
-            int ki = 0x7fffffff;
-            for (int r = lane; r < M; r += 32) {
-                const float4 v = __ldg(R + r);
-                const unsigned dk = dist_key(dist2_f32(qx, qy, qz, v.x, v.y, v.z));
-                if (dk < k) { k = dk; ki = r; }
-            }
-            warp_merge_min(k, ki, wk, wi);
-        } else {
+    // candidate chunks: four queries at a time, eight lanes each
+#pragma unroll 1
+    for (int it = 0; it < 4; ++it) {
+        const int src = it * 8 + grp * 2;                  // two queries per group and round
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (c[j] < 0) continue;
-                const int r0 = c[j] * kChunk + lane, r1 = r0 + 32;
-                const float4 v0 = __ldg(R + min(r0, M - 1)), v1 = __ldg(R + min(r1, M - 1));
-                unsigned k0 = r0 < M ? dist_key(dist2_f32(qx, qy, qz, v0.x, v0.y, v0.z)) : 0x7f800000u;
-                const unsigned k1 = r1 < M ? dist_key(dist2_f32(qx, qy, qz, v1.x, v1.y, v1.z)) : 0x7f800000u;
-                int ki = r0;
-                if (k1 < k0) { k0 = k1; ki = r1; }
-                warp_merge_min(k0, ki, wk, wi);
+        for (int half = 0; half < 2; ++half) {
+            const int q = src + half;
+            const float qx = __shfl_sync(0xffffffffu, o.x, q), qy = __shfl_sync(0xffffffffu, o.y, q),
+                        qz = __shfl_sync(0xffffffffu, o.z, q);
+            const int qo = __shfl_sync(0xffffffffu, obj, q);
+            const int c0 = __shfl_sync(0xffffffffu, cd.x, q), c1 = __shfl_sync(0xffffffffu, cd.y, q),
+                      c2 = __shfl_sync(0xffffffffu, cd.z, q), c3 = __shfl_sync(0xffffffffu, cd.w, q);
+            const bool qv = wq0 + q < Qtot && c0 >= 0;      // valid and not a whole-cloud query
+            unsigned bk = 0x7f800000u;
+            int bi = 0x7fffffff;
+            int M = 1;
+            if (qv) {
+                const float4 *R = a.L.obj[qo].R;
+                M = a.L.obj[qo].M;
+                group_chunk(R, M, c0, sub, qx, qy, qz, bk, bi);
+                if (c1 >= 0) group_chunk(R, M, c1, sub, qx, qy, qz, bk, bi);
+                if (c2 >= 0) group_chunk(R, M, c2, sub, qx, qy, qz, bk, bi);
+                if (c3 >= 0) group_chunk(R, M, c3, sub, qx, qy, qz, bk, bi);
+            }
+#pragma unroll
+            for (int off = 1; off < 8; off <<= 1) {
+                const unsigned ok = __shfl_xor_sync(0xffffffffu, bk, off);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                if (ok < bk || (ok == bk && oi < bi)) { bk = ok; bi = oi; }
+            }
+            if (qv && sub == 0) {
+                a.nn_idx[wq0 + q] = bk < 0x7f800000u && bi < M ? bi : 0;   // no finite distance: 0
+                if (a.dbg_d2) a.dbg_d2[wq0 + q] = __uint_as_float(bk < 0x7f800000u ? bk : 0x7f800000u);
             }
         }
-        if (lane == src) { my_key = wk; my_idx = wk < 0x7f800000u ? wi : 0x7fffffff; }
     }
-    if (!valid) return;
-    const int bi = my_idx < a.L.obj[obj].M ? my_idx : 0;   // no finite distance at all (not reached with finite inputs)
-    a.nn_idx[g] = bi;
-    if (a.dbg_d2) a.dbg_d2[g] = __uint_as_float(my_key);
-    if (a.dbg_sp) {
-        a.dbg_sp[g * 3 + 0] = o.x;
-        a.dbg_sp[g * 3 + 1] = o.y;
-        a.dbg_sp[g * 3 + 2] = o.z;
+    // whole-cloud queries, one at a time by the warp together
+    unsigned pending = __ballot_sync(0xffffffffu, valid && cd.x == -2);
+    while (pending) {
+        const int src = __ffs(pending) - 1;
+        pending &= pending - 1;
+        const float qx = __shfl_sync(0xffffffffu, o.x, src), qy = __shfl_sync(0xffffffffu, o.y, src),
+                    qz = __shfl_sync(0xffffffffu, o.z, src);
+        const int qo = __shfl_sync(0xffffffffu, obj, src);
+        const float4 *R = a.L.obj[qo].R;
+        const int M = a.L.obj[qo].M;
+        unsigned k = 0x7f800000u;
+        int ki = 0x7fffffff;
+        for (int r = lane; r < M; r += 32) {
+            const float4 v = __ldg(R + r);
+            const unsigned dk = __float_as_uint(dist2_f32(qx, qy, qz, v.x, v.y, v.z));
+            if (dk < k) { k = dk; ki = r; }
+        }
+        unsigned wk = 0x7f800000u;
+        int wi = 0x7fffffff;
+        warp_merge_min(k, ki, wk, wi);
+        if (lane == src) {
+            a.nn_idx[g] = wk < 0x7f800000u && wi < M ? wi : 0;
+            if (a.dbg_d2) a.dbg_d2[g] = __uint_as_float(wk);
+        }
     }
 }
 
