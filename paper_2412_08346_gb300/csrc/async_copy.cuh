@@ -58,9 +58,9 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
     return true;
 }
 
-// The same for a whole warp: lane 0 polls (backing off between polls so that a
-// warp full of waiters does not crowd the barrier's shared memory), the warp
-// then continues together.  Returns the same verdict on every lane.
+// The same for a whole warp: lane 0 polls (try_wait suspends in hardware; a
+// software back-off between polls measured slower), the warp then continues
+// together.  Returns the same verdict on every lane.
 __device__ __forceinline__ bool mbar_wait_warp(unsigned long long *bar, unsigned parity)
 {
     bool ok = true;
@@ -69,7 +69,6 @@ __device__ __forceinline__ bool mbar_wait_warp(unsigned long long *bar, unsigned
             const long long t0 = clock64();
             while (!mbar_try_wait(bar, parity)) {
                 if (clock64() - t0 > kWaitCycles) { ok = false; break; }
-                __nanosleep(32);
             }
         }
     }
