@@ -20,6 +20,7 @@ import numpy as np
 from . import asicp, proposal, synth
 
 P_DEFAULT = 3
+FWD_SHAPE = asicp.FWD_SHAPES - 1      # the tensor-core matching shape (fastest on these workloads)
 
 
 def object_clouds(n: int, m: int, seed: int) -> np.ndarray:
@@ -30,7 +31,8 @@ def object_clouds(n: int, m: int, seed: int) -> np.ndarray:
 def _context(preshapes, n_obj, K, k_max, stream, init_radius=0.15):
     P = len(preshapes)
     cfg = asicp.asicp_config_default(P=P, K=int(np.max(K)), k_max=k_max, k_stein=synth.k_stein_for(k_max),
-                                     schedule=0, cuda_stream=stream, n_objects=n_obj, init_radius=init_radius)
+                                     schedule=0, cuda_stream=stream, n_objects=n_obj, init_radius=init_radius,
+                                     fwd_shape=FWD_SHAPE)
     ctx = asicp.asicp_create(cfg)
     asicp.asicp_set_particle_counts(ctx, np.full(n_obj * P, K, np.int32) if np.isscalar(K) else K)
     for p, ps in enumerate(preshapes):

@@ -228,21 +228,61 @@ def test_planted_duplicates_resolve_to_lowest_index(stream):
     N = 40
     S = np.concatenate([R[:20], R[100:120] + np.float32(1e-3)]).astype(np.float32)
     sdf = -np.ones((8, 8, 8), np.float32)
-    cfg = asicp.asicp_config_default(P=1, K=1, k_max=1, k_stein=0, conv_tol=-1.0, debug=1, cuda_stream=stream)
-    ctx = asicp.asicp_create(cfg)
-    try:
-        asicp.asicp_set_object(ctx, R)
-        asicp.asicp_set_gripper_sdf(ctx, 0, S, sdf, np.full(3, -0.1, np.float32), np.float32(0.2 / 7))
-        asicp.asicp_set_state(ctx, np.array([[0, 0, 0, 1, 0, 0, 0]], np.float32), 0)
-        asicp.asicp_step(ctx, 0)
-        st = tl.read_state(ctx, 1, 1, N, M)
-    finally:
-        asicp.asicp_destroy(ctx)
-    idx = st["nn_idx"][0]
-    assert np.array_equal(idx[:20], np.arange(20))
-    assert np.all(st["nn_d2"][0, :20] == 0.0)
-    rep = {}
-    tl.check_nn(st["s_prime"][0], R, idx, rep)
+    for shape in (0, asicp.FWD_SHAPES - 1):       # float32 kernel; tensor-core screening + exact choice
+        cfg = asicp.asicp_config_default(P=1, K=1, k_max=1, k_stein=0, conv_tol=-1.0, debug=1, cuda_stream=stream,
+                                         fwd_shape=shape)
+        ctx = asicp.asicp_create(cfg)
+        try:
+            asicp.asicp_set_object(ctx, R)
+            asicp.asicp_set_gripper_sdf(ctx, 0, S, sdf, np.full(3, -0.1, np.float32), np.float32(0.2 / 7))
+            asicp.asicp_set_state(ctx, np.array([[0, 0, 0, 1, 0, 0, 0]], np.float32), 0)
+            asicp.asicp_step(ctx, 0)
+            st = tl.read_state(ctx, 1, 1, N, M)
+        finally:
+            asicp.asicp_destroy(ctx)
+        idx = st["nn_idx"][0]
+        assert np.array_equal(idx[:20], np.arange(20)), shape
+        assert np.all(st["nn_d2"][0, :20] == 0.0), shape
+        rep = {}
+        tl.check_nn(st["s_prime"][0], R, idx, rep)
+
+
+def test_tensor_core_far_and_tiny_queries(stream):
+    """Tensor-core shape on queries its f16 split cannot represent (a particle 40 m away: the scaled
+    coordinates leave the f16 range, so the whole cloud is scanned) and on an object cloud of tiny
+    extent: indices equal the FP64 argmin over the float32 queries up to near-ties, on both shapes.  The
+    two shapes agree exactly on the near particles of the ordinary object; for the far particle (whose
+    exact-form float32 distances carry rounding far above the gaps between object points) and the tiny
+    object they may pick different near-tie partners: the whole-cloud scan takes the float32 argmin over
+    every point, the float32 kernel's screening the float32 argmin over the chunks nearest in exact
+    arithmetic."""
+    g = np.random.default_rng(31)
+    for scale in (1.0, 1e-3):
+        M = 1000 + int(scale < 1)                       # a ragged last chunk either way
+        R = (g.uniform(-0.05, 0.05, (M, 3)) * scale).astype(np.float32)
+        N = 96
+        S = (g.uniform(-0.04, 0.04, (N, 3)) * scale).astype(np.float32)
+        sdf = -np.ones((8, 8, 8), np.float32)
+        theta = np.array([[0.01 * scale, 0, 0, 1, 0, 0, 0], [40.0, 0, 0, 0, 1, 0, 0], [0, 0.02 * scale, 0, 0.5, 0.5, 0.5, 0.5]],
+                         np.float32)
+        got = []
+        for shape in (0, asicp.FWD_SHAPES - 1):
+            cfg = asicp.asicp_config_default(P=1, K=3, k_max=1, k_stein=0, conv_tol=-1.0, debug=1, cuda_stream=stream,
+                                             fwd_shape=shape)
+            ctx = asicp.asicp_create(cfg)
+            try:
+                asicp.asicp_set_object(ctx, R)
+                asicp.asicp_set_gripper_sdf(ctx, 0, S, sdf, np.full(3, -0.1, np.float32), np.float32(0.2 / 7))
+                asicp.asicp_set_state(ctx, theta, 0)
+                asicp.asicp_step(ctx, 0)
+                st = tl.read_state(ctx, 1, 3, N, M)
+            finally:
+                asicp.asicp_destroy(ctx)
+            rep = {}
+            tl.check_nn(st["s_prime"].reshape(-1, 3), R, st["nn_idx"].reshape(-1), rep)
+            got.append(st["nn_idx"].copy())
+        if scale == 1.0:
+            assert np.array_equal(got[0][[0, 2]], got[1][[0, 2]])
 
 
 def test_graph_replay_equals_direct_steps(stream):
