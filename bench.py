@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--small", action="store_true", help="small workload (debugging only)")
     ap.add_argument("--fwd-shape", type=int, default=-1,
                     help="forward-matching kernel shape (index into asicp.FWD_VARIANTS); -1: autotune")
+    ap.add_argument("--large", action="store_true",
+                    help="mixed-precision configuration (3 x 1024 particles, N 4096, M 65536, SDF 128^3): both "
+                         "matching shapes timed and compared")
     ap.add_argument("--batched", type=int, default=0, metavar="OBJECTS",
                     help="time OBJECTS objects (point counts 1k-32k, 128/256/512 particles per preshape) optimised "
                          "together against each object alone; prints its own JSON line")
@@ -508,6 +511,58 @@ def run_batched(args):
                    "pairs_per_iteration": pairs, "fwd_shape": asicp.FWD_VARIANTS[shape]}}), flush=True)
 
 
+def run_large(args):
+    """The mixed-precision configuration (3 preshapes x 1024 particles, N=4096, M=65536 superquadric
+    partial view, SDF 128^3): the float32 matching kernel (the autotuner's best float32 shape) and the
+    tensor-core screening + exact choice, each timed over a 4-iteration run (per-launch device time
+    from the library's event timers), and the fraction of correspondences on which the two agree in
+    one step from the same poses."""
+    import torch
+    from paper_2412_08346_gb300 import asicp, synth
+    import oracle
+    w = synth.large_case(k_max=4)
+    P, K, N, M = len(w.preshapes), w.K, w.preshapes[0].S.shape[0], len(w.objects[0].points)
+    stream = torch.cuda.current_stream()
+    R_dev = torch.from_numpy(w.objects[0].points).cuda()
+    pre_dev = [(torch.from_numpy(p.S).cuda(), torch.from_numpy(p.sdf).cuda()) for p in w.preshapes]
+    com = w.objects[0].points.astype(np.float64).mean(0)
+    th0 = np.tile(oracle.fibonacci_init(K, com, 0.15), (P, 1)).astype(np.float32)
+    tc_shape = asicp.FWD_VARIANTS.index(TC_SHAPE)
+    out, idx = {}, {}
+    for name, shape in (("float32", 5), ("tensor_core", tc_shape)):
+        cfg = asicp.asicp_config_default(P=P, K=K, k_max=w.k_max, k_stein=w.k_stein, schedule=w.schedule, profile=1,
+                                         debug=1, cuda_stream=stream.cuda_stream, fwd_shape=shape)
+        ctx = asicp.asicp_create(cfg)
+        try:
+            asicp.asicp_set_object(ctx, R_dev)
+            for p, (S, g) in enumerate(pre_dev):
+                asicp.asicp_set_gripper_sdf(ctx, p, S, g, w.preshapes[p].origin, w.preshapes[p].voxel)
+            asicp.asicp_set_state(ctx, th0, 0)
+            asicp.asicp_step(ctx, 0)
+            nn = np.zeros((P * K, N), np.int32)
+            asicp.asicp_get_state(ctx, nn_idx=nn)
+            idx[name] = nn
+            asicp.asicp_run(ctx, th0)                 # warm-up (captures the loop)
+            torch.cuda.synchronize()
+            asicp.asicp_kernel_times(ctx, reset=True)
+            asicp.asicp_run(ctx, th0)
+            ms, n = asicp.asicp_kernel_times(ctx, reset=True)
+            per = (ms[0] / n[0]) + (ms[5] / n[5] if n[5] else 0.0)
+            out[name] = {"fwd_shape": asicp.FWD_VARIANTS[shape], "matching_ms_per_pass": per,
+                         "pairs_per_s": P * K * N * M / (per / 1e3),
+                         "kernel_ms_per_pass": {k: v / max(c, 1) for k, v, c in zip(asicp.KERNEL_KINDS, ms, n)}}
+        finally:
+            asicp.asicp_destroy(ctx)
+    same = float(np.mean(idx["float32"] == idx["tensor_core"]))
+    print(json.dumps({"metric": "matching ms per pass, float32 vs tensor-core shape (mixed-precision configuration)",
+                      "config": {"workload": w.name, "P": P, "K": K, "N": N, "M": M,
+                                 "pairs_per_pass": P * K * N * M},
+                      "float32": out["float32"], "tensor_core": out["tensor_core"],
+                      "speedup": out["float32"]["matching_ms_per_pass"] / out["tensor_core"]["matching_ms_per_pass"],
+                      "identical_correspondences": same, "queries": int(idx["float32"].size),
+                      "data": "synthetic"}), flush=True)
+
+
 def run_learned(args):
     """Learned initial poses (64 particles per preshape, 30 iterations) against the plain method
     (256 Fibonacci particles, 100 iterations) and against Fibonacci at the learned budget."""
@@ -543,6 +598,9 @@ def main():
         return
     if args.batched:
         run_batched(args)
+        return
+    if args.large:
+        run_large(args)
         return
     if args.profile_case:
         run_profile_case(args)
