@@ -68,8 +68,12 @@ typedef enum {
  *                  extended across objects)
  *   autotune      1: the first asicp_run times the forward-matching kernel shapes on its
  *                  workload and keeps the fastest (see asicp_autotune); 0: use fwd_shape
- *   fwd_shape     forward-matching kernel shape, 0 .. ASICP_FWD_SHAPES-1 (0 = default;
- *                  the shapes differ in speed only, never in results)
+ *   fwd_shape     forward-matching kernel shape, 0 .. ASICP_FWD_SHAPES-1 (0 = default):
+ *                  0 .. ASICP_FWD_SHAPES-2 are float32 kernels, ASICP_FWD_SHAPES-1 the
+ *                  tensor-core screening with its exact-choice kernel (not with mini-batches).
+ *                  Every shape returns the lowest-index minimum of the exact-form float32
+ *                  distance over the points that can be nearest; they can differ only where
+ *                  several points' float32 distances tie within rounding (near-ties)
  *   init_mode     initial poses when asicp_run gets none: 0 = Fibonacci sphere of radius
  *                  init_radius around the CoM, approach axis towards the CoM; 1 = the
  *                  variant of the paper's experiments (Section VI-A, Fig. 3 (b)):
@@ -273,8 +277,9 @@ asicp_status asicp_set_minibatch(asicp_ctx *ctx, const int *offsets, const int *
  * objects and poses (the Fibonacci initial poses when none are set) and keep the
  * fastest for later steps and runs.  *chosen receives the shape index
  * (0 .. ASICP_FWD_SHAPES-1), ms[ASICP_FWD_SHAPES] the mean launch time of each
- * shape (either may be NULL).  The results of every shape are identical; only
- * their speed differs.
+ * shape (either may be NULL).  The shapes differ in speed; their results agree
+ * up to near-ties (see config.fwd_shape).  With a mini-batch ramp set, the
+ * tensor-core shape is skipped (its ms entry is 0).
  * Errors: STATE (inputs not set), CUDA. */
 asicp_status asicp_autotune(asicp_ctx *ctx, int *chosen, float *ms);
 
