@@ -95,15 +95,17 @@ def test_host_pointer_inputs_match_device_pointer_inputs(stream):
         assert np.array_equal(a, b)
 
 
-def test_free_running_small_box_final_poses(stream):
-    """50 free-running iterations on both sides: final poses within 1 mm / 1e-3 rad."""
+@pytest.mark.parametrize("shape", [0, asicp.FWD_SHAPES - 1])
+def test_free_running_small_box_final_poses(stream, shape):
+    """50 free-running iterations on both sides: final poses within 1 mm / 1e-3 rad (float32 and
+    tensor-core matching)."""
     import oracle
     w = synth.small_box_case()
     orc = tl.make_oracle(w)
     sched = orc.schedule(k_max=w.k_max, k_stein=w.k_stein, schedule=w.schedule, g0=w.g0, g1=w.g1, N=orc.N)
     theta0 = oracle.fibonacci_init(w.K, orc.R.mean(0), 0.15)
     ost, order = orc.run(theta0.astype(np.float32).astype(np.float64)[None], sched, nthreads=4, topk=8)
-    ctx = _ctx(w, stream, debug=False)
+    ctx = _ctx(w, stream, debug=False, fwd_shape=shape)
     try:
         keep = tl.upload(ctx, w)
         asicp.asicp_run(ctx, np.ascontiguousarray(theta0.astype(np.float32)))
@@ -124,11 +126,14 @@ def test_free_running_small_box_final_poses(stream):
 
 def test_paper_scale_sampled_step(stream):
     """3 x 256 particles, N=2048, M=8192, SDF 64^3: one SVGD and one SGD step, sampled particles,
-    in the launch configuration the benchmark uses."""
+    in the launch configuration the benchmark uses (the tensor-core matching shape, which the
+    autotuner picks at this workload; the float32 shape is covered at this size as well)."""
     w = synth.paper_scale_case()
     g = np.random.default_rng(3)
     sample = sorted(g.choice(w.K * 3, 24, replace=False).tolist())
-    rep = _teacher_forced_run(w, stream, [0, 60], {}, sample=sample)
+    rep = _teacher_forced_run(w, stream, [0, 60], {}, sample=sample, fwd_shape=asicp.FWD_SHAPES - 1)
+    print("paper scale sampled (tensor cores):", rep)
+    rep = _teacher_forced_run(w, stream, [0], {}, sample=sample[:8], fwd_shape=0)
     print("paper scale sampled:", rep)
 
 
@@ -340,15 +345,17 @@ def _uneven_batch(seed=43):
     return pre, objs, K
 
 
-def test_batched_objects_match_solo_runs(stream):
+@pytest.mark.parametrize("shape", [0, asicp.FWD_SHAPES - 1])
+def test_batched_objects_match_solo_runs(stream, shape):
     """Objects optimised together (one launch per kernel covering all of them) give bit-identical
-    poses, costs and rankings to running each object alone."""
+    poses, costs and rankings to running each object alone, with the float32 and with the
+    tensor-core matching."""
     pre, objs, K = _uneven_batch()
     P, k_max, k_stein = 2, 6, 3
 
     def make(nobj):
         cfg = asicp.asicp_config_default(P=P, K=8, k_max=k_max, k_stein=k_stein, conv_tol=-1.0, cuda_stream=stream,
-                                         n_objects=nobj)
+                                         n_objects=nobj, fwd_shape=shape)
         return asicp.asicp_create(cfg)
 
     ctx = make(len(objs))
@@ -399,13 +406,15 @@ def test_batched_objects_match_solo_runs(stream):
         first += n
 
 
-def test_batched_step_teacher_forced(stream):
-    """One batched SVGD step against the oracle, object by object (uneven sizes and particle counts)."""
+@pytest.mark.parametrize("shape", [0, asicp.FWD_SHAPES - 1])
+def test_batched_step_teacher_forced(stream, shape):
+    """One batched SVGD step against the oracle, object by object (uneven sizes and particle counts),
+    with the float32 and with the tensor-core matching."""
     pre, objs, K = _uneven_batch(seed=47)
     import oracle
     P, N = 2, 256
     cfg = asicp.asicp_config_default(P=P, K=8, k_max=4, k_stein=2, conv_tol=-1.0, debug=1, cuda_stream=stream,
-                                     n_objects=len(objs))
+                                     n_objects=len(objs), fwd_shape=shape)
     ctx = asicp.asicp_create(cfg)
     try:
         asicp.asicp_set_particle_counts(ctx, K.ravel())
