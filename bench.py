@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--small", action="store_true", help="small workload (debugging only)")
     ap.add_argument("--fwd-shape", type=int, default=-1,
                     help="forward-matching kernel shape (index into asicp.FWD_VARIANTS); -1: autotune")
+    ap.add_argument("--k-sweep", action="store_true",
+                    help="ms per grasp set of the paper-scale workload for K = 32 .. 1024 particles per preshape")
     ap.add_argument("--large", action="store_true",
                     help="mixed-precision configuration (3 x 1024 particles, N 4096, M 65536, SDF 128^3): both "
                          "matching shapes timed and compared")
@@ -295,9 +297,14 @@ def run_gpu(args, rank, world, local_rank):
         oracle.build()
         nthreads = os.cpu_count() or 1
         v, info = oracle_sample(w, args.cpu_seconds, nthreads)
+        v1, info1 = oracle_sample(w, max(1.0, args.cpu_seconds / 3), 1)
         cpu = {"value": v, "unit": "pairs/s", "cores": nthreads, "kind": "oracle",
                "sample": (f"FP64 oracle, {info['particles_per_preshape']} particles per preshape x {P} preshapes, "
-                          f"{info['iterations']} whole iterations (N={N}, M={M}), {info['seconds']:.1f} s")}
+                          f"{info['iterations']} whole iterations (N={N}, M={M}), {info['seconds']:.1f} s"),
+               "single_thread_value": v1,
+               "single_thread_sample": (f"1 thread, {info1['particles_per_preshape']} particle per preshape x {P} "
+                                        f"preshapes, {info1['iterations']} whole iterations, "
+                                        f"{info1['seconds']:.1f} s")}
     asicp.asicp_destroy(ctx)
     if rank == 0:
         line = {
@@ -511,6 +518,50 @@ def run_batched(args):
                    "pairs_per_iteration": pairs, "fwd_shape": asicp.FWD_VARIANTS[shape]}}), flush=True)
 
 
+def run_k_sweep(args):
+    """Time per grasp set against the particle count (the paper's time-versus-initialisations axis):
+    the paper-scale workload with K = 32 .. 1024 particles per preshape, the kernel shape autotuned
+    for each K, L2 flushed before every timed run."""
+    import torch
+    from paper_2412_08346_gb300 import asicp, synth
+    w = synth.paper_scale_case()
+    P, N, M = len(w.preshapes), w.preshapes[0].S.shape[0], len(w.objects[0].points)
+    stream = torch.cuda.current_stream()
+    R_dev = torch.from_numpy(w.objects[0].points).cuda()
+    pre_dev = [(torch.from_numpy(p.S).cuda(), torch.from_numpy(p.sdf).cuda()) for p in w.preshapes]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    rows = []
+    for K in (32, 64, 128, 256, 512, 1024):
+        cfg = asicp.asicp_config_default(P=P, K=K, k_max=w.k_max, k_stein=w.k_stein, schedule=w.schedule,
+                                         cuda_stream=stream.cuda_stream)
+        ctx = asicp.asicp_create(cfg)
+        try:
+            asicp.asicp_set_object(ctx, R_dev)
+            for p, (S, g) in enumerate(pre_dev):
+                asicp.asicp_set_gripper_sdf(ctx, p, S, g, w.preshapes[p].origin, w.preshapes[p].voxel)
+            shape, _ = asicp.asicp_autotune(ctx)
+            for _ in range(2):
+                asicp.asicp_run(ctx)
+            times = []
+            for _ in range(max(2, args.steps)):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                asicp.asicp_run(ctx)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            ms = float(np.median(times))
+            rows.append({"K": K, "ms_per_grasp_set": ms, "pairs_per_s": P * K * N * M * (w.k_max + 1) / (ms / 1e3),
+                         "fwd_shape": asicp.FWD_VARIANTS[shape]})
+        finally:
+            asicp.asicp_destroy(ctx)
+    print(json.dumps({"metric": "ms per grasp set against particles per preshape", "unit": "ms/grasp set",
+                      "higher_is_better": False, "config": {"workload": w.name, "P": P, "N": N, "M": M,
+                                                            "iterations": w.k_max},
+                      "sweep": rows, "data": "synthetic"}), flush=True)
+
+
 def run_large(args):
     """The mixed-precision configuration (3 preshapes x 1024 particles, N=4096, M=65536 superquadric
     partial view, SDF 128^3): the float32 matching kernel (the autotuner's best float32 shape) and the
@@ -601,6 +652,9 @@ def main():
         return
     if args.large:
         run_large(args)
+        return
+    if args.k_sweep:
+        run_k_sweep(args)
         return
     if args.profile_case:
         run_profile_case(args)
