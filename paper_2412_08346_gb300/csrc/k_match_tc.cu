@@ -135,23 +135,6 @@ __device__ __forceinline__ float ld_min64(uint32_t taddr)
     return m;
 }
 
-// Exact-form nearest point among the object points of chunk [lo, lo + kChunk) below
-// M, merged into (best, bi) with ties to the lower index.  A fixed trip count with
-// clamped addresses lets sixteen loads be in flight at once: with most of shared
-// memory given to the tile ring, the object cloud is not L1-resident and each load
-// pays the L2 latency.
-__device__ __forceinline__ void exact_chunk_tie(const float4 *__restrict__ R, int lo, int M, float3 q, float &best,
-                                                int &bi)
-{
-#pragma unroll 16
-    for (int k = 0; k < kChunk; ++k) {
-        const int r = lo + k;
-        const float4 v = __ldg(R + min(r, M - 1));
-        const float d = dist2_f32(q.x, q.y, q.z, v.x, v.y, v.z);
-        if (r < M && (d < best || (d == best && r < bi))) { best = d; bi = r; }
-    }
-}
-
 }  // namespace
 
 // Augmented object tiles for the tensor-core kernel: point r goes to tile
