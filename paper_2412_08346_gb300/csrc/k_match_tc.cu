@@ -26,7 +26,7 @@
 // would leave the f16 range takes the whole-cloud scan.  Each query keeps its kTop
 // best chunk minima (chunks of 64 object points) and the best of the rest; the
 // chunks within 2 delta_tc of the best are rescanned with the exact-form float32
-// distance (ties to the lower index) by tc_exact_kernel, one thread per query, or,
+// distance (ties to the lower index) by tc_exact_kernel, eight lanes per query, or,
 // when more than kTop qualify, by a warp scanning the whole cloud for that query
 // together.  The result is the exact-form argmin over every point that can be
 // nearest, as in the float32 kernel.
