@@ -3,7 +3,26 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace asicp {
+
+constexpr int kDeviceSlots = 64;       // devices a process can use the library on
+
+// A launch value that depends on the device (its SM count, an occupancy) and
+// sets the kernel attributes it relies on: compute() runs once per device, with
+// that device current, under a lock, so several devices and several host
+// threads each get their own value.  Returns 0 (an invalid grid, which the
+// launch then reports) if the current device cannot be read.
+template <class F>
+int per_device_value(int (&cache)[kDeviceSlots], std::mutex &mu, F compute)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDeviceSlots) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache[dev] == 0) cache[dev] = compute();
+    return cache[dev];
+}
 
 constexpr int kRefTilePts = 2048;      // object points per shared-memory tile of the matching kernel
 constexpr int kFwdSums = 13;           // per-particle matching sums (see match kernel)

@@ -452,13 +452,14 @@ cudaError_t init_collision_attributes()
 
 cudaError_t launch_collide_nn(const CollideArgs &a, cudaStream_t st)
 {
-    static int grid = 0;
-    if (grid == 0) {
+    static int grids[kDeviceSlots] = {};
+    static std::mutex mu;
+    const int grid = per_device_value(grids, mu, [] {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        grid = 4 * sms;
-    }
+        return 4 * sms;
+    });
     const size_t smem = 2 * sizeof(float4) * (size_t)((a.L.N + 63) / 64 * 64) + 32 * sizeof(float4);
     collide_nn_kernel<<<grid, kColThreads, smem, st>>>(a);
     return cudaGetLastError();

@@ -275,17 +275,17 @@ using Shape6 = FwdShape<6, 64, 128, 1024, 4>;
 template <class Shape>
 int shape_grid()
 {
-    static int grid = 0;
-    if (grid == 0) {
+    static int grid[kDeviceSlots] = {};
+    static std::mutex mu;
+    return per_device_value(grid, mu, [] {
         const int smem = 2 * Shape::kTile * 16;
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaFuncSetAttribute(fwd_match_kernel<Shape>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_match_kernel<Shape>, Shape::kThreads, smem);
-        grid = sms * (per_sm > 0 ? per_sm : 1);
-    }
-    return grid;
+        return sms * (per_sm > 0 ? per_sm : 1);
+    });
 }
 
 template <class Shape>

@@ -570,17 +570,17 @@ __global__ void __launch_bounds__(256) tc_exact_kernel(const FwdArgs a)
 // shared-memory request leaves no room for a third.
 int fwd_tc_grid()
 {
-    static int grid = 0;
-    if (grid == 0) {
+    static int grid[kDeviceSlots] = {};
+    static std::mutex mu;
+    return per_device_value(grid, mu, [] {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaFuncSetAttribute(fwd_match_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
         cudaFuncSetAttribute(fwd_match_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
-        grid = 2 * sms;
-    }
-    return grid;
+        return 2 * sms;
+    });
 }
 
 int fwd_tc_threads() { return kQueries; }
