@@ -179,7 +179,8 @@ asicp_status asicp_set_particle_counts(asicp_ctx *ctx, const int *K, int n);
  * sampled on a node-centred grid of nx*ny*nz float32 values, x fastest, positive
  * inside the gripper (Eq. 12), node (0,0,0) at origin, spacing voxel.  Computes
  * TCP = centroid of S (Section IV-B).  Every preshape must have the same N
- * (1 <= N <= 6144).
+ * (1 <= N <= 6144).  The context keeps a copy of the grid and a corner-packed
+ * copy for the lookups (32 bytes per cell: 8 (nx-1)(ny-1)(nz-1) floats).
  * Errors: INVALID_ARG (index, N out of range, a grid dimension < 2, voxel <= 0, N differing
  * from an earlier preshape, non-finite value). */
 asicp_status asicp_set_gripper_sdf(asicp_ctx *ctx, int preshape, const float *S_xyz, int N,

@@ -93,6 +93,7 @@ struct asicp_ctx {
     std::vector<char> pre_set;
     std::vector<SdfMeta> meta;
     std::vector<DevMem> grids;
+    std::vector<DevMem> cells;         // corner-packed grids
     int k_next = 0;
 
     // mini-batches of the object cloud per iteration (Table I), one object only
@@ -749,6 +750,7 @@ asicp_status asicp_create(const asicp_config *cfg, asicp_ctx **out)
     c->pre_set.assign(cfg->P, 0);
     c->meta.assign(cfg->P, SdfMeta{});
     c->grids.resize(cfg->P);
+    c->cells.resize(cfg->P);
     c->objs.resize(c->nobj);
     c->Kg.assign((size_t)c->nobj * cfg->P, cfg->K);
     asicp_status s = guarded(c, [&] {
@@ -874,6 +876,9 @@ asicp_status asicp_set_gripper_sdf(asicp_ctx *ctx, int preshape, const float *S_
         ctx->grids[preshape].ensure(sizeof(float) * nv, "sdf grid");
         ck(cudaMemcpyAsync(ctx->grids[preshape].p, sdf, sizeof(float) * nv, cudaMemcpyDefault, ctx->st), "copy sdf");
         ck(launch_check_finite(ctx->grids[preshape].as<float>(), (long long)nv, ctx->errw.as<int>(), ctx->st), "check sdf");
+        ctx->cells[preshape].ensure(sdf_cells_bytes(nx, ny, nz), "corner-packed sdf grid");
+        ck(launch_sdf_pack_cells(ctx->grids[preshape].as<float>(), nx, ny, nz, ctx->cells[preshape].as<float4>(), ctx->st),
+           "pack sdf cells");
         // index box of the positive nodes -> gripper-frame box holding every cell that
         // has a positive corner (trilinear values outside it cannot be > 0)
         ctx->box.ensure(sizeof(int) * 6, "sdf box");
@@ -885,6 +890,7 @@ asicp_status asicp_set_gripper_sdf(asicp_ctx *ctx, int preshape, const float *S_
         sync_and_check_err(ctx, "set_gripper_sdf");
         SdfMeta m{};
         m.grid = ctx->grids[preshape].as<float>();
+        m.cells = ctx->cells[preshape].as<float4>();
         m.nx = nx; m.ny = ny; m.nz = nz;
         m.ox = org[0]; m.oy = org[1]; m.oz = org[2];
         m.voxel = voxel;

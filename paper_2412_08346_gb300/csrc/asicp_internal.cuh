@@ -35,6 +35,9 @@ enum : int { kDevOk = 0, kDevNonFinite = 1, kDevTimeout = 2 };
 
 struct SdfMeta {           // one preshape's grid
     const float *grid;     // nx*ny*nz values, x fastest, positive inside the gripper
+    const float4 *cells;   // the same values corner-packed: per cell (x fastest over the
+                           // (nx-1)(ny-1)(nz-1) cells) its 8 corners as two float4,
+                           // {c000, c100, c010, c110} {c001, c101, c011, c111} (index x, y, z)
     int nx, ny, nz;
     float ox, oy, oz;      // position of node (0,0,0)
     float voxel;
@@ -309,6 +312,8 @@ cudaError_t launch_gather_points(const float4 *R, const int *idx, int n, float4 
 cudaError_t launch_store_meta(ObjMeta *dst, const ObjMeta &v, cudaStream_t st);
 cudaError_t launch_set_theta(const float *theta7, int T, float *theta8, int *err, cudaStream_t st);
 cudaError_t launch_sdf_box(const float *grid, int nx, int ny, int nz, int *box6, cudaStream_t st);
+cudaError_t launch_sdf_pack_cells(const float *grid, int nx, int ny, int nz, float4 *cells, cudaStream_t st);
+size_t sdf_cells_bytes(int nx, int ny, int nz);
 cudaError_t launch_select(const Layout &L, const double *cost, const int *ncol, int *order, cudaStream_t st);
 cudaError_t launch_uniform_groups(int *part_grp, int *grp_off, int P, int K, cudaStream_t st);
 

@@ -14,7 +14,9 @@ constexpr int kColU = 4;          // collision points per thread per compaction 
 
 // Trilinear interpolation of a node-centred grid at gripper-frame point (x, y, z).
 // Returns false when the point lies outside the grid's node box (the grid covers
-// the gripper, so such a point is not inside it).
+// the gripper, so such a point is not inside it).  The eight corner values come
+// from the corner-packed copy of the grid: one 32-byte record per cell, read as
+// two float4 from a single 32-byte sector.
 __device__ __forceinline__ bool sdf_lookup(const SdfMeta &m, float x, float y, float z, float &val)
 {
     const float ux = __fdiv_rn(__fsub_rn(x, m.ox), m.voxel);
@@ -27,12 +29,10 @@ __device__ __forceinline__ bool sdf_lookup(const SdfMeta &m, float x, float y, f
     const int iy = min((int)floorf(uy), m.ny - 2);
     const int iz = min((int)floorf(uz), m.nz - 2);
     const float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
-    const float *g = m.grid + (size_t)ix + (size_t)m.nx * ((size_t)iy + (size_t)m.ny * iz);
-    const size_t sy = m.nx, sz = (size_t)m.nx * m.ny;
-    const float c000 = __ldg(g), c100 = __ldg(g + 1);
-    const float c010 = __ldg(g + sy), c110 = __ldg(g + sy + 1);
-    const float c001 = __ldg(g + sz), c101 = __ldg(g + sz + 1);
-    const float c011 = __ldg(g + sz + sy), c111 = __ldg(g + sz + sy + 1);
+    const float4 *cell = m.cells + 2 * ((size_t)ix + (size_t)(m.nx - 1) * ((size_t)iy + (size_t)(m.ny - 1) * iz));
+    const float4 z0 = __ldg(cell), z1 = __ldg(cell + 1);
+    const float c000 = z0.x, c100 = z0.y, c010 = z0.z, c110 = z0.w;
+    const float c001 = z1.x, c101 = z1.y, c011 = z1.z, c111 = z1.w;
     const float gx = 1.f - fx, gy = 1.f - fy, gz = 1.f - fz;
     val = gx * gy * gz * c000 + fx * gy * gz * c100 + gx * fy * gz * c010 + fx * fy * gz * c110 +
           gx * gy * fz * c001 + fx * gy * fz * c101 + gx * fy * fz * c011 + fx * fy * fz * c111;
@@ -482,6 +482,32 @@ __global__ void sdf_box_kernel(const float *grid, int nx, int ny, int nz, int *b
         if (lo[a] != INT_MAX) atomicMin(box6 + a, lo[a]);
         if (hi[a] != INT_MIN) atomicMax(box6 + 3 + a, hi[a]);
     }
+}
+
+// Corner-packed copy of a grid: cell (ix, iy, iz), x fastest over the
+// (nx-1)(ny-1)(nz-1) cells, gets its eight corner values as two float4.
+__global__ void sdf_pack_cells_kernel(const float *grid, int nx, int ny, int nz, float4 *cells)
+{
+    const long long nc = (long long)(nx - 1) * (ny - 1) * (nz - 1);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(c % (nx - 1)), iy = (int)((c / (nx - 1)) % (ny - 1)), iz = (int)(c / ((long long)(nx - 1) * (ny - 1)));
+        const float *g = grid + (size_t)ix + (size_t)nx * ((size_t)iy + (size_t)ny * iz);
+        const size_t sy = nx, sz = (size_t)nx * ny;
+        cells[2 * c] = make_float4(g[0], g[1], g[sy], g[sy + 1]);
+        cells[2 * c + 1] = make_float4(g[sz], g[sz + 1], g[sz + sy], g[sz + sy + 1]);
+    }
+}
+
+size_t sdf_cells_bytes(int nx, int ny, int nz) { return 2 * sizeof(float4) * (size_t)(nx - 1) * (ny - 1) * (nz - 1); }
+
+cudaError_t launch_sdf_pack_cells(const float *grid, int nx, int ny, int nz, float4 *cells, cudaStream_t st)
+{
+    const long long nc = (long long)(nx - 1) * (ny - 1) * (nz - 1);
+    long long blocks = (nc + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) return cudaSuccess;
+    sdf_pack_cells_kernel<<<(int)blocks, 256, 0, st>>>(grid, nx, ny, nz, cells);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sdf_box(const float *grid, int nx, int ny, int nz, int *box6, cudaStream_t st)
