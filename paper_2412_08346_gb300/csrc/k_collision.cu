@@ -269,9 +269,15 @@ __global__ void __launch_bounds__(kColThreads) collide_nn_kernel(const CollideAr
     __shared__ float s_smax[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int slots = Npad / 64;                 // point pairs per lane
+    // Two barriers per item.  Thread 0 takes the next item right after the first
+    // (its index is read at the top of the loop, after the second).  After the
+    // second barrier the transformed cloud and sC are no longer read, so the
+    // next item may overwrite them while slower threads still add this item's
+    // sums; those read only sRec, which the next item writes after its own
+    // first barrier.
+    if (threadIdx.x == 0) s_item = atomicAdd(&a.col_items[1], 1);
+    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&a.col_items[1], 1);
-        __syncthreads();
         const int item = s_item;
         if (item >= a.col_items[0]) break;
         const int pk = a.col_list[2 * item], chunk = a.col_list[2 * item + 1];
@@ -322,6 +328,7 @@ __global__ void __launch_bounds__(kColThreads) collide_nn_kernel(const CollideAr
         for (int o = 16; o > 0; o >>= 1) smax2 = fmaxf(smax2, __shfl_xor_sync(0xffffffffu, smax2, o));
         if (lane == 0) s_smax[warp] = smax2;
         __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(&a.col_items[1], 1);
         float sm2 = 0.f;
         for (int w8 = 0; w8 < kWarps; ++w8) sm2 = fmaxf(sm2, s_smax[w8]);
         const float smax = sqrtf(sm2) * 1.0001f;
@@ -434,7 +441,6 @@ __global__ void __launch_bounds__(kColThreads) collide_nn_kernel(const CollideAr
                 a.csums[(om.csum_base + (long long)(pk - om.pfirst) * om.chunks + chunk) * kColSums + e] =
                     (double)acc.hi + (double)acc.lo;
         }
-        __syncthreads();   // shared buffers and s_item are reused by the next item
     }
 }
 
