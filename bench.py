@@ -284,8 +284,8 @@ def run_gpu(args, rank, world, local_rank):
     roofline = roofline_entry(tc, pairs_per_launch, match_avg_s, exact_avg_s, pairs_rate, peak_alu, peak_fma,
                               ms, launches)
     # match, collide, collide_nn, finalize per pass (+ the exact choice with the tensor-core shape),
-    # Stein per SVGD pass, + init, reset, select, gather
-    launches_per_step = (5 if tc else 4) * (w.k_max + 1) + w.k_stein + 4
+    # Stein direction and Stein update per SVGD pass, + init, reset, select, gather
+    launches_per_step = (5 if tc else 4) * (w.k_max + 1) + 2 * w.k_stein + 4
 
     e2e = None
     if not args.no_e2e:

@@ -9,7 +9,9 @@
 namespace asicp {
 
 namespace {
-constexpr int kColThreads = 256;
+constexpr int kColThreads = 256;       // reverse matching
+constexpr int kTestThreads = 128;      // collision test: one CTA per particle, small enough that every
+                                       // particle of a paper-scale launch is resident at once
 constexpr int kColU = 4;          // collision points per thread per compaction round
 
 // Trilinear interpolation of a node-centred grid at gripper-frame point (x, y, z).
@@ -52,7 +54,7 @@ __device__ __forceinline__ void block_reduce_store(dfloat (&acc)[NV], double (*s
     __syncthreads();
     if (threadIdx.x < NV) {
         double s = 0.0;
-        for (int w = 0; w < kColThreads / 32; ++w) s += sred[w][threadIdx.x];
+        for (int w = 0; w < kTestThreads / 32; ++w) s += sred[w][threadIdx.x];
         out[threadIdx.x] = s;
     }
 }
@@ -68,10 +70,10 @@ __device__ __forceinline__ void block_reduce_store(dfloat (&acc)[NV], double (*s
 //     looked up in the preshape's SDF and kept when the value is > 0.  The
 //     colliding indices are compacted in ascending order (warp ballots and a
 //     block prefix), so results do not depend on scheduling.
-__global__ void __launch_bounds__(kColThreads) collide_kernel(const CollideArgs a)
+__global__ void __launch_bounds__(kTestThreads) collide_kernel(const CollideArgs a)
 {
-    __shared__ int swarp[kColU][kColThreads / 32];
-    __shared__ double sred[kColThreads / 32][kFwdSums];
+    __shared__ int swarp[kColU][kTestThreads / 32];
+    __shared__ double sred[kTestThreads / 32][kFwdSums];
     const int pk = blockIdx.x;
     const int grp = a.L.part_grp[pk], p = grp % a.L.P;
     const ObjMeta om = a.L.obj[grp / a.L.P];
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(kColThreads) collide_kernel(const CollideArgs 
         for (int c = 0; c < kFwdSums; ++c) acc[c] = dfloat{0.f, 0.f};
         const float4 *S = a.S + (size_t)p * N;
         const int *idx = a.nn_idx + (size_t)pk * N;
-        for (int i = threadIdx.x; i < N; i += kColThreads) {
+        for (int i = threadIdx.x; i < N; i += kTestThreads) {
             const float4 s = S[i];
             const float4 r = __ldg(om.R + idx[i]);
             const float rv[3] = {r.x, r.y, r.z}, sv[3] = {s.x, s.y, s.z};
@@ -108,17 +110,17 @@ __global__ void __launch_bounds__(kColThreads) collide_kernel(const CollideArgs 
     int count = 0;
     // kU points per thread per round (their loads and lookups overlap), one
     // compaction per round in ascending point order (round slot, warp, lane)
-    for (int c0 = 0; c0 < Mc; c0 += kColThreads * kColU) {
+    for (int c0 = 0; c0 < Mc; c0 += kTestThreads * kColU) {
         float4 v[kColU];
 #pragma unroll
         for (int u = 0; u < kColU; ++u) {
-            const int c = c0 + u * kColThreads + threadIdx.x;
+            const int c = c0 + u * kTestThreads + threadIdx.x;
             v[u] = c < Mc ? om.C[c] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         bool hit[kColU];
 #pragma unroll
         for (int u = 0; u < kColU; ++u) {
-            const int c = c0 + u * kColThreads + threadIdx.x;
+            const int c = c0 + u * kTestThreads + threadIdx.x;
             hit[u] = false;
             if (c < Mc) {
                 const float dx = __fsub_rn(v[u].x, tx), dy = __fsub_rn(v[u].y, ty), dz = __fsub_rn(v[u].z, tz);
@@ -144,13 +146,13 @@ __global__ void __launch_bounds__(kColThreads) collide_kernel(const CollideArgs 
         for (int u = 0; u < kColU; ++u) {
             int mine = 0;
 #pragma unroll
-            for (int w = 0; w < kColThreads / 32; ++w) {
+            for (int w = 0; w < kTestThreads / 32; ++w) {
                 const int n = swarp[u][w];
                 mine += w < warp ? n : 0;
                 tot += n;
             }
             if (hit[u])
-                colidx[count + before + mine + __popc(bal[u] & ((1u << lane) - 1u))] = c0 + u * kColThreads + threadIdx.x;
+                colidx[count + before + mine + __popc(bal[u] & ((1u << lane) - 1u))] = c0 + u * kTestThreads + threadIdx.x;
             before = tot;
         }
         count += tot;
@@ -446,7 +448,7 @@ __global__ void __launch_bounds__(kColThreads) collide_nn_kernel(const CollideAr
 
 cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st)
 {
-    collide_kernel<<<a.L.T, kColThreads, 0, st>>>(a);
+    collide_kernel<<<a.L.T, kTestThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -156,9 +156,14 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(const Update
     }
 }
 
-// SVGD phase, one CTA of kSteinThreads per preshape; each particle i is served
-// by T = kSteinThreads / K' threads (K' = K rounded up to a power of two), so a
-// preshape of 256 particles still fills 32 warps:
+// SVGD phase, kSteinSplit CTAs of kSteinThreads per preshape.  Every CTA of a
+// preshape computes the bandwidth (the same deterministic selection), then the
+// Stein direction of its share of ceil(K / kSteinSplit) particles; the poses are
+// updated by stein_update_kernel afterwards, because every CTA reads all poses of
+// its preshape.  For the bandwidth each particle i is served by T = kSteinThreads
+// / K' threads (K' = K rounded up to a power of two); for the direction each
+// particle of the share by T' = kSteinThreads / K'' threads (K'' = the share
+// rounded up), at most a warp:
 //  - bandwidth: exact lower median of |t_i - t_j|^2 (i < j): the value range is
 //    narrowed by histograms over linear bins (usually one pass) until the bin
 //    holding the median has at most kSelCand values, which are then ranked
@@ -166,10 +171,12 @@ __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(const Update
 //    takes partners i + o (mod K), o = 1 + sub + T m <= K/2, the o = K/2 pairs
 //    only from i < K/2 when K is even);
 //  - Stein direction of Eq. 8 read as the mean of Eq. 6 with the kernels of
-//    Eqs. 9-10 per block: thread (i, sub) sums over j = sub, sub + T, ..., the T
-//    partial sums of particle i (adjacent lanes) are added by shuffles;
-//  - the update of Eq. 7.
+//    Eqs. 9-10 per block: thread (i, sub) sums over j = sub, sub + T', ..., the T'
+//    partial sums of particle i (adjacent lanes) are added by shuffles, and
+//    written to phi;
+//  - the update of Eq. 7 (stein_update_kernel).
 constexpr int kSteinThreads = 1024;
+constexpr int kSteinSplit = 8;         // CTAs per preshape
 constexpr int kSelBins = 1024;         // histogram bins per narrowing pass of the median selection
 constexpr int kSelCand = 1024;         // values ranked exactly at the end
 
@@ -186,8 +193,10 @@ __global__ void __launch_bounds__(kSteinThreads) stein_kernel(const UpdateArgs a
     __shared__ unsigned s_lo, s_hi, s_rank, s_n, s_bin, s_before, s_fill;
     __shared__ float s_h;
 
-    const int grp = blockIdx.x, base = a.L.grp_off[grp], K = a.L.grp_off[grp + 1] - base;
-    if (K <= 0) return;
+    const int grp = blockIdx.x / kSteinSplit, part = blockIdx.x % kSteinSplit;
+    const int base = a.L.grp_off[grp], K = a.L.grp_off[grp + 1] - base;
+    const int share = (K + kSteinSplit - 1) / kSteinSplit, i0 = part * share;
+    if (K <= 0 || i0 >= K) return;      // (whole CTAs; no CTA waits on another)
     int Kp = 1;
     while (Kp < K) Kp <<= 1;
     const int T = min(kSteinThreads / Kp, 32);        // threads per particle: a power of two <= a warp
@@ -329,13 +338,19 @@ __global__ void __launch_bounds__(kSteinThreads) stein_kernel(const UpdateArgs a
         __syncthreads();
         h = s_h;
     }
-    if (threadIdx.x == 0) a.h[grp] = h;
+    if (part == 0 && threadIdx.x == 0) a.h[grp] = h;
 
-    const float4 ti = sT[active ? i : 0], qi = sQ[active ? i : 0];
+    // Stein direction of particles [i0, min(K, i0 + share)) of this preshape
+    int Sp = 1;
+    while (Sp < share) Sp <<= 1;
+    const int T2 = min(kSteinThreads / Sp, 32);
+    const int i2 = i0 + threadIdx.x / T2, sub2 = threadIdx.x % T2;
+    const bool active2 = threadIdx.x / T2 < share && i2 < K;
+    const float4 ti = sT[active2 ? i2 : 0], qi = sQ[active2 ? i2 : 0];
     const float inv_h = 1.f / h, two_h = 2.f / h;
     float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};     // t (3), q (4), sign count
-    if (active) {
-        for (int jj = sub; jj < K; jj += T) {
+    if (active2) {
+        for (int jj = sub2; jj < K; jj += T2) {
             const float4 tj = sT[jj], qj = sQ[jj], dt = sDt[jj], dq = sDq[jj];
             const float ex = ti.x - tj.x, ey = ti.y - tj.y, ez = ti.z - tj.z;
             const float kt = expf(-(ex * ex + ey * ey + ez * ez) * inv_h);
@@ -347,12 +362,12 @@ __global__ void __launch_bounds__(kSteinThreads) stein_kernel(const UpdateArgs a
             f[7] += c < 0.f ? -1.f : 1.f;
         }
     }
-    // the T threads of a particle are adjacent lanes of one warp (T is a power of two <= 32)
-    for (int o = 1; o < T; o <<= 1)
+    // the T2 threads of a particle are adjacent lanes of one warp (T2 is a power of two <= 32)
+    for (int o = 1; o < T2; o <<= 1)
 #pragma unroll
         for (int u = 0; u < 8; ++u) f[u] += __shfl_xor_sync(0xffffffffu, f[u], o);
-    if (active && sub == 0) {
-        const size_t pk = (size_t)base + i;
+    if (active2 && sub2 == 0) {
+        const size_t pk = (size_t)base + i2;
         const float invK = 1.f / (float)K;
         float g[7] = {f[0] * invK, f[1] * invK, f[2] * invK,
                       (f[3] + f[7] * qi.x) * invK, (f[4] + f[7] * qi.y) * invK,
@@ -360,16 +375,26 @@ __global__ void __launch_bounds__(kSteinThreads) stein_kernel(const UpdateArgs a
         // tangent projection at q_i (removes the radial kernel-gradient term)
         const float d = g[3] * qi.x + g[4] * qi.y + g[5] * qi.z + g[6] * qi.w;
         g[3] -= d * qi.x; g[4] -= d * qi.y; g[5] -= d * qi.z; g[6] -= d * qi.w;
-        float *th = a.theta + pk * 8;
         for (int u = 0; u < 7; ++u) a.phi[pk * 8 + u] = g[u];
-        const double es = a.eta_svgd;
-        double nq[4] = {qi.x + es * g[3], qi.y + es * g[4], qi.z + es * g[5], qi.w + es * g[6]};
-        const double nn = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
-        th[0] = (float)(ti.x + es * g[0]);
-        th[1] = (float)(ti.y + es * g[1]);
-        th[2] = (float)(ti.z + es * g[2]);
-        for (int u = 0; u < 4; ++u) th[3 + u] = (float)(nq[u] / nn);
     }
+}
+
+// The SVGD update of Eq. 7 from the Stein direction: t += eta phi_t, q <-
+// normalise(q + eta phi_q) (phi_q is tangent at q), one thread per particle.
+__global__ void stein_update_kernel(const UpdateArgs a)
+{
+    const int pk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pk >= a.L.T) return;
+    float *th = a.theta + (size_t)pk * 8;
+    const float *g = a.phi + (size_t)pk * 8;
+    const float tx = th[0], ty = th[1], tz = th[2], qw = th[3], qx = th[4], qy = th[5], qz = th[6];
+    const double es = a.eta_svgd;
+    double nq[4] = {qw + es * g[3], qx + es * g[4], qy + es * g[5], qz + es * g[6]};
+    const double nn = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
+    th[0] = (float)(tx + es * g[0]);
+    th[1] = (float)(ty + es * g[1]);
+    th[2] = (float)(tz + es * g[2]);
+    for (int u = 0; u < 4; ++u) th[3 + u] = (float)(nq[u] / nn);
 }
 
 cudaError_t init_update_attributes()
@@ -387,7 +412,10 @@ cudaError_t launch_finalize(const UpdateArgs &a, cudaStream_t st)
 cudaError_t launch_stein(const UpdateArgs &a, cudaStream_t st)
 {
     const size_t smem = sizeof(float4) * 4 * (size_t)kMaxK;
-    stein_kernel<<<a.L.G, kSteinThreads, smem, st>>>(a);
+    stein_kernel<<<a.L.G * kSteinSplit, kSteinThreads, smem, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    stein_update_kernel<<<(a.L.T + 255) / 256, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
