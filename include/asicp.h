@@ -162,7 +162,11 @@ asicp_status asicp_destroy(asicp_ctx *ctx);
 
 /* Object cloud R (M x 3) used for matching (Eq. 1, the reference cloud R of
  * Section III-A) and collision cloud C (Mc x 3; object and table, Section IV-A).
- * C_xyz = NULL uses C = R.  Computes CoM = centroid of R (Algorithm 1).
+ * C_xyz = NULL uses C = R.  Computes CoM = centroid of R (Algorithm 1).  A new
+ * object with the same M and Mc as the previous one keeps the context's layout,
+ * its poses and its captured iteration loop; other sizes need new poses
+ * (asicp_set_state or asicp_run) before asicp_step.  Mini-batches set with
+ * asicp_set_minibatch are dropped.
  * Errors: INVALID_ARG (NULL R, M < 1, Mc < 1 when C is given, non-finite value). */
 asicp_status asicp_set_object(asicp_ctx *ctx, const float *R_xyz, int M, const float *C_xyz, int Mc);
 
@@ -195,7 +199,8 @@ asicp_status asicp_set_state(asicp_ctx *ctx, const float *theta, int k);
 /* One iteration k (0 <= k < k_max) of Algorithm 1 for all preshapes and
  * particles: transform, match, cost/gradient, collision test and collision
  * gradient, then the SVGD update (k < k_stein, Eqs. 7-11) or the SGD-ICP update
- * (Eq. 3).  Errors: STATE (inputs or poses not set), INVALID_ARG (k), CUDA. */
+ * (Eq. 3).  Errors: STATE (inputs or poses not set, or sizes changed since the
+ * poses were set), INVALID_ARG (k), CUDA. */
 asicp_status asicp_step(asicp_ctx *ctx, int k);
 
 /* Full optimisation of every object's grasp set: initial poses theta0 (T*7,

@@ -665,8 +665,14 @@ void set_object_impl(asicp_ctx *ctx, int o, const float *R_xyz, int M, const flo
     if (C_xyz && Mc < 1) fail(ASICP_ERR_INVALID_ARG, "set_object: Mc must be >= 1 when C is given");
     ObjBufs &b = ctx->objs[o];
     const int mc = C_xyz ? Mc : M;
-    ctx->mb_off.clear();          // mini-batches index the previous cloud
-    ++ctx->mb_version;
+    if (!ctx->mb_off.empty()) {   // mini-batches index the previous cloud
+        ctx->mb_off.clear();
+        ++ctx->mb_version;
+    }
+    // what the layout (object table, work plan) and the captured loop depend on
+    const bool was_set = b.set;
+    const void *was[4] = {b.R.p, b.Rx.p, b.Rt.p, b.C.p};
+    const int was_M = b.M, was_Mc = b.Mc, was_Mpad = b.Mpad;
     b.set = false;
     ctx->run_done = false;
     ctx->stage.ensure(sizeof(float) * 3 * (size_t)(M > mc ? M : mc), "staging");
@@ -691,7 +697,11 @@ void set_object_impl(asicp_ctx *ctx, int o, const float *R_xyz, int M, const flo
     b.Mpad = Mpad;
     b.Mc = mc;
     b.set = true;
-    ctx->layout_dirty = true;
+    // a new object of the same sizes in the same buffers keeps the layout, the poses
+    // and the captured loop (whose kernels read the object's data at replay)
+    if (!was_set || M != was_M || mc != was_Mc || Mpad != was_Mpad || b.R.p != was[0] || b.Rx.p != was[1] ||
+        b.Rt.p != was[2] || b.C.p != was[3])
+        ctx->layout_dirty = true;
 }
 
 }  // namespace

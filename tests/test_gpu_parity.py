@@ -315,6 +315,63 @@ def test_graph_replay_equals_direct_steps(stream):
     assert np.array_equal(a, c)
 
 
+@pytest.mark.parametrize("shape", [0, asicp.FWD_SHAPES - 1])
+def test_new_object_of_the_same_size_reuses_the_context(stream, shape):
+    """A context that already ran on one object, given a second object with the same point count
+    (same layout, same captured loop, whose kernels read the new object's data at replay), gives
+    exactly the results of a fresh context on that object; stepping right after the new object
+    continues from the kept poses; an object of another size needs new poses before a step."""
+    import copy
+    import oracle
+    w1 = synth.custom_case(P=2, K=16, N=300, M=2500, grid=24, k_max=6, seed=43, k_stein=3)
+    w2 = copy.copy(w1)
+    w2.objects = [synth.partial_object(2500, 4343)]
+    th0 = np.tile(oracle.fibonacci_init(w1.K, np.zeros(3), 0.08), (2, 1)).astype(np.float32)
+
+    def outputs(ctx):
+        best = np.zeros(8 * 7, np.float32)
+        cost = np.zeros(8, np.float32)
+        pre = np.zeros(8, np.int32)
+        asicp.asicp_best_grasps(ctx, 8, best, cost, pre)
+        return tl.read_theta(ctx, 32), best, cost, pre
+
+    ctx = _ctx(w1, stream, debug=False, fwd_shape=shape)
+    try:
+        keep = tl.upload(ctx, w1)
+        asicp.asicp_run(ctx, th0)
+        R2 = torch.from_numpy(np.ascontiguousarray(w2.objects[0].points)).cuda()
+        asicp.asicp_set_object(ctx, R2)
+        asicp.asicp_run(ctx, th0)
+        reused = outputs(ctx)
+        asicp.asicp_set_state(ctx, th0, 0)
+        asicp.asicp_step(ctx, 0)
+        stepped = tl.read_theta(ctx, 32)
+        asicp.asicp_set_object(ctx, R2)         # same size: the poses stay set
+        asicp.asicp_step(ctx, 1)
+        R3 = torch.from_numpy(np.ascontiguousarray(synth.partial_object(2600, 4444).points)).cuda()
+        asicp.asicp_set_object(ctx, R3)         # another size: new poses needed
+        with pytest.raises(asicp.AsicpError) as e:
+            asicp.asicp_step(ctx, 2)
+        assert e.value.status == asicp.ASICP_ERR_STATE
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
+    ctx = _ctx(w2, stream, debug=False, fwd_shape=shape)
+    try:
+        keep = tl.upload(ctx, w2)
+        asicp.asicp_run(ctx, th0)
+        fresh = outputs(ctx)
+        asicp.asicp_set_state(ctx, th0, 0)
+        asicp.asicp_step(ctx, 0)
+        fresh_step = tl.read_theta(ctx, 32)
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
+    for a, b in zip(reused, fresh):
+        assert np.array_equal(a, b)
+    assert np.array_equal(stepped, fresh_step)
+
+
 def test_kernel_times_from_graph_replays(stream):
     """With profiling on, asicp_run's graph replays report one timed launch per kernel and pass; the
     tensor-core shape adds one exact-choice launch per matching pass."""
