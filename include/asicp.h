@@ -230,9 +230,11 @@ asicp_status asicp_get_state(asicp_ctx *ctx, const asicp_state_view *view);
  * path's kernels since the last reset.  ms[ASICP_KERNEL_KINDS] / launches[...]
  * order: forward matching (screening; with the float32 shapes also the exact
  * choice), collision test (with the matching sums), reverse matching, finalize
- * (cost, gradient, convergence, SGD step), Stein (SVGD step), and the exact
- * choice of the tensor-core shape (no launches with the float32 shapes).  reset = 1
- * clears the counters after reading.  Errors: STATE (profile off). */
+ * (cost, gradient, convergence, SGD step), Stein (SVGD step: the Stein direction
+ * and the update kernel, timed and counted together as one launch per pass), and
+ * the exact choice of the tensor-core shape (no launches with the float32
+ * shapes).  reset = 1 clears the counters after reading.  Errors: STATE (profile
+ * off). */
 #define ASICP_KERNEL_KINDS 6
 asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[ASICP_KERNEL_KINDS], long long launches[ASICP_KERNEL_KINDS],
                                 int reset);
