@@ -12,6 +12,13 @@
  * (Eqs. 6, 8-10), SVGD / SGD-ICP updates (Eqs. 7, 3) and the final argmin
  * (Alg. 1).  Where the paper is silent or ambiguous the reading taken is named
  * at the point of use.
+ *
+ * The paper prints no worked example, intermediate value or trajectory, so the
+ * pins in tests/test_oracle_pins.py are closed forms, invariants, library
+ * routines and brute force on tiny inputs; the final poses of a whole run are
+ * pinned only through such properties (rigid-motion equivariance of whole
+ * iterations, recovery of a known rigid transform by SGD-ICP, one SVGD step with
+ * K = 1 equal to one SGD step), not against values from the paper.
  */
 #include "asicp_oracle.h"
 
