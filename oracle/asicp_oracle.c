@@ -448,6 +448,67 @@ void orc_quarter_init(int K, const double com[3], double radius, double *theta)
     }
 }
 
+/* Distances to the nearest and second-nearest of m reference points (plain
+ * definition of Eq. 1's minimum, extended to the runner-up). */
+static void nearest_two(const double q[3], const double *ref, int m, double *d1, double *d2)
+{
+    double b1 = INFINITY, b2 = INFINITY;
+    for (int r = 0; r < m; ++r) {
+        double dx = q[0] - ref[r * 3 + 0], dy = q[1] - ref[r * 3 + 1], dz = q[2] - ref[r * 3 + 2];
+        double d = dx * dx + dy * dy + dz * dz;
+        if (d < b1) { b2 = b1; b1 = d; }
+        else if (d < b2) b2 = d;
+    }
+    *d1 = sqrt(b1);
+    *d2 = sqrt(b2);
+}
+
+/* How far the discrete decisions of one step at pose theta are from changing:
+ * the smallest of (a) over gripper points, the distance to the second-nearest
+ * object point minus the distance to the nearest (Eq. 1), (b) over collision
+ * points inside the grid, |SDF value| (the collision test of Eq. 12 flips at 0),
+ * (c) over colliding points, the gap between their nearest and second-nearest
+ * gripper points (Eq. 18).  All in metres: moving the gripper points, or a
+ * point against the SDF (|grad SDF| <= 1 for a distance field), by less than
+ * half of it changes none of them.  Used by the tests to tell apart the
+ * particles whose trajectory may fork under rounding.  Reported, not used by
+ * the method. */
+double orc_decision_margin(const orc_problem *pb, int p, const double theta[7])
+{
+    const int N = pb->N;
+    const double *S = pb->S + (size_t)p * N * 3;
+    double Rm[9];
+    orc_rotation(theta + 3, Rm);
+    double *Sp = (double *)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+    for (int i = 0; i < N; ++i) transform(Rm, theta, S + i * 3, Sp + i * 3);
+    double margin = INFINITY;
+    for (int i = 0; i < N; ++i) {
+        double d1, d2;
+        nearest_two(Sp + i * 3, pb->R, pb->M, &d1, &d2);
+        if (d2 - d1 < margin) margin = d2 - d1;
+    }
+    const double *grid = pb->sdf + pb->sdf_off[p];
+    const int *dims = pb->sdf_dims + 3 * p;
+    const double *org = pb->sdf_origin + 3 * p;
+    for (int c = 0; c < pb->Mc; ++c) {
+        const double *cp = pb->C + (size_t)c * 3;
+        double d[3] = {cp[0] - theta[0], cp[1] - theta[1], cp[2] - theta[2]};
+        double x[3];
+        for (int a = 0; a < 3; ++a) x[a] = Rm[0 * 3 + a] * d[0] + Rm[1 * 3 + a] * d[1] + Rm[2 * 3 + a] * d[2];
+        int inside;
+        double v = orc_trilinear(grid, dims, org, pb->sdf_voxel[p], x, &inside);
+        if (!inside) continue;
+        if (fabs(v) < margin) margin = fabs(v);
+        if (v > 0.0) {
+            double d1, d2;
+            nearest_two(cp, Sp, N, &d1, &d2);
+            if (d2 - d1 < margin) margin = d2 - d1;
+        }
+    }
+    free(Sp);
+    return margin;
+}
+
 static void particle_cost_grad(const orc_problem *pb, const orc_state *st, int p, int j,
                                double *cost, double g[7], int *ncol)
 {
@@ -462,6 +523,7 @@ static void particle_cost_grad(const orc_problem *pb, const orc_state *st, int p
         orc_collision_cost_grad(pb, p, th, list, n, cost, g, st->col_nn ? st->col_nn + pj * pb->Mc : NULL);
     *ncol = n;
     if (!st->col_list) free(list);
+    if (st->margin) st->margin[pj] = orc_decision_margin(pb, p, th);
 }
 
 /* One iteration k of Algorithm 1 for every preshape and particle. */

@@ -55,6 +55,8 @@ typedef struct {
     int *col_list;            /* P*K*Mc colliding point indices, ascending (nullable) */
     int *col_nn;              /* P*K*Mc reverse-NN gripper index per colliding point (nullable) */
     double *sdf_val;          /* P*K*Mc interpolated SDF at every C point (nullable) */
+    double *margin;           /* P*K    decision margin of the step (nullable), see
+                                 orc_decision_margin                               */
 } orc_state;
 
 void orc_rotation(const double q[4], double Rm[9]);
@@ -84,6 +86,7 @@ void orc_centroid(const double *X, int n, double c[3]);
 void orc_step(const orc_problem *pb, const orc_schedule *sc, orc_state *st, int k, int nthreads);
 void orc_evaluate(const orc_problem *pb, orc_state *st, int nthreads);
 void orc_select(const double *cost, const int *ncol, int total, int topk, int *order);
+double orc_decision_margin(const orc_problem *pb, int p, const double theta[7]);
 
 #ifdef __cplusplus
 }

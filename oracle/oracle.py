@@ -50,7 +50,7 @@ class _Schedule(C.Structure):
 class _State(C.Structure):
     _fields_ = [("theta", _dp), ("cost", _dp), ("grad", _dp), ("phi", _dp), ("ncol", _ip),
                 ("frozen", _ip), ("prev_cost", _dp), ("h", _dp), ("nn_idx", _ip), ("col_list", _ip),
-                ("col_nn", _ip), ("sdf_val", _dp)]
+                ("col_nn", _ip), ("sdf_val", _dp), ("margin", _dp)]
 
 
 def _load():
@@ -81,6 +81,8 @@ def _load():
         lib.orc_step.argtypes = [C.POINTER(_Problem), C.POINTER(_Schedule), C.POINTER(_State), C.c_int, C.c_int]
         lib.orc_evaluate.argtypes = [C.POINTER(_Problem), C.POINTER(_State), C.c_int]
         lib.orc_select.argtypes = [_dp, _ip, C.c_int, C.c_int, _ip]
+        lib.orc_decision_margin.argtypes = [C.POINTER(_Problem), C.c_int, _dp]
+        lib.orc_decision_margin.restype = C.c_double
         _lib = lib
     return _lib
 
@@ -272,7 +274,12 @@ class Oracle:
         return cost.value, g, nn_[:len(lst)].copy()
 
     # ---- whole iterations
-    def new_state(self, theta, debug=False):
+    def decision_margin(self, p, theta):
+        """Smallest gap (metres) by which the step's discrete decisions at theta could change."""
+        th, tp = _d(theta)
+        return _load().orc_decision_margin(C.byref(self._pb), int(p), tp)
+
+    def new_state(self, theta, debug=False, margin=False):
         P, K = self.P, self.K
         st = {
             "theta": np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(P, K, 7).copy()),
@@ -285,6 +292,8 @@ class Oracle:
             st["col_list"] = np.zeros((P, K, len(self.Cc)), np.int32)
             st["col_nn"] = np.zeros((P, K, len(self.Cc)), np.int32)
             st["sdf_val"] = np.zeros((P, K, len(self.Cc)))
+        if margin:
+            st["margin"] = np.zeros((P, K))
         return st
 
     def _cstate(self, st):
@@ -294,7 +303,8 @@ class Oracle:
         def ip(k):
             return st[k].ctypes.data_as(_ip) if k in st else None
         return _State(dp("theta"), dp("cost"), dp("grad"), dp("phi"), ip("ncol"), ip("frozen"),
-                      dp("prev_cost"), dp("h"), ip("nn_idx"), ip("col_list"), ip("col_nn"), dp("sdf_val"))
+                      dp("prev_cost"), dp("h"), ip("nn_idx"), ip("col_list"), ip("col_nn"), dp("sdf_val"),
+                      dp("margin"))
 
     @staticmethod
     def schedule(k_max, k_stein, schedule=0, C_cycles=5.0, p_exp=2.0, g0=0.1, g1=1.0, eta_sgd=1.0,

@@ -593,3 +593,165 @@ def test_match_cost_with_a_given_com():
     ref = (d2[np.arange(30), nn].sum() + ((Rm @ tcp + th[:3] - com) ** 2).sum()) / 30
     cost, _ = o.match_terms(0, th, nn.astype(np.int32))
     assert abs(cost - ref) <= 1e-12 * ref
+
+
+# ------------------------------------------------------------------ convergence (Table I, Section IV-D)
+CONV_TOL = 2e-4            # Table I: convergence criterion 0.02 %
+
+
+def _three_particles(oracle_mod, g):
+    orc = _tiny_problem(oracle_mod, g, K=3)
+    th = np.stack([np.concatenate([g.uniform(-0.03, 0.03, 3) + [0, 0, 0.2], rand_quat(g)]) for _ in range(3)])
+    return orc, th
+
+
+def test_convergence_threshold_freezes_below_and_not_above(oracle_mod):
+    """SGD phase: a particle whose relative cost change |L_k - L_(k-1)| / L_(k-1) is just below the
+    criterion stops (its pose is kept exactly), one just above takes the full SGD step; the
+    change counts in either direction.  L_k is computed independently by the per-particle cost."""
+    g = np.random.default_rng(40)
+    orc, th = _three_particles(oracle_mod, g)
+    L = np.array([orc.match_cost_grad(0, th[j])[0] for j in range(3)])
+    grads = np.stack([orc.match_cost_grad(0, th[j])[1] for j in range(3)])
+    for sign in (1.0, -1.0):
+        # relative changes 0.9, 1.1 and 0.5 x the criterion (prev above or below L)
+        rel = np.array([0.9, 1.1, 0.5]) * CONV_TOL
+        prev = L / (1.0 + sign * rel)
+        st = orc.new_state(th[None])
+        st["prev_cost"][0] = prev
+        orc.step(st, orc.schedule(k_max=4, k_stein=1, N=orc.N, conv_tol=CONV_TOL), 2)
+        assert st["frozen"][0].tolist() == [1, 0, 1]
+        assert np.array_equal(st["theta"][0, 0], th[0]) and np.array_equal(st["theta"][0, 2], th[2])
+        new = th[1] - grads[1]
+        new[3:] /= np.linalg.norm(new[3:])
+        assert np.allclose(st["theta"][0, 1], new, atol=1e-15)
+        assert np.array_equal(st["prev_cost"][0], L)       # the next step compares against this cost
+    # conv_tol < 0 switches freezing off: every particle steps
+    st = orc.new_state(th[None])
+    st["prev_cost"][0] = L
+    orc.step(st, orc.schedule(k_max=4, k_stein=1, N=orc.N, conv_tol=-1.0), 2)
+    assert st["frozen"][0].tolist() == [0, 0, 0]
+    assert not np.array_equal(st["theta"][0, 0], th[0])
+
+
+def test_no_freeze_in_the_svgd_phase_or_without_a_previous_cost(oracle_mod):
+    """Nothing freezes while k < k_stein (the SVGD update moves every particle, Eq. 7), nor at the
+    first step of a run, where no previous cost exists (prev_cost < 0)."""
+    g = np.random.default_rng(41)
+    orc, th = _three_particles(oracle_mod, g)
+    L = np.array([orc.match_cost_grad(0, th[j])[0] for j in range(3)])
+    st = orc.new_state(th[None])
+    st["prev_cost"][0] = L                       # zero relative change
+    orc.step(st, orc.schedule(k_max=4, k_stein=2, N=orc.N, conv_tol=CONV_TOL), 1)
+    assert st["frozen"][0].tolist() == [0, 0, 0]
+    assert all(not np.array_equal(st["theta"][0, j], th[j]) for j in range(3))
+    st = orc.new_state(th[None])                 # prev_cost = -1
+    orc.step(st, orc.schedule(k_max=4, k_stein=0, N=orc.N, conv_tol=1.0), 0)
+    assert st["frozen"][0].tolist() == [0, 0, 0]
+
+
+def test_collision_unfreezes_a_particle(oracle_mod):
+    """Section IV-D: a frozen particle whose gripper collides is set back to unconverged and takes the
+    collision step (Eq. 18), even with no change in its cost."""
+    pts = [[0.001, 0.001, -0.005], [0.0, 0.0, 0.05]]
+    orc, S = _palm_problem(oracle_mod, pts)
+    th = np.array([0, 0, 0, 1.0, 0, 0, 0])
+    lst, _ = orc.collision_points(0, th)
+    Lc, gc, _ = orc.collision_cost_grad(0, th, lst)
+    st = orc.new_state(th[None, None])
+    st["frozen"][0, 0] = 1
+    st["prev_cost"][0, 0] = Lc
+    orc.step(st, orc.schedule(k_max=2, k_stein=0, N=orc.N, conv_tol=CONV_TOL), 1)
+    assert st["ncol"][0, 0] == 1 and st["frozen"][0, 0] == 0
+    new = th - gc
+    new[3:] /= np.linalg.norm(new[3:])
+    assert np.allclose(st["theta"][0, 0], new, atol=1e-15)
+    # without the collision the same frozen particle stays where it is
+    orc2, _ = _palm_problem(oracle_mod, [[0.0, 0.0, 0.05]])
+    L2 = orc2.match_cost_grad(0, th)[0]
+    st = orc2.new_state(th[None, None])
+    st["frozen"][0, 0] = 1
+    st["prev_cost"][0, 0] = L2
+    orc2.step(st, orc2.schedule(k_max=2, k_stein=0, N=orc2.N, conv_tol=CONV_TOL), 1)
+    assert st["frozen"][0, 0] == 1 and np.array_equal(st["theta"][0, 0], th)
+
+
+def test_freezing_run_matches_the_free_run_up_to_the_criterion(oracle_mod):
+    """SGD-ICP on the known-transform problem, once with freezing and once without: the two runs are
+    identical up to the first iteration k* >= 1 at which the free run's cost sequence meets the
+    criterion; from k* on the frozen run's pose and cost no longer change."""
+    g = np.random.default_rng(12)
+    N = 20
+    S = g.uniform(-0.5, 0.5, (N, 3))
+    R_true = Rotation.from_rotvec([0.3, -0.2, 0.1]).as_matrix()
+    t_true = np.array([0.1, 0.2, -0.1])
+    obj = S @ R_true.T + t_true + g.normal(0, 1e-3, (N, 3))     # noisy: the cost settles above 0
+    grid = -np.ones((4, 4, 4))
+    orc = oracle_mod.Oracle(S[None], [(grid, np.full(3, -5.0), 10.0 / 3)], obj, K=1, w_com=0.0)
+    xyzw = Rotation.from_matrix(R_true).as_quat()
+    q0 = np.array([xyzw[3], xyzw[0], xyzw[1], xyzw[2]]) + np.array([0.0, 0.02, -0.01, 0.015])
+    th0 = np.concatenate([t_true + [0.03, -0.02, 0.01], q0 / np.linalg.norm(q0)])
+    n_it = 60
+    free, frz = orc.new_state(th0[None, None]), orc.new_state(th0[None, None])
+    sf, sz = (orc.schedule(k_max=n_it, k_stein=0, N=N, conv_tol=c) for c in (-1.0, CONV_TOL))
+    costs, thetas_free, thetas_frz, frozen = [], [], [], []
+    for k in range(n_it):
+        orc.step(free, sf, k)
+        orc.step(frz, sz, k)
+        costs.append(free["cost"][0, 0])
+        thetas_free.append(free["theta"][0, 0].copy())
+        thetas_frz.append(frz["theta"][0, 0].copy())
+        frozen.append(int(frz["frozen"][0, 0]))
+    kstar = next(k for k in range(1, n_it) if abs(costs[k] - costs[k - 1]) <= CONV_TOL * costs[k - 1])
+    assert 1 <= kstar < n_it - 5
+    assert frozen[:kstar] == [0] * kstar and frozen[kstar:] == [1] * (n_it - kstar)
+    for k in range(kstar):
+        assert np.array_equal(thetas_frz[k], thetas_free[k])
+    for k in range(kstar, n_it):
+        assert np.array_equal(thetas_frz[k], thetas_free[kstar - 1])
+
+
+def test_convergence_criterion_includes_equality(oracle_mod):
+    """Reading of Table I's 0.02 %: a relative change equal to the criterion counts as converged
+    (|L_k - L_(k-1)| <= tol L_(k-1)).  With tol = 0 only an unchanged cost meets it: equality
+    freezes, the smallest change in either direction does not."""
+    g = np.random.default_rng(42)
+    orc, th = _three_particles(oracle_mod, g)
+    L = np.array([orc.match_cost_grad(0, th[j])[0] for j in range(3)])
+    st = orc.new_state(th[None])
+    st["prev_cost"][0] = [L[0], np.nextafter(L[1], np.inf), np.nextafter(L[2], -np.inf)]
+    orc.step(st, orc.schedule(k_max=4, k_stein=1, N=orc.N, conv_tol=0.0), 2)
+    assert st["frozen"][0].tolist() == [1, 0, 0]
+
+
+def test_decision_margin_brute_force(oracle_mod):
+    """The decision margin the free-running tests use to tell near-tie particles apart: the smallest
+    of the nearest-vs-runner-up distance gaps of every gripper point (Eq. 1), |SDF| of every
+    collision point inside the grid (Eq. 12) and the gaps of the colliding points' reverse matches
+    (Eq. 18), against numpy on a palm problem with a colliding point and a planted exact tie."""
+    pts = np.array([[0.001, 0.001, -0.005], [0.0, 0.0, 0.05], [0.03, -0.02, 0.01]])
+    orc, S = _palm_problem(oracle_mod, pts)
+    for th in (np.array([0, 0, 0, 1.0, 0, 0, 0]), np.array([0.002, -0.001, 0.003, 0.99, 0.1, 0.0, 0.05])):
+        th = th.copy()
+        th[3:] /= np.linalg.norm(th[3:])
+        R = Rotation.from_quat([th[4], th[5], th[6], th[3]]).as_matrix()
+        Sp = S.astype(np.float64) @ R.T + th[:3]
+        d = np.sqrt(((Sp[:, None, :] - orc.R[None]) ** 2).sum(-1))
+        ds = np.sort(d, axis=1)
+        m = (ds[:, 1] - ds[:, 0]).min()
+        lst, vals = orc.collision_points(0, th)
+        xg = (pts - th[:3]) @ R                        # collision points in the gripper frame
+        sdf, origin, voxel = synth.sdf_grid(0.0, 41)
+        n = np.array(sdf.shape[::-1])
+        inside = np.all((xg - origin) / voxel >= 0, 1) & np.all((xg - origin) / voxel <= n - 1, 1)
+        m = min(m, np.abs(vals[inside]).min())
+        for c in lst:
+            dc = np.sort(np.sqrt(((Sp - pts[c]) ** 2).sum(-1)))
+            m = min(m, dc[1] - dc[0])
+        assert orc.decision_margin(0, th) == pytest.approx(m, rel=1e-12, abs=1e-15)
+        st = orc.new_state(th[None, None], margin=True)
+        orc.evaluate(st)
+        assert st["margin"][0, 0] == orc.decision_margin(0, th)
+    # a planted duplicate object point is an exact tie: margin 0
+    orc2, _ = _palm_problem(oracle_mod, np.concatenate([pts, pts[2:3]]))
+    assert orc2.decision_margin(0, np.array([0, 0, 0, 1.0, 0, 0, 0])) == 0.0
