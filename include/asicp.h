@@ -196,6 +196,18 @@ asicp_status asicp_set_gripper_sdf(asicp_ctx *ctx, int preshape, const float *S_
  * teacher-force a single step.  Errors: INVALID_ARG, STATE (inputs not set). */
 asicp_status asicp_set_state(asicp_ctx *ctx, const float *theta, int k);
 
+/* Set the convergence state that the next SGD-phase step reads (Table I's
+ * convergence criterion, Section IV-D): prev_cost[T] (float64; the cost of the
+ * previous iteration, negative = none) and frozen[T] (int; nonzero = converged,
+ * the SGD update skips the particle).  In the SGD phase a step freezes a particle
+ * whose relative cost change |L_k - L_(k-1)| / L_(k-1) is at most conv_tol and
+ * unfreezes every particle with a colliding point; every step then stores its
+ * cost as the next previous cost.  Call after asicp_set_state (which clears
+ * both) to resume or teacher-force a step; either pointer may be NULL (that part
+ * is kept).  Host or device pointers, copied.  Errors: STATE (poses not set),
+ * CUDA. */
+asicp_status asicp_set_convergence(asicp_ctx *ctx, const double *prev_cost, const int *frozen);
+
 /* One iteration k (0 <= k < k_max) of Algorithm 1 for all preshapes and
  * particles: transform, match, cost/gradient, collision test and collision
  * gradient, then the SVGD update (k < k_stein, Eqs. 7-11) or the SGD-ICP update
@@ -244,13 +256,15 @@ asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[ASICP_KERNEL_KINDS], l
  * real-time control loops that reserve all memory at start-up and cannot afford the
  * device synchronisation of cudaMalloc/cudaFree, or runtimes that hand out all
  * device memory from their own pool.  It computes what asicp_step's matching stage
- * computes (Eq. 1): for every particle p*K+j and gripper point i, the index of the
- * nearest object point, ties to the lowest index, written to
- * nn_idx[(p*K + j)*N + i].
+ * computes: for every particle p*K+j and gripper point i, the index of the nearest
+ * object point, ties to the lowest index, written to nn_idx[(p*K + j)*N + i].
  *   theta   P*K*7 floats (poses, quaternions are normalised), S_xyz P*N*3 floats
  *           (gripper clouds, preshape-major), R_xyz M*3 floats: host or device memory
+ *           (host inputs are staged through the scratch array, not allocated)
  *   nn_idx  P*K*N int32 output, device memory
- *   cuda_stream  cudaStream_t (NULL: default stream); the call synchronises it
+ *   cuda_stream  cudaStream_t (NULL: default stream); the call waits for the stream
+ *           twice (after checking the inputs and at the end) and returns when nn_idx
+ *           is written
  * Its scratch is one fixed-size static device array (5 MiB) that every device that
  * loads the library keeps until the process exits; it bounds the sizes to
  * P*K <= ASICP_NOALLOC_MAX_PK, P*N <= ASICP_NOALLOC_MAX_PN, M <= ASICP_NOALLOC_MAX_M
@@ -258,8 +272,9 @@ asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[ASICP_KERNEL_KINDS], l
  * array's device address up once (make it before any stream capture).  All calls
  * share the array: calls that overlap on the GPU race and must be ordered by the
  * caller.  Returns INVALID_ARG for NULL pointers, sizes < 1 or beyond the limits,
- * nn_idx not in device memory, or a non-finite input; TIMEOUT if a bounded device
- * wait expired; CUDA for a failed CUDA call. */
+ * nn_idx not in device memory, or a non-finite input (nn_idx is then left
+ * untouched); TIMEOUT if a bounded device wait expired (nn_idx undefined); CUDA for
+ * a failed CUDA call. */
 #define ASICP_NOALLOC_MAX_PK 16384
 #define ASICP_NOALLOC_MAX_PN 65536
 #define ASICP_NOALLOC_MAX_M 65536
@@ -290,6 +305,19 @@ asicp_status asicp_set_minibatch(asicp_ctx *ctx, const int *offsets, const int *
  * tensor-core shape is skipped (its ms entry is 0).
  * Errors: STATE (inputs not set), CUDA. */
 asicp_status asicp_autotune(asicp_ctx *ctx, int *chosen, float *ms);
+
+/* Testing aid for the bounded-wait path.  Every device-side wait of the library
+ * is bounded (2^32 SM clock cycles, about 2 s); when one expires, the kernel sets
+ * the context's error word, drains its copies in flight with the full budget and
+ * returns, the later kernels of the pass see the error word and skip their work,
+ * and the next call that reads results (asicp_get_state, asicp_best_grasps)
+ * returns TIMEOUT and clears the word; the context stays usable.  With on != 0 the
+ * float32 matching shapes' kernels of later asicp_step / asicp_run calls make each
+ * CTA's first copy wait on an mbarrier that nothing arrives at, for 1000 cycles,
+ * so that it expires; on = 0 restores normal waits (a captured loop is
+ * re-captured).  The tensor-core shape ignores it.  Errors: none beyond a NULL
+ * context. */
+asicp_status asicp_test_expire_waits(asicp_ctx *ctx, int on);
 
 /* Message of the last failing call on ctx (owned by ctx, valid until its next call). */
 const char *asicp_last_error(const asicp_ctx *ctx);

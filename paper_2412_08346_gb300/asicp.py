@@ -28,7 +28,7 @@ EXPORTED = ("asicp_config_default", "asicp_create", "asicp_destroy", "asicp_set_
             "asicp_set_gripper_sdf", "asicp_set_state", "asicp_step", "asicp_run", "asicp_best_grasps",
             "asicp_get_state", "asicp_kernel_times", "asicp_last_error", "asicp_match_noalloc",
             "asicp_set_object_at", "asicp_set_particle_counts", "asicp_best_grasps_at", "asicp_autotune",
-            "asicp_set_minibatch")
+            "asicp_set_minibatch", "asicp_set_convergence", "asicp_test_expire_waits")
 
 
 class AsicpError(RuntimeError):
@@ -79,6 +79,8 @@ def load(build_if_missing: bool = True):
     lib.asicp_set_object.argtypes = [vp, vp, ip, vp, ip]
     lib.asicp_set_gripper_sdf.argtypes = [vp, ip, vp, ip, vp, ip, ip, ip, vp, C.c_float]
     lib.asicp_set_state.argtypes = [vp, vp, ip]
+    lib.asicp_set_convergence.argtypes = [vp, vp, vp]
+    lib.asicp_test_expire_waits.argtypes = [vp, ip]
     lib.asicp_step.argtypes = [vp, ip]
     lib.asicp_run.argtypes = [vp, vp]
     lib.asicp_best_grasps.argtypes = [vp, ip, vp, vp, vp, C.POINTER(C.c_int)]
@@ -180,6 +182,14 @@ def asicp_set_gripper_sdf(ctx, preshape, S_xyz, sdf_zyx, origin, voxel) -> None:
 
 def asicp_set_state(ctx, theta, k: int) -> None:
     _check(ctx, load().asicp_set_state(ctx, _ptr(theta), int(k)))
+
+
+def asicp_set_convergence(ctx, prev_cost=None, frozen=None) -> None:
+    _check(ctx, load().asicp_set_convergence(ctx, _ptr(prev_cost), _ptr(frozen)))
+
+
+def asicp_test_expire_waits(ctx, on: bool) -> None:
+    _check(ctx, load().asicp_test_expire_waits(ctx, int(bool(on))))
 
 
 def asicp_step(ctx, k: int) -> None:

@@ -99,10 +99,11 @@ struct asicp_ctx {
     // mini-batches of the object cloud per iteration (Table I), one object only
     std::vector<int> mb_off;          // [iters + 1] on the host (sizes are fixed at capture)
     long long mb_version = 0;         // bumped by every asicp_set_minibatch
-    DevMem mb_idx, mb_R, mb_Rx, mb_rmax;
+    DevMem mb_idx, mb_R, mb_Rx;
 
     int fwd_variant = 0;              // forward-matching kernel shape (autotuner's choice)
     bool tuned = false;
+    bool expire_test = false;         // the float32 matching kernels' first copy waits expire (testing)
 
     // layout (rebuilt when objects, particle counts or N change)
     bool layout_dirty = true;
@@ -111,7 +112,7 @@ struct asicp_ctx {
     std::vector<int> grp_off_h;
     std::vector<ObjMeta> objmeta_h;
 
-    DevMem partgrp, grpoff, objmeta, items, ctaoff, com, rmax, colitems, collist, box, stage, S, pconst, dmeta, theta, fsums,
+    DevMem partgrp, grpoff, objmeta, items, ctaoff, com, frame, colitems, collist, box, stage, S, pconst, dmeta, theta, fsums,
         csums, ncol, colidx, cost, grad, prev, frozen, phi, h, order, errw, out7, outc, outi, nnidx, tccand, dbg_d2, dbg_sp,
         dbg_colnn;
 
@@ -149,7 +150,7 @@ struct asicp_ctx {
         L.grp_off = grpoff.as<int>();
         L.obj = objmeta.as<ObjMeta>();
         L.com = com.as<double>();
-        L.rmax = rmax.as<float>();
+        L.frame = frame.as<float4>();
         return L;
     }
     cudaEvent_t take_event()
@@ -426,7 +427,9 @@ void select_minibatch(asicp_ctx *c, int k)
         const int Mpad = (cnt + kRefTilePts - 1) / kRefTilePts * kRefTilePts;
         ck(launch_gather_points(c->objs[0].R.as<float4>(), c->mb_idx.as<int>() + first, cnt, c->mb_R.as<float4>(), st),
            "mini-batch gather");
-        ck(launch_ref_prep(c->mb_R.as<float4>(), cnt, Mpad, c->mb_Rx.p, c->mb_rmax.as<float>(), st), "mini-batch prep");
+        // the mini-batch keeps the whole object's frame (its points are a subset)
+        ck(launch_ref_prep(c->mb_R.as<float4>(), cnt, Mpad, c->mb_Rx.p, c->frame.as<float4>(), false, st),
+           "mini-batch prep");
         m.R = c->mb_R.as<float4>();
         m.Rx = c->mb_Rx.as<ulonglong2>();
         m.M = cnt;
@@ -450,6 +453,7 @@ void iterate(asicp_ctx *c, int mode, float gamma, int k)
     fa.nn_idx = c->nnidx.as<int>();
     fa.cand = c->tccand.as<int4>();
     fa.variant = c->fwd_variant;
+    fa.expire_test = c->expire_test ? 1 : 0;
     if (c->cfg.debug) {
         fa.dbg_d2 = c->dbg_d2.as<float>();
         fa.dbg_sp = c->dbg_sp.as<float>();
@@ -470,6 +474,7 @@ void iterate(asicp_ctx *c, int mode, float gamma, int k)
     ca.csums = c->csums.as<double>();
     ca.col_items = c->colitems.as<int>();
     ca.col_list = c->collist.as<int>();
+    ca.err = c->errw.as<int>();
     if (c->cfg.debug) ca.dbg_colnn = c->dbg_colnn.as<int>();
     timed(c, kTimeCollide, [&](cudaStream_t st) { return launch_collide(ca, st); }, "collision kernel");
     timed(c, kTimeCollideNN, [&](cudaStream_t st) { return launch_collide_nn(ca, st); }, "collision matching kernel");
@@ -496,6 +501,7 @@ void iterate(asicp_ctx *c, int mode, float gamma, int k)
     ua.phi = c->phi.as<float>();
     ua.h = c->h.as<float>();
     ua.col_items = c->colitems.as<int>();
+    ua.err = c->errw.as<int>();
     ua.prior_t_sigma = c->cfg.prior_t_sigma;
     ua.prior_q_kappa = c->cfg.prior_q_kappa;
     {
@@ -532,13 +538,14 @@ void run_loop(asicp_ctx *c)
 // read at replay, so new objects of the same sizes reuse the graph).
 std::vector<const void *> loop_key(const asicp_ctx *c)
 {
-    return {c->partgrp.p, c->grpoff.p, c->objmeta.p, c->items.p, c->ctaoff.p, c->com.p, c->rmax.p, c->colitems.p, c->collist.p,
+    return {c->partgrp.p, c->grpoff.p, c->objmeta.p, c->items.p, c->ctaoff.p, c->com.p, c->frame.p, c->colitems.p, c->collist.p,
             c->S.p, c->pconst.p, c->dmeta.p, c->theta.p, c->fsums.p, c->csums.p, c->ncol.p, c->colidx.p, c->cost.p,
             c->grad.p, c->prev.p, c->frozen.p, c->phi.p, c->h.p, c->order.p, c->errw.p, c->nnidx.p, c->tccand.p, c->dbg_d2.p,
             c->dbg_sp.p, c->dbg_colnn.p, c->mb_idx.p, c->mb_R.p, c->mb_Rx.p,
             reinterpret_cast<const void *>((size_t)c->mb_version), reinterpret_cast<const void *>((size_t)c->T),
             reinterpret_cast<const void *>((size_t)c->G), reinterpret_cast<const void *>((size_t)c->n_items),
-            reinterpret_cast<const void *>((size_t)c->N), reinterpret_cast<const void *>((size_t)c->fwd_variant)};
+            reinterpret_cast<const void *>((size_t)c->N), reinterpret_cast<const void *>((size_t)c->fwd_variant),
+            reinterpret_cast<const void *>((size_t)c->expire_test)};
 }
 
 // Replay the captured loop on the caller's stream, capturing it first when the
@@ -689,9 +696,10 @@ void set_object_impl(asicp_ctx *ctx, int o, const float *R_xyz, int M, const flo
     ck(launch_centroid(b.R.as<float4>(), M, ctx->com.as<double>() + 3 * o, ctx->st), "centroid");
     const int Mpad = (M + kRefTilePts - 1) / kRefTilePts * kRefTilePts;
     b.Rx.ensure(sizeof(float4) * (size_t)Mpad, "screening layout");
-    ck(launch_ref_prep(b.R.as<float4>(), M, Mpad, b.Rx.p, ctx->rmax.as<float>() + o, ctx->st), "ref prep");
+    ck(launch_ref_prep(b.R.as<float4>(), M, Mpad, b.Rx.p, ctx->frame.as<float4>() + o, true, ctx->st), "ref prep");
     b.Rt.ensure(tc_ref_bytes(Mpad), "tensor-core object tiles");
-    ck(launch_tc_ref_prep(b.R.as<float4>(), M, Mpad, ctx->rmax.as<float>() + o, b.Rt.p, ctx->st), "tensor-core ref prep");
+    ck(launch_tc_ref_prep(b.R.as<float4>(), M, Mpad, ctx->frame.as<float4>() + o, b.Rt.p, ctx->st),
+       "tensor-core ref prep");
     sync_and_check_err(ctx, "set_object");
     b.M = M;
     b.Mpad = Mpad;
@@ -769,7 +777,7 @@ asicp_status asicp_create(const asicp_config *cfg, asicp_ctx **out)
         ck(init_collision_attributes(), "collision kernel attributes");
         ck(init_update_attributes(), "update kernel attributes");
         c->com.ensure(sizeof(double) * 3 * c->nobj, "com");
-        c->rmax.ensure(sizeof(float) * c->nobj, "rmax");
+        c->frame.ensure(sizeof(float4) * c->nobj, "screening frames");
         c->pconst.ensure(sizeof(double) * 12 * cfg->P, "pconst");
         c->dmeta.ensure(sizeof(SdfMeta) * cfg->P, "sdf meta");
         c->errw.ensure(sizeof(int), "error word");
@@ -847,7 +855,6 @@ asicp_status asicp_set_minibatch(asicp_ctx *ctx, const int *offsets, const int *
         ctx->mb_idx.ensure(sizeof(int) * idx.size(), "mini-batch indices");
         ctx->mb_R.ensure(sizeof(float4) * M, "mini-batch points");
         ctx->mb_Rx.ensure(sizeof(float4) * Mpad, "mini-batch screening layout");
-        ctx->mb_rmax.ensure(sizeof(float), "mini-batch rmax");
         ck(cudaMemcpy(ctx->mb_idx.p, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice), "upload indices");
         ctx->mb_off = off;
         ctx->run_done = false;
@@ -939,6 +946,20 @@ asicp_status asicp_set_state(asicp_ctx *ctx, const float *theta, int k)
         ctx->theta_set = true;
         ctx->stepped = false;
         ctx->run_done = false;
+    });
+}
+
+asicp_status asicp_set_convergence(asicp_ctx *ctx, const double *prev_cost, const int *frozen)
+{
+    return guarded(ctx, [&] {
+        if (!ctx->theta_set || ctx->layout_dirty) fail(ASICP_ERR_STATE, "set_convergence: set the poses first");
+        const size_t T = ctx->T;
+        if (prev_cost)
+            ck(cudaMemcpyAsync(ctx->prev.p, prev_cost, sizeof(double) * T, cudaMemcpyDefault, ctx->st),
+               "copy prev_cost");
+        if (frozen)
+            ck(cudaMemcpyAsync(ctx->frozen.p, frozen, sizeof(int) * T, cudaMemcpyDefault, ctx->st), "copy frozen");
+        ck(cudaStreamSynchronize(ctx->st), "set_convergence");
     });
 }
 
@@ -1071,6 +1092,11 @@ asicp_status asicp_autotune(asicp_ctx *ctx, int *chosen, float *ms)
         autotune_impl(ctx, ms);
         if (chosen) *chosen = ctx->fwd_variant;
     });
+}
+
+asicp_status asicp_test_expire_waits(asicp_ctx *ctx, int on)
+{
+    return guarded(ctx, [&] { ctx->expire_test = on != 0; });
 }
 
 asicp_status asicp_kernel_times(asicp_ctx *ctx, double ms[ASICP_KERNEL_KINDS], long long launches[ASICP_KERNEL_KINDS],

@@ -211,7 +211,8 @@ struct Layout {
     const int *grp_off;       // [G + 1] first particle of every group
     const ObjMeta *obj;       // [nobj]
     const double *com;        // [nobj][3] object centroids (CoM)
-    const float *rmax;        // [nobj] max |r| per object (rounded up)
+    const float4 *frame;      // [nobj] screening frame: centre c (x, y, z; the bounding-box
+                              // centre) and w = max |fl(r - c)| rounded up (see ref_prep_kernel)
 };
 
 // A unit of forward-matching work: queries [q0, q0 + nq) of the flattened
@@ -234,6 +235,8 @@ struct FwdArgs {
     float *dbg_sp;           // [T][N][3] or null
     int4 *cand;              // [T][N] tensor-core shape only: candidate chunks per query
     int variant;             // kernel shape (0 .. kFwdVariants - 1), chosen by the autotuner
+    int expire_test;         // float32 shapes: the first copy wait of a CTA waits on an mbarrier
+                             // that nothing arrives at, for kTestWaitCycles (tests the timeout path)
 };
 constexpr int kFwdItemQueries = 1024;  // queries per forward-matching work item
 constexpr int kFwdVariants = 8;        // kernel shapes of the forward matching (7: tensor cores)
@@ -249,8 +252,12 @@ int fwd_shape_queries(int v);          // queries per work item (at most) of ker
 const char *fwd_variant_name(int v);
 cudaError_t init_collision_attributes();
 cudaError_t init_update_attributes();
-cudaError_t launch_ref_prep(const float4 *R, int M, int Mpad, void *Rx, float *rmax, cudaStream_t st);
-cudaError_t launch_tc_ref_prep(const float4 *R, int M, int Mpad, const float *rmax, void *Rt, cudaStream_t st);
+// Screening layout of R relative to the frame's centre.  compute_frame = true finds the
+// centre and radius of R and stores them in *frame; false keeps the given frame (a
+// subset of a cloud whose frame is already set, e.g. a mini-batch).
+cudaError_t launch_ref_prep(const float4 *R, int M, int Mpad, void *Rx, float4 *frame, bool compute_frame,
+                            cudaStream_t st);
+cudaError_t launch_tc_ref_prep(const float4 *R, int M, int Mpad, const float4 *frame, void *Rt, cudaStream_t st);
 size_t tc_ref_bytes(int Mpad);         // bytes of the tensor-core object tiles
 cudaError_t launch_fwd_match_tc(const FwdArgs &a, cudaStream_t st);
 cudaError_t launch_tc_exact(const FwdArgs &a, cudaStream_t st);
@@ -272,6 +279,7 @@ struct CollideArgs {
     int *dbg_colnn;           // like colidx, or null
     int *col_items;           // (count, next) of the reverse-matching work list
     int *col_list;            // [2 * items] (particle, chunk) pairs
+    const int *err;           // error word: a kernel of the pass found an error, skip the work
 };
 cudaError_t launch_collide(const CollideArgs &a, cudaStream_t st);
 cudaError_t launch_collide_nn(const CollideArgs &a, cudaStream_t st);
@@ -299,6 +307,7 @@ struct UpdateArgs {
     float prior_t_sigma;      // Gaussian prior on t around the object's CoM (<= 0: off)
     float prior_q_kappa;      // von Mises prior on q (<= 0: off)
     float prior_q_mean[4];    // its unit mean
+    const int *err;           // error word: a kernel of the pass found an error, skip the work
 };
 cudaError_t launch_finalize(const UpdateArgs &a, cudaStream_t st);   // cost/gradient, convergence, SGD step
 cudaError_t launch_stein(const UpdateArgs &a, cudaStream_t st);      // SVGD step (mode 1)

@@ -5,6 +5,7 @@
 namespace asicp {
 
 constexpr long long kWaitCycles = 1LL << 32;   // bounded mbarrier wait (~2 s)
+constexpr long long kTestWaitCycles = 1000;    // the wait made to expire when testing the timeout path
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
 {
@@ -16,10 +17,13 @@ __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned coun
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+// Arrive on the mbarrier at shared-memory address addr.
+__device__ __forceinline__ void mbar_arrive_at(unsigned addr)
 {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
 }
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) { mbar_arrive_at(smem_u32(bar)); }
 
 __device__ __forceinline__ void mbar_arrive_tx(unsigned long long *bar, unsigned bytes)
 {
@@ -35,7 +39,7 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+__device__ __forceinline__ bool mbar_try_wait_at(unsigned addr, unsigned parity)
 {
     unsigned ok;
     asm volatile(
@@ -43,36 +47,47 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(addr), "r"(parity)
         : "memory");
     return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase: false when the budget ran out.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+{
+    return mbar_try_wait_at(smem_u32(bar), parity);
+}
+
+// Bounded wait on an mbarrier phase: false when the budget (SM clock cycles) ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, long long limit = kWaitCycles)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
-// The same for a whole warp: lane 0 polls (try_wait suspends in hardware; a
-// software back-off between polls measured slower), the warp then continues
-// together.  Returns the same verdict on every lane.
-__device__ __forceinline__ bool mbar_wait_warp(unsigned long long *bar, unsigned parity)
+// The same for a whole warp (barrier at shared-memory address addr): lane 0 polls
+// (try_wait suspends in hardware; a software back-off between polls measured
+// slower), the warp then continues together.  Returns the same verdict on every
+// lane.
+__device__ __forceinline__ bool mbar_wait_warp_at(unsigned addr, unsigned parity)
 {
     bool ok = true;
     if ((threadIdx.x & 31) == 0) {
-        if (!mbar_try_wait(bar, parity)) {
+        if (!mbar_try_wait_at(addr, parity)) {
             const long long t0 = clock64();
-            while (!mbar_try_wait(bar, parity)) {
+            while (!mbar_try_wait_at(addr, parity)) {
                 if (clock64() - t0 > kWaitCycles) { ok = false; break; }
             }
         }
     }
     return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_warp(unsigned long long *bar, unsigned parity)
+{
+    return mbar_wait_warp_at(smem_u32(bar), parity);
 }
 
 }  // namespace asicp

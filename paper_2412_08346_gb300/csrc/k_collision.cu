@@ -72,6 +72,7 @@ __device__ __forceinline__ void block_reduce_store(dfloat (&acc)[NV], double (*s
 //     block prefix), so results do not depend on scheduling.
 __global__ void __launch_bounds__(kTestThreads) collide_kernel(const CollideArgs a)
 {
+    if (a.err && *a.err != kDevOk) return;    // the matching gave up: its correspondences are not valid
     __shared__ int swarp[kColU][kTestThreads / 32];
     __shared__ double sred[kTestThreads / 32][kFwdSums];
     const int pk = blockIdx.x;
@@ -237,12 +238,16 @@ __constant__ unsigned char kColSel[kColSums][2] = {
 // (-2 s', |s'|^2), point pairs (l + 64 m, l + 32 + 64 m) at slot 32 m + l, and
 // exact (float4), chunk l contiguous with a stride of KC + 1 (no bank
 // conflicts).  Each warp matches kQW colliding points c:
-//  1. screening: lane l evaluates d~ = |s'|^2 - 2 c.s' over chunk l (packed
+//  1. screening, relative to the particle's translation t (so the error does not
+//     grow with the distance from the origin): with b = fl(s' - t) and
+//     a = fl(c - t), lane l evaluates d~ = |b|^2 - 2 a.b over chunk l (packed
 //     f32x2 FMAs, 3-input min); warp min-reductions give the best chunk minimum
 //     b1 (lane l1, the lowest on ties) and the best of the other chunks b2;
-//  2. exact choice: with delta = u (7 Smax^2 + 6.1 |c| Smax) bounding the error of
-//     d~ (Smax = max |s'|), the nearest point lies in chunk l1 unless b2 <= b1 +
-//     2 delta; four lanes per colliding point re-evaluate chunk l1 with the
+//  2. exact choice: with delta = u (9 B^2 + 10.1 A B) bounding the error of d~
+//     against |c - s'|^2 + const (B = max |b|, A = |a|: the float32 evaluation
+//     within u (7 B^2 + 6.1 A B), the rounding of a and b within u (2 B^2 + 4 A B)
+//     beyond a term that does not depend on s'), the nearest point lies in chunk
+//     l1 unless b2 <= b1 + 2 delta; four lanes per colliding point re-evaluate chunk l1 with the
 //     exact-form distance, ties to the lowest index; in the rare other case the
 //     warp scans the whole cloud that way.
 // The sums the collision cost and gradient are linear in are then accumulated
@@ -254,6 +259,7 @@ __constant__ unsigned char kColSel[kColSums][2] = {
 // which CTA took which item.
 __global__ void __launch_bounds__(kColThreads) collide_nn_kernel(const CollideArgs a)
 {
+    if (a.err && *a.err != kDevOk) return;
     constexpr int kWarps = kColThreads / 32;
     constexpr int kQW = kColChunk / kWarps;                  // colliding points per warp
     static_assert(kQW == 8 && kColChunk == 64, "lane groups of four per colliding point");
@@ -312,8 +318,9 @@ __global__ void __launch_bounds__(kColThreads) collide_nn_kernel(const CollideAr
                     const float4 sv = S[r];
                     const float3 o = xform_f32(Rm, tx, ty, tz, sv.x, sv.y, sv.z);
                     e = make_float4(o.x, o.y, o.z, 0.f);
-                    ax[h] = -2.f * o.x; ay[h] = -2.f * o.y; az[h] = -2.f * o.z;
-                    w[h] = __fmaf_rn(o.x, o.x, __fmaf_rn(o.y, o.y, __fmul_rn(o.z, o.z)));
+                    const float bx = __fsub_rn(o.x, tx), by = __fsub_rn(o.y, ty), bz = __fsub_rn(o.z, tz);
+                    ax[h] = -2.f * bx; ay[h] = -2.f * by; az[h] = -2.f * bz;
+                    w[h] = __fmaf_rn(bx, bx, __fmaf_rn(by, by, __fmul_rn(bz, bz)));
                     smax2 = fmaxf(smax2, w[h]);
                 } else {
                     ax[h] = ay[h] = az[h] = 0.f;
@@ -341,7 +348,8 @@ __global__ void __launch_bounds__(kColThreads) collide_nn_kernel(const CollideAr
 #pragma unroll
         for (int q = 0; q < kQW; ++q) {
             const float4 c = sC[warp * kQW + q];
-            qx[q] = pk2(c.x, c.x); qy[q] = pk2(c.y, c.y); qz[q] = pk2(c.z, c.z);
+            const float ax = __fsub_rn(c.x, tx), ay = __fsub_rn(c.y, ty), az = __fsub_rn(c.z, tz);
+            qx[q] = pk2(ax, ax); qy[q] = pk2(ay, ay); qz[q] = pk2(az, az);
             cm[q] = __int_as_float(0x7f800000);
         }
         for (int m = 0; m < slots; ++m) {
@@ -366,8 +374,9 @@ __global__ void __launch_bounds__(kColThreads) collide_nn_kernel(const CollideAr
             const int l1 = __ffs(__ballot_sync(0xffffffffu, key == k1)) - 1;
             const unsigned k2 = __reduce_min_sync(0xffffffffu, lane == l1 ? 0xffffffffu : key);
             const float4 c = sC[warp * kQW + q];
-            const float cn = sqrtf(c.x * c.x + c.y * c.y + c.z * c.z) * 1.001f;
-            const float win = 2.02f * 5.9604645e-8f * (7.f * smax * smax + 6.1f * cn * smax);
+            const float ax = __fsub_rn(c.x, tx), ay = __fsub_rn(c.y, ty), az = __fsub_rn(c.z, tz);
+            const float cn = sqrtf(ax * ax + ay * ay + az * az) * 1.001f;
+            const float win = 2.02f * 5.9604645e-8f * (9.f * smax * smax + 10.1f * cn * smax);
             if (key_val(k2) <= key_val(k1) + win) full_scan |= 1u << q;
             if (g == q) my_l1 = l1;
         }

@@ -5,23 +5,30 @@
 // the smallest squared distance, ties to the lowest index (Eq. 1).
 //
 // Search in two stages, exact in the end:
-//  1. Screening.  For every object point r the kernel evaluates
-//     d~(r) = |r|^2 - 2 s'.r  (= |s' - r|^2 - |s'|^2, the same ranking) as three
-//     fused multiply-adds on precomputed (-2r, |r|^2), two object points per
-//     packed f32x2 instruction, and keeps per chunk of kChunk points the chunk
-//     minimum with a 3-input min.  Per query it tracks the best two chunk
-//     minima b1 <= b2 with their chunk ids, and the third-best b3.
-//  2. Exact choice.  |d~ - (|r|^2 - 2 s'.r)| <= delta with
-//     delta = u (4.01 Rmax^2 + 6.02 |s'| Rmax), u = 2^-24, Rmax = max |r|
-//     (float32 rounding of |r|^2 plus three roundings of the FMA chain, with
-//     sum |s_k r_k| <= |s'| |r|).  The true nearest point r* therefore has
-//     d~(r*) <= b1 + 2 delta, so every chunk whose minimum exceeds that bound is
-//     excluded.  If only chunk c1 (and c2 when b2 <= b1 + 2 delta) can hold r*,
-//     their points are re-evaluated with the exact-form distance
-//     (dx^2 + dy^2 + dz^2 in float32) in index order; if a third chunk could
-//     (b3 <= b1 + 2 delta, rare), the warp scans the whole cloud for that query
-//     together.  The result is the lowest-index minimum of the exact-form
-//     float32 distance among all points that can be nearest.
+//  1. Screening, in coordinates relative to the object's frame centre c (the
+//     centre of its bounding box, so the screening error does not grow with the
+//     object's distance from the origin): with b = fl(r - c) and a = fl(s' - c)
+//     the kernel evaluates d~(r) = |b|^2 - 2 a.b (= |a - b|^2 - |a|^2, the same
+//     ranking as |s' - r|^2 up to the rounding of a and b) as three fused
+//     multiply-adds on precomputed (-2b, |b|^2), two object points per packed
+//     f32x2 instruction, and keeps per chunk of kChunk points the chunk minimum
+//     with a 3-input min.  Per query it tracks the best two chunk minima
+//     b1 <= b2 with their chunk ids, and the third-best b3.
+//  2. Exact choice.  With u = 2^-24, B = max |b| and A = |a|, the float32
+//     evaluation is within u (4.01 B^2 + 6.02 A B) of |b|^2 - 2 a.b (rounding of
+//     |b|^2 plus three roundings of the FMA chain, with sum |a_k b_k| <= A B).
+//     The rounding of a and b changes |a - b|^2 - |a|^2 against |s' - r|^2 by a
+//     term independent of r (which does not change the ranking) plus at most
+//     u (2 B^2 + 4 A B), so d~(r) = |s' - r|^2 + const + e(r) with
+//     |e(r)| <= delta = u (6.01 B^2 + 10.02 A B).  The true nearest point r*
+//     therefore has d~(r*) <= b1 + 2 delta, so every chunk whose minimum exceeds
+//     that bound is excluded.  If only chunk c1 (and c2 when b2 <= b1 + 2 delta)
+//     can hold r*, their points are re-evaluated with the exact-form distance
+//     (dx^2 + dy^2 + dz^2 of s' - r in float32, original coordinates) in index
+//     order; if a third chunk could (b3 <= b1 + 2 delta, rare), the warp scans
+//     the whole cloud for that query together.  The result is the lowest-index
+//     minimum of the exact-form float32 distance among all points that can be
+//     nearest.
 //
 // Object tiles are staged in shared memory by 1D bulk (TMA) copies into two
 // buffers guarded by mbarriers; waits are bounded and report a timeout through
@@ -85,8 +92,9 @@ __device__ __forceinline__ float min3(float a, float b, float c)
 // through the two shared buffers; `seq` counts the tiles this CTA has consumed,
 // which gives each buffer's mbarrier phase.
 template <class Shape, int Q>
-__device__ __forceinline__ bool match_pass(const FwdArgs &a, const ObjMeta &om, float rmax, long long q0, int nq,
-                                           ulonglong2 *tiles, unsigned long long *full, int &seq, int *s_abort)
+__device__ __forceinline__ bool match_pass(const FwdArgs &a, const ObjMeta &om, float4 fr, long long q0, int nq,
+                                           ulonglong2 *tiles, unsigned long long *full, unsigned long long *never,
+                                           int &seq, int *s_abort)
 {
     constexpr int kThreads = Shape::kThreads, kChunk = Shape::kChunk, kTile = Shape::kTile;
     const int ntiles = om.Mpad / kTile;
@@ -117,17 +125,25 @@ __device__ __forceinline__ bool match_pass(const FwdArgs &a, const ObjMeta &om, 
             o = xform_f32(Rm, th[0], th[1], th[2], s.x, s.y, s.z);
         }
         sx[q] = o.x; sy[q] = o.y; sz[q] = o.z;
-        qx[q] = pack2(o.x, o.x); qy[q] = pack2(o.y, o.y); qz[q] = pack2(o.z, o.z);
-        const float sn = sqrtf(o.x * o.x + o.y * o.y + o.z * o.z) * 1.001f;
+        // the query relative to the frame centre (a = fl(s' - c))
+        const float ax = __fsub_rn(o.x, fr.x), ay = __fsub_rn(o.y, fr.y), az = __fsub_rn(o.z, fr.z);
+        qx[q] = pack2(ax, ax); qy[q] = pack2(ay, ay); qz[q] = pack2(az, az);
+        const float an = sqrtf(ax * ax + ay * ay + az * az) * 1.001f;
         // 2 delta with a 1 % margin for the float32 evaluation of the bound itself
-        win[q] = 2.02f * 5.9604645e-8f * (4.01f * rmax * rmax + 6.02f * sn * rmax);
+        win[q] = 2.02f * 5.9604645e-8f * (6.01f * fr.w * fr.w + 10.02f * an * fr.w);
         b1[q] = b2[q] = b3[q] = __int_as_float(0x7f800000);
         c1[q] = c2[q] = 0;
     }
 
     for (int t = 0; t < ntiles; ++t, ++seq) {
         const int buf = seq & 1;
-        if (!mbar_wait(&full[buf], (seq >> 1) & 1)) { atomicExch(a.err, kDevTimeout); *s_abort = 1; }
+        // (testing the timeout path: the CTA's first wait is on a barrier nothing arrives at)
+        const bool landed = a.expire_test && seq == 0 ? mbar_wait(never, 0u, kTestWaitCycles)
+                                                      : mbar_wait(&full[buf], (seq >> 1) & 1);
+        if (!landed) {
+            atomicExch(a.err, kDevTimeout);
+            *s_abort = 1;
+        }
         __syncthreads();
         if (*s_abort) return false;
         const ulonglong2 *tp = tiles + (size_t)buf * kTile;
@@ -209,14 +225,14 @@ __device__ __forceinline__ bool match_pass(const FwdArgs &a, const ObjMeta &om, 
 
 // match_pass with the smallest queries-per-thread count Q >= qn (Q <= QMAX).
 template <class Shape, int QMAX>
-__device__ __forceinline__ bool dispatch_pass(int qn, const FwdArgs &a, const ObjMeta &om, float rmax, long long q0,
-                                              int nq, ulonglong2 *tiles, unsigned long long *full, int &seq,
-                                              int *s_abort)
+__device__ __forceinline__ bool dispatch_pass(int qn, const FwdArgs &a, const ObjMeta &om, float4 fr, long long q0,
+                                              int nq, ulonglong2 *tiles, unsigned long long *full,
+                                              unsigned long long *never, int &seq, int *s_abort)
 {
     if constexpr (QMAX > 1) {
-        if (qn < QMAX) return dispatch_pass<Shape, QMAX - 1>(qn, a, om, rmax, q0, nq, tiles, full, seq, s_abort);
+        if (qn < QMAX) return dispatch_pass<Shape, QMAX - 1>(qn, a, om, fr, q0, nq, tiles, full, never, seq, s_abort);
     }
-    return match_pass<Shape, QMAX>(a, om, rmax, q0, nq, tiles, full, seq, s_abort);
+    return match_pass<Shape, QMAX>(a, om, fr, q0, nq, tiles, full, never, seq, s_abort);
 }
 
 // Persistent: CTA b runs the work items the host planned for it
@@ -230,7 +246,7 @@ __global__ void __launch_bounds__(Shape::kThreads, Shape::kMinBlocks) fwd_match_
     constexpr int kThreads = Shape::kThreads;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     ulonglong2 *tiles = reinterpret_cast<ulonglong2 *>(smem_raw);
-    __shared__ __align__(8) unsigned long long full[2];
+    __shared__ __align__(8) unsigned long long full[2], never;
     __shared__ int s_abort;
     const int it0 = a.cta_off ? a.cta_off[blockIdx.x] : blockIdx.x;
     const int it1 = a.cta_off ? a.cta_off[blockIdx.x + 1] : a.n_items;
@@ -240,6 +256,7 @@ __global__ void __launch_bounds__(Shape::kThreads, Shape::kMinBlocks) fwd_match_
         s_abort = 0;
         mbar_init(&full[0], 1);
         mbar_init(&full[1], 1);
+        mbar_init(&never, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -256,11 +273,11 @@ __global__ void __launch_bounds__(Shape::kThreads, Shape::kMinBlocks) fwd_match_
             item.obj = 0;
         }
         const ObjMeta om = a.L.obj[item.obj];
-        const float rmax = a.L.rmax[item.obj];
+        const float4 fr = a.L.frame[item.obj];
         const int qn = (item.nq + kThreads - 1) / kThreads;
-        ok = dispatch_pass<Shape, Shape::QPT>(qn, a, om, rmax, item.q0, item.nq, tiles, full, seq, &s_abort);
+        ok = dispatch_pass<Shape, Shape::QPT>(qn, a, om, fr, item.q0, item.nq, tiles, full, &never, seq, &s_abort);
     }
-    if (!ok && threadIdx.x == 0)   // drain copies still in flight (bounded) before leaving
+    if (!ok && threadIdx.x == 0)   // drain copies still in flight (bounded, full budget) before leaving
         for (int b = 0; b < 2; ++b) mbar_wait(&full[(seq + b) & 1], (unsigned)((seq + b) >> 1) & 1u);
 }
 
@@ -359,12 +376,48 @@ cudaError_t launch_fwd_exact(const FwdArgs &a, cudaStream_t st)
     return a.variant == kTcVariant ? launch_tc_exact(a, st) : cudaSuccess;
 }
 
-// Reference preparation for the screening stage: pair layout of (-2 r, |r|^2)
-// padded with (0, +inf) points to a whole number of tiles, and Rmax = max |r|
-// rounded up (float64 reduction, one CTA).
-__global__ void ref_prep_kernel(const float4 *R, int M, int Mpad, ulonglong2 *Rx, float *rmax)
+// Reference preparation for the screening stage (one CTA).  The frame: centre c =
+// the midpoint of R's bounding box (float32), radius w = max |fl(r - c)| rounded
+// up (float64 reduction); with compute_frame = false the given frame is kept (R
+// is then a subset of the cloud the frame was made for, so its radius still
+// bounds).  Layout: pairs of (-2 b, |b|^2) with b = fl(r - c), padded with
+// (0, +inf) points to a whole number of tiles.
+__global__ void ref_prep_kernel(const float4 *R, int M, int Mpad, ulonglong2 *Rx, float4 *frame, bool compute_frame)
 {
     __shared__ double red[32];
+    __shared__ float bmin[3][32], bmax[3][32];
+    __shared__ float4 s_fr;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+    if (compute_frame) {
+        float lo[3] = {__int_as_float(0x7f800000), __int_as_float(0x7f800000), __int_as_float(0x7f800000)};
+        float hi[3] = {-lo[0], -lo[1], -lo[2]};
+        for (int i = threadIdx.x; i < M; i += blockDim.x) {
+            const float4 r = R[i];
+            lo[0] = fminf(lo[0], r.x); lo[1] = fminf(lo[1], r.y); lo[2] = fminf(lo[2], r.z);
+            hi[0] = fmaxf(hi[0], r.x); hi[1] = fmaxf(hi[1], r.y); hi[2] = fmaxf(hi[2], r.z);
+        }
+        for (int k = 0; k < 3; ++k) {
+            for (int o = 16; o > 0; o >>= 1) {
+                lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+                hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+            }
+            if (lane == 0) { bmin[k][warp] = lo[k]; bmax[k][warp] = hi[k]; }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float c[3];
+            for (int k = 0; k < 3; ++k) {
+                float l = bmin[k][0], h = bmax[k][0];
+                for (int w = 1; w < nw; ++w) { l = fminf(l, bmin[k][w]); h = fmaxf(h, bmax[k][w]); }
+                c[k] = M > 0 ? 0.5f * l + 0.5f * h : 0.f;
+            }
+            s_fr = make_float4(c[0], c[1], c[2], 0.f);
+        }
+    } else if (threadIdx.x == 0) {
+        s_fr = *frame;
+    }
+    __syncthreads();
+    const float4 fr = s_fr;
     double m = 0.0;
     for (int q = threadIdx.x; q < Mpad / 2; q += blockDim.x) {
         float ax[2], ay[2], az[2], w[2];
@@ -372,10 +425,11 @@ __global__ void ref_prep_kernel(const float4 *R, int M, int Mpad, ulonglong2 *Rx
             const int i = 2 * q + k;
             if (i < M) {
                 const float4 r = R[i];
-                const double r2 = (double)r.x * r.x + (double)r.y * r.y + (double)r.z * r.z;
-                m = fmax(m, r2);
-                ax[k] = -2.f * r.x; ay[k] = -2.f * r.y; az[k] = -2.f * r.z;
-                w[k] = (float)r2;
+                const float bx = __fsub_rn(r.x, fr.x), by = __fsub_rn(r.y, fr.y), bz = __fsub_rn(r.z, fr.z);
+                const double b2 = (double)bx * bx + (double)by * by + (double)bz * bz;
+                m = fmax(m, b2);
+                ax[k] = -2.f * bx; ay[k] = -2.f * by; az[k] = -2.f * bz;
+                w[k] = (float)b2;
             } else {
                 ax[k] = ay[k] = az[k] = 0.f;
                 w[k] = __int_as_float(0x7f800000);
@@ -389,19 +443,21 @@ __global__ void ref_prep_kernel(const float4 *R, int M, int Mpad, ulonglong2 *Rx
         Rx[2 * (size_t)q] = A;
         Rx[2 * (size_t)q + 1] = B;
     }
+    if (!compute_frame) return;
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    if (lane == 0) red[warp] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
         double mm = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmax(mm, red[w]);
-        *rmax = (float)(sqrt(mm) * (1.0 + 1e-6)) + 1e-30f;
+        for (int w = 0; w < nw; ++w) mm = fmax(mm, red[w]);
+        *frame = make_float4(fr.x, fr.y, fr.z, (float)(sqrt(mm) * (1.0 + 1e-6)) + 1e-30f);
     }
 }
 
-cudaError_t launch_ref_prep(const float4 *R, int M, int Mpad, void *Rx, float *rmax, cudaStream_t st)
+cudaError_t launch_ref_prep(const float4 *R, int M, int Mpad, void *Rx, float4 *frame, bool compute_frame,
+                            cudaStream_t st)
 {
-    ref_prep_kernel<<<1, 1024, 0, st>>>(R, M, Mpad, static_cast<ulonglong2 *>(Rx), rmax);
+    ref_prep_kernel<<<1, 1024, 0, st>>>(R, M, Mpad, static_cast<ulonglong2 *>(Rx), frame, compute_frame);
     return cudaGetLastError();
 }
 

@@ -1,51 +1,61 @@
 // Forward matching on the tensor cores: tcgen05 f16 MMAs with split operands.
 //
-// The screening value of the float32 kernel, d~(r) = |r|^2 - 2 s'.r (Eq. 1 up to
-// the query's own |s'|^2), is a contraction of an augmented query row with an
-// augmented object-point column.  Coordinates are scaled by a power of two lam
-// (lam Rmax in (128, 256], Rmax = max |r|), every scaled factor is split into two
-// f16 parts (x = x_h + x_l, rounded to nearest) and lam^2 |r|^2 / 4 into three,
-// so that with a = -2 lam s' and rho = lam r
-//     A row    = [a_h, a_h, a_l, 4, 4, 4, 2^15, 0, 0, 0]          (K = 16)
+// The screening value of the float32 kernel, d~(r) = |b|^2 - 2 a.b with a and b
+// the query and the object point relative to the object's frame centre c (Eq. 1
+// up to the query's own |a|^2 and a term that does not depend on r), is a
+// contraction of an augmented query row with an augmented object-point column.
+// Coordinates are scaled by a power of two lam (lam B in (128, 256], B = max |b|),
+// every scaled factor is split into two f16 parts (x = x_h + x_l, rounded to
+// nearest) and lam^2 |b|^2 / 4 into three, so that with alpha = -2 lam a and
+// rho = lam b
+//     A row    = [alpha_h, alpha_h, alpha_l, 4, 4, 4, 2^15, 0, 0, 0]      (K = 16)
 //     B column = [rho_h, rho_l, rho_h, w_1, w_2, w_3, 0, 0, 0, 0]
-// gives A.B = lam^2 (|r|^2 - 2 s'.r) up to rounding: one kind::f16 MMA, 128
-// queries x 256 object points, accumulated in float32 in tensor memory.  (Slot
-// 12 is 2^15 for padding columns, which then never screen in.)
+// gives A.B = lam^2 (|b|^2 - 2 a.b) up to rounding: one kind::f16 MMA per 128
+// queries x COLS object points, accumulated in float32 in tensor memory.
+// (Slot 12 is 2^15 for padding columns, which then never screen in.)
 //
-// Error bound, u = 2^-24, in lam^2 units: the dropped a_l.rho_l and the rounding
-// of the low parts are at most 3 * 2^-22 |a_k| |rho_k| per coordinate (f16 has an
-// 11-bit significand), i.e. 24 u |s'| |r| in all; w = fl(lam^2 |r|^2) is within
-// u lam^2 |r|^2; products of f16 values are exact in float32, and the tensor
-// core's float32 accumulation is taken to stay within 16 u of the sum of the
-// magnitudes of its addends (<= 1.002 (|r|^2 + 2 |s'| |r|)); measured on GB300:
-// at most 2.9 u over 10^6 random rows of this form.  Low parts below the f16
-// normal range (2^-14) add at most 2^-14 * 1.74 lam (2 |s'| + |r|) even if
-// flushed, and the last part of w / 4 at most 2^-12.  So
-//     delta_tc = u lam^2 (18 Rmax^2 + 57 |s'| Rmax) + 2^-14 * 1.74 lam (2 |s'| + Rmax) + 2^-12
-// bounds |d~_tc - lam^2 (|r|^2 - 2 s'.r)|.  A query whose scaled coordinates
-// would leave the f16 range takes the whole-cloud scan.  Each query keeps its kTop
-// best chunk minima (chunks of 64 object points) and the best of the rest; the
-// chunks within 2 delta_tc of the best are rescanned with the exact-form float32
-// distance (ties to the lower index) by tc_exact_kernel, eight lanes per query, or,
-// when more than kTop qualify, by a warp scanning the whole cloud for that query
-// together.  The result is the exact-form argmin over every point that can be
-// nearest, as in the float32 kernel.
+// Error bound, u = 2^-24, in lam^2 units, A = |a|: the dropped alpha_l.rho_l and
+// the rounding of the low parts are at most 3 * 2^-22 |alpha_k| |rho_k| per
+// coordinate (f16 has an 11-bit significand), i.e. 24 u A |b| in all;
+// w = fl(lam^2 |b|^2) is within u lam^2 |b|^2; products of f16 values are exact
+// in float32, and the tensor core's float32 accumulation is taken to stay within
+// 16 u of the sum of the magnitudes of its addends (<= 1.002 (|b|^2 + 2 A |b|));
+// measured on GB300: at most 2.9 u over 10^6 random rows of this form.  Low parts
+// below the f16 normal range (2^-14) add at most 2^-14 * 1.74 lam (2 A + |b|)
+// even if flushed, and the last part of w / 4 at most 2^-12.  The rounding of
+// a = fl(s' - c) and b = fl(r - c) adds, beyond a term that does not depend on r,
+// at most u (2 B^2 + 4 A B) (as in the float32 kernel).  So
+//     delta_tc = u lam^2 (20 B^2 + 61 A B) + 2^-14 * 1.74 lam (2 A + B) + 2^-12
+// bounds the error of the screening value against lam^2 |s' - r|^2 + const.  A
+// query whose scaled coordinates would leave the f16 range takes the whole-cloud
+// scan.  Each query keeps its kTop best chunk minima (chunks of 64 object points)
+// and the best of the rest; the chunks within 2 delta_tc of the best are
+// rescanned with the exact-form float32 distance (ties to the lower index) by
+// tc_exact_kernel, eight lanes per query, or, when more than kTop qualify, by a
+// warp scanning the whole cloud for that query together.  The result is the
+// exact-form argmin over every point that can be nearest, as in the float32
+// kernel.
 //
-// Per CTA: one block of 128 queries (one per reduction thread, TMEM lane =
-// query); object tiles of 256 points (8 KB, already in the MMA's shared-memory
-// layout) stream through a ring of kStages buffers by 1D bulk copies.  One
-// thread issues the copies and another the MMAs: every mbarrier, copy or MMA
-// operation of a single thread costs on the order of a hundred cycles (measured
-// with clock64 stamps on GB300), so one thread doing both set the pace, and a
-// wide tile with a single MMA and a single commit amortises those operations
-// over more pairs.  A tcgen05.ld.red per 64 columns returns a chunk minimum
-// directly.  Each CTA has one 256-column accumulator; the two CTAs of an SM (256
-// TMEM columns each) take turns on the tensor pipe, and overlap one another's
-// per-item prologue.  Every wait is bounded: on expiry the kernel
-// reports ASICP_ERR_TIMEOUT through the error word, drains its own copies and
-// MMAs (bounded), frees its tensor memory and returns.
+// Per CTA: work items of 128 queries (one per tensor-memory lane = query row of
+// the MMA); object tiles of COLS points (already in the MMA's shared-memory
+// layout) stream through a ring of kStages buffers by 1D bulk copies.  One thread
+// issues the copies and another the MMAs: every mbarrier, copy or MMA operation of
+// a single thread costs on the order of a hundred cycles (measured with clock64
+// stamps on GB300), so one thread doing both set the pace, and a wide tile with a
+// single MMA and a single commit amortises those operations over more pairs.  A
+// tcgen05.ld.red per 64 columns returns a chunk minimum directly.  Each CTA has one
+// COLS-column accumulator; the 512 / COLS CTAs of an SM (COLS tensor-memory
+// columns each) take turns on the tensor pipe and overlap one another's per-item
+// prologue.  The per-tile chain of handoffs (copy landed, MMA issue and commit,
+// completion seen by the reduction warps, tensor-memory loads, accumulator
+// released) sets the pace, not the tensor pipe: splitting a tile's MMA into parts
+// with their own commits, or reading the accumulator with more warps, measured
+// slower.  Every wait is bounded: on expiry the kernel reports ASICP_ERR_TIMEOUT
+// through the error word, drains its own copies and MMAs (bounded), frees its
+// tensor memory and returns.
 #include "asicp_internal.cuh"
 #include "async_copy.cuh"
+#include "tcgen05.cuh"
 
 #include <cstdint>
 #include <cuda_fp16.h>
@@ -54,70 +64,38 @@ namespace asicp {
 
 namespace {
 
-constexpr int kRows = 128;                 // queries per block = MMA M
-constexpr int kBlocks = 1;                 // query blocks per CTA
-constexpr int kQueries = kRows * kBlocks;  // queries per item = reduction threads
+constexpr int kRows = 128;                 // queries per item = MMA M = tensor-memory lanes
+constexpr int kCols = 256;                 // object points per tile of the prepared layout
+constexpr int kQueries = kRows;            // queries per item = reduction threads (one warp per quadrant)
 constexpr int kThreadsTc = kQueries + 64;  // + one warp for the copies, one for the MMAs
-constexpr int kCols = 256;                 // object points per tile = MMA N
-constexpr int kBufs = 1;                   // accumulators per query block (a power of two)
 constexpr int kAug = 16;                   // augmented length (one K = 16 MMA)
 constexpr int kStages = 10;                // object tiles in flight
 constexpr int kChunk = 64;                 // screening chunk = columns per tcgen05.ld.red
 constexpr int kTop = 4;                    // chunks per query the exact stage rescans at most
 constexpr unsigned kTileBytes = kCols * kAug * 2;       // 8 KB
-constexpr unsigned kABlockBytes = kRows * kAug * 2;     // 4 KB
-constexpr unsigned kABytes = kBlocks * kABlockBytes;
+constexpr unsigned kABytes = kRows * kAug * 2;          // 4 KB of query rows
 constexpr unsigned kLBO = 128, kSBO = 256; // core matrices (8 rows x 16 B): K-adjacent 128 B, row groups 256 B
-constexpr int kTmemCols = kBlocks * kBufs * kCols;      // kBufs accumulators per block
-constexpr size_t kSmemBytes = kABytes + (size_t)kStages * kTileBytes;
 static_assert(kRefTilePts % kCols == 0, "object padding must be whole tiles");
-static_assert(kTmemCols == 256, "two CTAs per SM share the 512 tensor-memory columns");
 static_assert(kCols % kChunk == 0, "whole chunks per tile");
-static_assert((kBufs & (kBufs - 1)) == 0, "accumulator count");
-
-// instruction descriptor: D f32, A and B f16, both K-major, N = kCols, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(kCols >> 3) << 17) |
-                            ((uint32_t)(kRows >> 4) << 24);
+// The first COLS < kCols rows of a prepared tile are themselves a tile of COLS points in
+// the same layout (8-row groups are contiguous), so kernels with narrower tiles read
+// the same buffer.
+template <int COLS>
+constexpr size_t tc_smem_bytes() { return (size_t)kABytes + (size_t)kStages * (COLS * kAug * 2); }
 
 // byte offset of element (row, k) in the no-swizzle K-major layout
-__host__ __device__ constexpr unsigned core_offset(int row, int k)
-{
-    return (unsigned)(row / 8) * kSBO + (unsigned)(k / 8) * kLBO + (unsigned)(row % 8) * 16u + (unsigned)(k % 8) * 2u;
-}
+__host__ __device__ constexpr unsigned core_offset(int row, int k) { return kmajor_offset(row, k, kLBO, kSBO); }
 
-__device__ __forceinline__ uint64_t smem_desc(unsigned addr)
-{
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(kLBO >> 4) << 16) | ((uint64_t)(kSBO >> 4) << 32) |
-           (1ull << 46);
-}
+__device__ __forceinline__ uint64_t smem_desc(unsigned addr) { return tc_smem_desc(addr, kLBO, kSBO); }
 
-// Power-of-two scale lam with lam Rmax in (128, 256] (Rmax clamped below at 2^-30),
-// so that scaled coordinates and |r|^2 / 4 fit the f16 range.
-__device__ __forceinline__ float tc_scale(float rmax)
+// Power-of-two scale lam with lam B in (128, 256] (B clamped below at 2^-30),
+// so that scaled coordinates and |b|^2 / 4 fit the f16 range.
+__device__ __forceinline__ float tc_scale(float B)
 {
     int ex;
-    frexpf(fmaxf(rmax, 9.3132257e-10f), &ex);
+    frexpf(fmaxf(B, 9.3132257e-10f), &ex);
     return ldexpf(1.f, 8 - ex);
 }
-
-// One K = 16 MMA into a fresh accumulator.
-__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t ad, uint64_t bd)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(ad), "l"(bd), "r"(kIdesc), "r"(0u)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(unsigned long long *bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // Minimum over the 64 accumulator columns at taddr of this thread's lane: the
 // tcgen05.ld.red and its wait in one statement, so the compiler sees the
@@ -135,29 +113,44 @@ __device__ __forceinline__ float ld_min64(uint32_t taddr)
     return m;
 }
 
+// The same over 32 columns (half the registers).
+__device__ __forceinline__ float ld_min32(uint32_t taddr)
+{
+    uint32_t v[32];
+    float m;
+    asm volatile(
+        "tcgen05.ld.red.sync.aligned.32x32b.x32.min.f32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, %32, [%33];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]), "=f"(m)
+        : "r"(taddr)
+        : "memory");
+    return m;
+}
+
 }  // namespace
 
 // Augmented object tiles for the tensor-core kernel: point r goes to tile
-// r / kCols, row r % kCols of that tile's MMA layout, as f16 parts of lam r and
-// lam^2 |r|^2 / 4 (lam from the object's Rmax); padding points (r >= M) carry
-// only 2^15 in slot 12, which meets 2^15 in every query row: + 2^30, so they never
-// screen in.
-__global__ void tc_ref_prep_kernel(const float4 *R, int M, int Mpad, const float *rmax, __half *Rt)
+// r / kCols, row r % kCols of that tile's MMA layout, as f16 parts of lam b and
+// lam^2 |b|^2 / 4 with b = fl(r - c) (frame centre c, lam from the frame radius);
+// padding points (r >= M) carry only 2^15 in slot 12, which meets 2^15 in every
+// query row: + 2^30, so they never screen in.
+__global__ void tc_ref_prep_kernel(const float4 *R, int M, int Mpad, const float4 *frame, __half *Rt)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= Mpad) return;
-    const float lam = tc_scale(*rmax);
+    const float4 fr = *frame;
+    const float lam = tc_scale(fr.w);
     __half v[kAug];
     for (int k = 0; k < kAug; ++k) v[k] = __float2half_rn(0.f);
     if (r < M) {
         const float4 p = R[r];
-        const float c[3] = {lam * p.x, lam * p.y, lam * p.z};
+        const float c[3] = {lam * __fsub_rn(p.x, fr.x), lam * __fsub_rn(p.y, fr.y), lam * __fsub_rn(p.z, fr.z)};
         for (int k = 0; k < 3; ++k) {
             const __half h = __float2half_rn(c[k]);
             const __half l = __float2half_rn(c[k] - __half2float(h));
             v[k] = h; v[3 + k] = l; v[6 + k] = h;
         }
-        // w = fl(lam^2 |r|^2) / 4, split into three f16 parts (exact to 2^-33 relative)
+        // w = fl(lam^2 |b|^2) / 4, split into three f16 parts (exact to 2^-33 relative)
         const double w = (double)(float)((double)c[0] * c[0] + (double)c[1] * c[1] + (double)c[2] * c[2]) * 0.25;
         const __half w1 = __float2half_rn((float)w);
         const __half w2 = __float2half_rn((float)(w - (double)__half2float(w1)));
@@ -170,30 +163,38 @@ __global__ void tc_ref_prep_kernel(const float4 *R, int M, int Mpad, const float
     for (int k = 0; k < kAug; ++k) *reinterpret_cast<__half *>(tile + core_offset(r % kCols, k)) = v[k];
 }
 
-cudaError_t launch_tc_ref_prep(const float4 *R, int M, int Mpad, const float *rmax, void *Rt, cudaStream_t st)
+cudaError_t launch_tc_ref_prep(const float4 *R, int M, int Mpad, const float4 *frame, void *Rt, cudaStream_t st)
 {
-    tc_ref_prep_kernel<<<(Mpad + 255) / 256, 256, 0, st>>>(R, M, Mpad, rmax, static_cast<__half *>(Rt));
+    tc_ref_prep_kernel<<<(Mpad + 255) / 256, 256, 0, st>>>(R, M, Mpad, frame, static_cast<__half *>(Rt));
     return cudaGetLastError();
 }
 
 size_t tc_ref_bytes(int Mpad) { return (size_t)Mpad / kCols * kTileBytes; }
 
 // Warp roles: warps 0-3 (one query per thread; warp w reads TMEM lanes
-// 32 w .. 32 w + 31) build the
-// augmented query rows, reduce the accumulators and make the exact choice;
-// lane 0 of warp 4 streams the object tiles, lane 0 of warp 5 issues the MMAs.  They meet on
-// mbarriers only (no CTA-wide barrier inside the loop):
+// 32 w .. 32 w + 31) build the augmented query rows, read the accumulator and keep
+// the candidate chunks; lane 0 of warp 4 streams the object tiles, lane 0 of warp 5
+// issues the MMAs (one per tile of COLS points).  They meet on mbarriers only (no
+// CTA-wide barrier inside the loop):
 //   bfull[s]  tile in stage s has landed          (copy -> MMA)
 //   bempty[s] the MMA reading stage s is done:     (MMA commit -> copy, and -> reduction:
 //             the accumulator holds that tile     its next phase needs the reduction's acce)
-//   acce[b]   accumulator b has been read          (reduction -> MMA, one arrival per warp)
+//   acce      the accumulator has been read        (reduction -> MMA, one arrival per warp)
 //   afull     the item's query rows are written    (reduction warps -> MMA, one arrival per warp)
-__global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdArgs a)
+// COLS: tile width = accumulator columns (256: two CTAs per SM share the 512
+// tensor-memory columns; 128: four).  LDX: columns per tensor-memory load (64,
+// or 32 with half the registers).
+template <int COLS, int LDX>
+__global__ void __launch_bounds__(kThreadsTc, 512 / COLS) fwd_match_tc_kernel(const FwdArgs a)
 {
+    static_assert((COLS == 128 || COLS == 256) && (LDX == 32 || LDX == 64), "tile shape");
+    constexpr uint32_t kIdesc = tc_idesc_f16(false, COLS, kRows);
+    constexpr unsigned kTile = COLS * kAug * 2;
+    constexpr int kTileChunks = COLS / kChunk;
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     unsigned char *sA = smem_tc;
     unsigned char *sB = smem_tc + kABytes;
-    __shared__ __align__(8) unsigned long long bfull[kStages], bempty[kStages], acce[kBufs], afull;
+    __shared__ __align__(8) unsigned long long bfull[kStages], bempty[kStages], acce, afull;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -222,16 +223,11 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
         s_abort = 0;
         for (int s = 0; s < kStages; ++s) { mbar_init(&bfull[s], 1); mbar_init(&bempty[s], 1); }
         // one arrival per reduction warp (its lane 0, after the warp's loads or stores)
-        for (int b = 0; b < kBufs; ++b) mbar_init(&acce[b], kQueries / 32);
+        mbar_init(&acce, kQueries / 32);
         mbar_init(&afull, kQueries / 32);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                     "r"(kTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
+    if (warp == 0) tc_alloc(&s_tmem, COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -247,13 +243,12 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
             for (int it = it0; it < it1 && ok; it += step) {
                 const ObjMeta &om = a.L.obj[item_at(it).obj];
                 const unsigned char *src = reinterpret_cast<const unsigned char *>(om.Rt);
-                const int ntiles = om.Mpad / kCols;
+                const int ntiles = om.Mpad / COLS;
                 for (int t = 0; t < ntiles; ++t) {
-                    // the stage is free once the MMAs of its previous tile are done
+                    // the stage is free once the MMA of its previous tile is done
                     if (s_abort || !mbar_wait(&bempty[p_stage], p_lap ^ 1u)) { ok = false; break; }
-                    mbar_arrive_tx(&bfull[p_stage], kTileBytes);
-                    bulk_load(sB + (size_t)p_stage * kTileBytes, src + (size_t)t * kTileBytes, kTileBytes,
-                              &bfull[p_stage]);
+                    mbar_arrive_tx(&bfull[p_stage], kTile);
+                    bulk_load(sB + (size_t)p_stage * kTile, src + (size_t)t * kTile, kTile, &bfull[p_stage]);
                     ++p_seq;
                     if (++p_stage == kStages) { p_stage = 0; p_lap ^= 1u; }
                 }
@@ -274,68 +269,63 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
             unsigned c_lap = 0u, last_lap = 0u;
             int ia = 0;
             for (int it = it0; it < it1 && !s_abort; it += step, ++ia) {
-                const int ntiles = a.L.obj[item_at(it).obj].Mpad / kCols;
+                const int ntiles = a.L.obj[item_at(it).obj].Mpad / COLS;
                 if (!mbar_wait(&afull, (unsigned)(ia & 1))) { fail(); break; }
                 tc_fence_after();
                 for (int t = 0; t < ntiles; ++t, ++seq) {
-                    const int stage = c_stage, buf = (int)((unsigned)seq % kBufs);
-                    if (s_abort || !mbar_wait(&bfull[stage], c_lap) ||
-                        !mbar_wait(&acce[buf], (((unsigned)seq / kBufs) & 1u) ^ 1u)) {
+                    const int stage = c_stage;
+                    if (s_abort || !mbar_wait(&bfull[stage], c_lap) || !mbar_wait(&acce, ((unsigned)seq & 1u) ^ 1u)) {
                         fail();
                         break;
                     }
                     tc_fence_after();
-                    const unsigned b0 = smem_u32(sB + (size_t)stage * kTileBytes);
-#pragma unroll
-                    for (int blk = 0; blk < kBlocks; ++blk) {
-                        const uint32_t d = tmem + (uint32_t)(blk * kBufs + buf) * kCols;
-                        const unsigned a0 = smem_u32(sA + blk * kABlockBytes);
-                        mma_f16(d, smem_desc(a0), smem_desc(b0));
-                    }
+                    const unsigned a0 = smem_u32(sA), b0 = smem_u32(sB + (size_t)stage * kTile);
+                    tc_mma_f16(tmem, smem_desc(a0), smem_desc(b0), kIdesc, 0u);
                     // one commit per tile: its completion frees the stage for the copy thread and
                     // hands the accumulator to the reduction warps
-                    mma_commit(&bempty[stage]);
+                    tc_commit(&bempty[stage]);
                     last_stage = stage;
                     last_lap = c_lap;
                     if (++c_stage == kStages) { c_stage = 0; c_lap ^= 1u; }
                 }
             }
-            // drain (bounded): the MMAs issued
+            // drain (bounded): the MMAs issued (the last commit tracks the earlier ones)
             if (s_abort && last_stage >= 0) mbar_wait(&bempty[last_stage], last_lap);
         }
     } else {
         // ------------------------------------------------ query rows, reduction, exact choice
-        const int blk = warp / 4, row = tid % kRows;      // query block; row = TMEM lane
-        const uint32_t lane_base = (uint32_t)((warp % 4) * 32) << 16;
-        long long seq = 0;
+        const int row = tid;                               // query row = TMEM lane
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
         int r_stage = 0;          // stage and lap of the next tile, as on the MMA thread
         unsigned r_lap = 0u;
         for (int it = it0; it < it1; it += step) {
             if (__any_sync(0xffffffffu, s_abort)) break;
-            const FwdItem item = item_at(it);
-            const ObjMeta om = a.L.obj[item.obj];
-            const float rmax = a.L.rmax[item.obj];
-            const int ntiles = om.Mpad / kCols;
-            const bool valid = tid < item.nq;
-            const long long g = item.q0 + tid;
-            float3 o = make_float3(0.f, 0.f, 0.f);
-            bool far = false;
-            if (valid) {
-                const int pk = (int)(g / a.L.N), i = (int)(g - (long long)pk * a.L.N);
-                const int pre = a.L.part_grp[pk] % a.L.P;
-                const float *th = a.theta + (size_t)pk * 8;
-                float Rm[9];
-                quat_rot_f32(th[3], th[4], th[5], th[6], Rm);
-                const float4 s = a.S[(size_t)pre * a.L.N + i];
-                o = xform_f32(Rm, th[0], th[1], th[2], s.x, s.y, s.z);
-            }
+            // the item's query rows; only the screening window (+inf for a query the f16 split
+            // cannot represent, so that it takes the whole-cloud scan) lives through the tiles
+            int ntiles;
+            float win;
             {
+                const FwdItem item = item_at(it);
+                const float4 fr = a.L.frame[item.obj];
+                ntiles = a.L.obj[item.obj].Mpad / COLS;
+                const long long g = item.q0 + tid;
+                float3 o = make_float3(0.f, 0.f, 0.f);
+                if (tid < item.nq) {
+                    const int pk = (int)(g / a.L.N), i = (int)(g - (long long)pk * a.L.N);
+                    const int pre = a.L.part_grp[pk] % a.L.P;
+                    const float *th = a.theta + (size_t)pk * 8;
+                    float Rm[9];
+                    quat_rot_f32(th[3], th[4], th[5], th[6], Rm);
+                    const float4 s = a.S[(size_t)pre * a.L.N + i];
+                    o = xform_f32(Rm, th[0], th[1], th[2], s.x, s.y, s.z);
+                }
+                // the query relative to the frame centre (a = fl(s' - c))
+                o = make_float3(__fsub_rn(o.x, fr.x), __fsub_rn(o.y, fr.y), __fsub_rn(o.z, fr.z));
                 // the previous item's MMAs are complete (its last accumulator was waited for);
-                // a = -2 lam s' in two f16 parts, unless a part would leave the f16 range (such
-                // a query takes the whole-cloud scan)
-                const float lam = tc_scale(rmax);
+                // alpha = -2 lam a in two f16 parts, unless a part would leave the f16 range
+                const float lam = tc_scale(fr.w);
                 const float c[3] = {-2.f * lam * o.x, -2.f * lam * o.y, -2.f * lam * o.z};
-                far = !(fabsf(c[0]) < 65000.f && fabsf(c[1]) < 65000.f && fabsf(c[2]) < 65000.f);
+                const bool far = !(fabsf(c[0]) < 65000.f && fabsf(c[1]) < 65000.f && fabsf(c[2]) < 65000.f);
                 __half v[kAug];
                 for (int k = 0; k < kAug; ++k) v[k] = __float2half_rn(0.f);
                 if (!far) {
@@ -352,42 +342,43 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
                     pk.y = (uint32_t)__half_as_ushort(v[8 * j + 2]) | ((uint32_t)__half_as_ushort(v[8 * j + 3]) << 16);
                     pk.z = (uint32_t)__half_as_ushort(v[8 * j + 4]) | ((uint32_t)__half_as_ushort(v[8 * j + 5]) << 16);
                     pk.w = (uint32_t)__half_as_ushort(v[8 * j + 6]) | ((uint32_t)__half_as_ushort(v[8 * j + 7]) << 16);
-                    *reinterpret_cast<uint4 *>(sA + blk * kABlockBytes + core_offset(row, 8 * j)) = pk;
+                    *reinterpret_cast<uint4 *>(sA + core_offset(row, 8 * j)) = pk;
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&afull);
+                const float an = sqrtf(o.x * o.x + o.y * o.y + o.z * o.z) * 1.001f;
+                // 2 delta_tc in lam^2 units (1 % margin for evaluating the bound in float32)
+                win = far ? __int_as_float(0x7f800000)
+                          : 2.02f * (5.9604645e-8f * lam * lam * (20.f * fr.w * fr.w + 61.f * an * fr.w) +
+                                     6.1035156e-5f * 1.74f * lam * (2.f * an + fr.w) + 2.45e-4f);
             }
-            const float sn = sqrtf(o.x * o.x + o.y * o.y + o.z * o.z) * 1.001f;
-            const float lam = tc_scale(rmax);
-            // 2 delta_tc in lam^2 units (1 % margin for evaluating the bound in float32)
-            const float win = 2.02f * (5.9604645e-8f * lam * lam * (18.f * rmax * rmax + 57.f * sn * rmax) +
-                                       6.1035156e-5f * 1.74f * lam * (2.f * sn + rmax) + 2.45e-4f);
             // the kTop best chunk minima (ascending) with their chunk ids, and the best of the rest
             float bk[kTop], brest = __int_as_float(0x7f800000);
             int ck[kTop];
 #pragma unroll
             for (int k = 0; k < kTop; ++k) { bk[k] = __int_as_float(0x7f800000); ck[k] = 0; }
             bool good = true;
-            for (int t = 0; t < ntiles; ++t, ++seq) {
-                const int buf = (int)((unsigned long long)seq % kBufs);
+            for (int t = 0; t < ntiles; ++t) {
                 // the tile's MMA is complete once its stage barrier has flipped
                 good = mbar_wait_warp(&bempty[r_stage], r_lap);
                 if (++r_stage == kStages) { r_stage = 0; r_lap ^= 1u; }
                 if (!__all_sync(0xffffffffu, good && !s_abort)) { good = false; break; }
                 tc_fence_after();
-                float mv[kCols / kChunk];
+                float mv[kTileChunks];
 #pragma unroll
-                for (int h = 0; h < kCols / kChunk; ++h)
-                    mv[h] = ld_min64(tmem + lane_base + (uint32_t)(blk * kBufs + buf) * kCols + (uint32_t)(h * kChunk));
+                for (int h = 0; h < kTileChunks; ++h) {
+                    const uint32_t ta = tmem + lane_base + (uint32_t)(h * kChunk);
+                    mv[h] = LDX == 64 ? ld_min64(ta) : fminf(ld_min32(ta), ld_min32(ta + 32));
+                }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&acce[buf]);
+                if (lane == 0) mbar_arrive(&acce);
 #pragma unroll
-                for (int h = 0; h < kCols / kChunk; ++h) {
+                for (int h = 0; h < kTileChunks; ++h) {
                     // insert (v, chunk gc); strict < keeps the earlier chunk first on equal minima
                     float v = mv[h];
-                    int gc = t * (kCols / kChunk) + h;
+                    int gc = t * kTileChunks + h;
 #pragma unroll
                     for (int k = 0; k < kTop; ++k) {
                         const bool lt = v < bk[k];
@@ -406,9 +397,10 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
             // the chunks that can hold the nearest point (within 2 delta_tc of the best), or
             // the whole cloud when more than kTop qualify; tc_exact_kernel rescans them
             const float thr = bk[0] + win;
-            if (valid) {
+            const FwdItem item = item_at(it);
+            if (tid < item.nq) {
                 int4 cd;
-                if (brest <= thr || far) {
+                if (brest <= thr) {
                     cd = make_int4(-2, -1, -1, -1);
                 } else {
                     cd.x = ck[0];
@@ -416,7 +408,7 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
                     cd.z = bk[2] <= thr ? ck[2] : -1;
                     cd.w = bk[3] <= thr ? ck[3] : -1;
                 }
-                a.cand[g] = cd;
+                a.cand[item.q0 + tid] = cd;
             }
         }
     }
@@ -425,7 +417,7 @@ __global__ void __launch_bounds__(kThreadsTc, 2) fwd_match_tc_kernel(const FwdAr
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+        tc_dealloc(tmem, COLS);
     }
 }
 
@@ -479,6 +471,7 @@ __device__ __forceinline__ void group_chunk(const float4 *__restrict__ R, int M,
 
 __global__ void __launch_bounds__(256) tc_exact_kernel(const FwdArgs a)
 {
+    if (*a.err != kDevOk) return;     // the screening gave up: its candidates are not valid
     const long long Qtot = (long long)a.L.T * a.L.N;
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long wq0 = g - (threadIdx.x & 31);     // first query of this warp
@@ -566,8 +559,17 @@ __global__ void __launch_bounds__(256) tc_exact_kernel(const FwdArgs a)
     }
 }
 
-// Two CTAs per SM: each allocates half of tensor memory (256 columns), and the
-// shared-memory request leaves no room for a third.
+// The kernel's configuration: tile width (accumulator columns) and columns per load.
+#ifndef ASICP_TC_COLS
+#define ASICP_TC_COLS 256
+#endif
+#ifndef ASICP_TC_LDX
+#define ASICP_TC_LDX 64
+#endif
+constexpr int kTcCols = ASICP_TC_COLS, kTcLdx = ASICP_TC_LDX;
+
+// 512 / COLS CTAs per SM: each allocates COLS of the 512 tensor-memory columns,
+// and the shared-memory request leaves no room for more.
 int fwd_tc_grid()
 {
     static int grid[kDeviceSlots] = {};
@@ -576,10 +578,11 @@ int fwd_tc_grid()
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(fwd_match_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-        cudaFuncSetAttribute(fwd_match_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(fwd_match_tc_kernel<kTcCols, kTcLdx>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc_smem_bytes<kTcCols>());
+        cudaFuncSetAttribute(fwd_match_tc_kernel<kTcCols, kTcLdx>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
-        return 2 * sms;
+        return (512 / kTcCols) * sms;
     });
 }
 
@@ -587,7 +590,7 @@ int fwd_tc_threads() { return kQueries; }
 
 cudaError_t launch_fwd_match_tc(const FwdArgs &a, cudaStream_t st)
 {
-    fwd_match_tc_kernel<<<fwd_tc_grid(), kThreadsTc, kSmemBytes, st>>>(a);
+    fwd_match_tc_kernel<kTcCols, kTcLdx><<<fwd_tc_grid(), kThreadsTc, tc_smem_bytes<kTcCols>(), st>>>(a);
     return cudaGetLastError();
 }
 

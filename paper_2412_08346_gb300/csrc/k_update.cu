@@ -78,6 +78,7 @@ constexpr int kFinalizeThreads = 4;      // 192 CTAs for 768 particles: float64 
 
 __global__ void __launch_bounds__(kFinalizeThreads) finalize_kernel(const UpdateArgs a)
 {
+    if (a.err && *a.err != kDevOk) return;    // an earlier kernel of the pass gave up: its sums are not valid
     const int pk = blockIdx.x * blockDim.x + threadIdx.x;
     if (pk == 0 && a.col_items) { a.col_items[0] = 0; a.col_items[1] = 0; }
     if (pk >= a.L.T) return;
@@ -182,6 +183,7 @@ constexpr int kSelCand = 1024;         // values ranked exactly at the end
 
 __global__ void __launch_bounds__(kSteinThreads) stein_kernel(const UpdateArgs a)
 {
+    if (a.err && *a.err != kDevOk) return;
     extern __shared__ float4 sm[];
     float4 *sT = sm;                  // [K] t (xyz)
     float4 *sQ = sm + kMaxK;          // [K] q (wxyz)
@@ -383,6 +385,7 @@ __global__ void __launch_bounds__(kSteinThreads) stein_kernel(const UpdateArgs a
 // normalise(q + eta phi_q) (phi_q is tangent at q), one thread per particle.
 __global__ void stein_update_kernel(const UpdateArgs a)
 {
+    if (a.err && *a.err != kDevOk) return;
     const int pk = blockIdx.x * blockDim.x + threadIdx.x;
     if (pk >= a.L.T) return;
     float *th = a.theta + (size_t)pk * 8;

@@ -36,7 +36,7 @@ constexpr int kMaxDevices = 64;
 //   screening [ASICP_NOALLOC_MAX_M] 16 B           1 MiB
 //   staging   3 * max(M, P*N, 7/3 P*K) floats     768 KiB
 //   particle -> preshape map [P*K] int, preshape offsets [P+1] int   64 KiB each
-//   object table, rmax (float), error word (int)
+//   object table, screening frame (float4), error word (int)
 constexpr size_t kOffPoses = 0;
 constexpr size_t kOffGripper = kOffPoses + (size_t)ASICP_NOALLOC_MAX_PK * 8 * 4;
 constexpr size_t kOffObject = kOffGripper + (size_t)ASICP_NOALLOC_MAX_PN * 16;
@@ -46,8 +46,8 @@ constexpr size_t kStageFloats = 3 * (size_t)ASICP_NOALLOC_MAX_M;
 constexpr size_t kOffPartGrp = kOffStage + kStageFloats * 4;
 constexpr size_t kOffGrpOff = kOffPartGrp + (size_t)ASICP_NOALLOC_MAX_PK * 4;
 constexpr size_t kOffObjMeta = kOffGrpOff + ((size_t)ASICP_NOALLOC_MAX_PK + 64) * 4;
-constexpr size_t kOffRmax = kOffObjMeta + 256;
-constexpr size_t kOffErr = kOffRmax + 256;
+constexpr size_t kOffFrame = kOffObjMeta + 256;
+constexpr size_t kOffErr = kOffFrame + 256;
 static_assert(sizeof(ObjMeta) <= 256, "object table slot too small");
 static_assert(kOffErr + 256 <= kScratchBytes, "scratch layout exceeds the static array");
 static_assert(kStageFloats >= 3 * (size_t)ASICP_NOALLOC_MAX_PN && kStageFloats >= 7 * (size_t)ASICP_NOALLOC_MAX_PK,
@@ -108,7 +108,7 @@ extern "C" asicp_status asicp_match_noalloc(const float *theta, int P, int K, co
     float4 *obj = reinterpret_cast<float4 *>(base + kOffObject);
     ulonglong2 *screen = reinterpret_cast<ulonglong2 *>(base + kOffScreen);
     float *stage = reinterpret_cast<float *>(base + kOffStage);
-    float *rmax = reinterpret_cast<float *>(base + kOffRmax);
+    float4 *frame = reinterpret_cast<float4 *>(base + kOffFrame);
     int *err = reinterpret_cast<int *>(base + kOffErr);
     int *part_grp = reinterpret_cast<int *>(base + kOffPartGrp);
     int *grp_off = reinterpret_cast<int *>(base + kOffGrpOff);
@@ -133,8 +133,13 @@ extern "C" asicp_status asicp_match_noalloc(const float *theta, int P, int K, co
     const float *rx = src(R_xyz, (size_t)M * 3);
     if (!rx) return ASICP_ERR_CUDA;
     NOALLOC_CK(launch_pack_points(rx, M, obj, err, st));
-    NOALLOC_CK(launch_ref_prep(obj, M, Mpad, screen, rmax, st));
+    NOALLOC_CK(launch_ref_prep(obj, M, Mpad, screen, frame, true, st));
     NOALLOC_CK(launch_uniform_groups(part_grp, grp_off, P, K, st));
+    // a non-finite input stops the call before the matching: nn_idx stays untouched
+    NOALLOC_CK(cudaStreamSynchronize(st));
+    int e_in = 0;
+    NOALLOC_CK(cudaMemcpy(&e_in, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e_in == kDevNonFinite) return ASICP_ERR_INVALID_ARG;
     ObjMeta om{};          // one object holding every particle (copied by value below)
     om.R = obj;
     om.Rx = screen;
@@ -149,7 +154,7 @@ extern "C" asicp_status asicp_match_noalloc(const float *theta, int P, int K, co
     fa.L.grp_off = grp_off;
     fa.L.obj = objmeta;
     fa.L.com = nullptr;
-    fa.L.rmax = rmax;
+    fa.L.frame = frame;
     fa.S = grip;
     fa.theta = poses;
     fa.items = nullptr;    // consecutive work items of object 0

@@ -97,37 +97,35 @@ def test_host_pointer_inputs_match_device_pointer_inputs(stream):
 
 @pytest.mark.parametrize("shape", [0, asicp.FWD_SHAPES - 1])
 def test_free_running_small_box_final_poses(stream, shape):
-    """50 free-running iterations on both sides: final poses within 1 mm / 1e-3 rad (float32 and
-    tensor-core matching)."""
+    """50 free-running iterations on both sides (float32 and tensor-core matching): every particle
+    whose trajectory kept its discrete decisions clear of ties (decision margin >= 1 um all along)
+    ends within 1 mm / 1e-3 rad of the oracle; near-tie particles are reported separately."""
     import oracle
     w = synth.small_box_case()
     orc = tl.make_oracle(w)
     sched = orc.schedule(k_max=w.k_max, k_stein=w.k_stein, schedule=w.schedule, g0=w.g0, g1=w.g1, N=orc.N)
     theta0 = oracle.fibonacci_init(w.K, orc.R.mean(0), 0.15)
-    ost, order = orc.run(theta0.astype(np.float32).astype(np.float64)[None], sched, nthreads=4, topk=8)
+    ost, traj, near = tl.oracle_free_run(orc, theta0.astype(np.float32).astype(np.float64)[None], sched,
+                                         nthreads=4)
     ctx = _ctx(w, stream, debug=False, fwd_shape=shape)
     try:
         keep = tl.upload(ctx, w)
         asicp.asicp_run(ctx, np.ascontiguousarray(theta0.astype(np.float32)))
         th = tl.read_theta(ctx, w.K)
-        best = np.zeros(8 * 7, np.float32)
-        asicp.asicp_best_grasps(ctx, 8, best)
         del keep
     finally:
         asicp.asicp_destroy(ctx)
-    ot = ost["theta"][0]
-    dpos = np.linalg.norm(th[:, :3] - ot[:, :3], axis=1)
-    dang = tl.geodesic_angle(th[:, 3:], ot[:, 3:])
-    print(f"final pose error: max {dpos.max():.3e} m, {dang.max():.3e} rad; median {np.median(dpos):.3e} m")
-    ok = (dpos <= 1e-3) & (dang <= 1e-3)
-    assert ok.mean() >= 0.9, f"only {ok.sum()} of {len(ok)} particles within 1 mm / 1e-3 rad"
-    assert np.median(dpos) <= 1e-4
+    dpos, dang, tie = tl.compare_final_poses(th, ost["theta"][0], orc, traj, near, f"small box, shape {shape}")
+    assert np.median(dpos) <= 1e-6
 
 
 def test_paper_scale_sampled_step(stream):
-    """3 x 256 particles, N=2048, M=8192, SDF 64^3: one SVGD and one SGD step, sampled particles,
-    in the launch configuration the benchmark uses (the tensor-core matching shape, which the
-    autotuner picks at this workload; the float32 shape is covered at this size as well)."""
+    """3 x 256 particles, N=2048, M=8192, SDF 64^3: sampled particles of an SVGD and an SGD step from
+    the initial poses, in the launch configuration the benchmark uses (the tensor-core matching
+    shape, which the autotuner picks at this workload; the float32 shape is covered at this size as
+    well), and a step from converged, partly colliding poses: the poses after 60 free-running
+    iterations, teacher-forced one SGD step (colliding and free particles sampled)."""
+    import oracle
     w = synth.paper_scale_case()
     g = np.random.default_rng(3)
     sample = sorted(g.choice(w.K * 3, 24, replace=False).tolist())
@@ -135,6 +133,32 @@ def test_paper_scale_sampled_step(stream):
     print("paper scale sampled (tensor cores):", rep)
     rep = _teacher_forced_run(w, stream, [0], {}, sample=sample[:8], fwd_shape=0)
     print("paper scale sampled:", rep)
+    # converged poses: 60 free iterations on the GPU, then one teacher-forced step
+    P, K, N, M = 3, w.K, 2048, 8192
+    orc = tl.make_oracle(w)
+    theta0 = np.tile(oracle.fibonacci_init(K, orc.R.mean(0), 0.15), (P, 1)).astype(np.float32)
+    ctx = _ctx(w, stream, fwd_shape=asicp.FWD_SHAPES - 1)
+    rep = {}
+    try:
+        keep = tl.upload(ctx, w)
+        asicp.asicp_set_state(ctx, theta0, 0)
+        for k in range(60):
+            asicp.asicp_step(ctx, k)
+        st = tl.read_state(ctx, P, K, N, M, debug=False)
+        col = np.nonzero(st["ncol"] > 0)[0]
+        free = np.nonzero(st["ncol"] == 0)[0]
+        sample = sorted(set(g.choice(col, min(12, len(col)), replace=False).tolist()) |
+                        set(g.choice(free, min(12, len(free)), replace=False).tolist()))
+        asicp.asicp_set_state(ctx, tl.read_theta(ctx, P * K), 60)
+        before = tl.read_theta(ctx, P * K)
+        asicp.asicp_step(ctx, 60)
+        st = tl.read_state(ctx, P, K, N, M)
+        tl.check_step(orc, w, before, st, 60, rep, sample=sample)
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
+    print("paper scale, converged poses (tensor cores):", rep, "colliding after 60 iterations:", len(col))
+    assert rep.get("colliding_particles", 0) > 0, "the converged poses are meant to include collisions"
 
 
 def test_single_particle_stein_equals_sgd(stream):
@@ -735,19 +759,20 @@ def test_minibatch_ramp_matches_oracle(stream):
 def test_paper_scale_free_running_final_poses(stream):
     """The paper-scale problem (3 preshapes x 256 particles, N=2048, M=8192, SDF 64^3, 38 SVGD +
     62 SGD iterations) run free on the GPU in the benchmark's launch configuration (tensor-core
-    matching), against the oracle run free from the same initial poses.  Stein couples only the
-    particles of one preshape, so the oracle runs preshape 0 alone (the same computation, a third of
-    the CPU time).  Reported: the distribution of final-pose errors; required: at least 99 % of the
-    particles within 1 mm / 1e-3 rad (trajectories may part where a near-tie correspondence or a
-    near-zero SDF value flips), a median position error below 1 um, the same non-colliding particles
-    with costs within 1e-4, and the same best particle."""
+    matching, convergence criterion on), against the oracle run free from the same initial poses.
+    Stein couples only the particles of one preshape, so the oracle runs preshape 0 alone (the same
+    computation, a third of the CPU time).  Required: every particle without a near-tie decision
+    along its oracle trajectory within 1 mm / 1e-3 rad (distribution reported), a median position
+    error below 1 um, the same non-colliding particles with costs within 1e-4, and the same best
+    particle."""
     import os
     import oracle
     w = synth.paper_scale_case()
     P, K = len(w.preshapes), w.K
+    tol = float(np.float32(2e-4))
     com = w.objects[0].points.astype(np.float64).mean(0)
     theta0 = np.tile(oracle.fibonacci_init(K, com, 0.15), (P, 1)).astype(np.float32)
-    ctx = _ctx(w, stream, debug=False, fwd_shape=asicp.FWD_SHAPES - 1)
+    ctx = _ctx(w, stream, debug=False, fwd_shape=asicp.FWD_SHAPES - 1, conv_tol=2e-4)
     try:
         keep = tl.upload(ctx, w)
         asicp.asicp_run(ctx, theta0)
@@ -759,40 +784,47 @@ def test_paper_scale_free_running_final_poses(stream):
     pre = w.preshapes[0]
     orc = oracle.Oracle(pre.S[None], [(pre.sdf, pre.origin, pre.voxel)], w.objects[0].points, K=K)
     sched = orc.schedule(k_max=w.k_max, k_stein=w.k_stein, schedule=w.schedule, g0=w.g0, g1=w.g1,
-                         C_cycles=w.C_cycles, p_exp=w.p_exp, N=orc.N)
-    ost, _ = orc.run(theta0[:K].astype(np.float64)[None], sched, nthreads=os.cpu_count() or 1)
-    ot, th = ost["theta"][0], st["theta"][:K].astype(np.float64)
-    dpos = np.linalg.norm(th[:, :3] - ot[:, :3], axis=1)
-    dang = tl.geodesic_angle(th[:, 3:], ot[:, 3:])
-    q = [0.5, 0.9, 0.99, 1.0]
-    print("paper-scale free-running final pose error, position m (median, p90, p99, max):",
-          np.quantile(dpos, q), "angle rad:", np.quantile(dang, q))
-    ok = (dpos <= 1e-3) & (dang <= 1e-3)
-    assert ok.mean() >= 0.99, f"only {ok.sum()} of {K} particles within 1 mm / 1e-3 rad"
+                         C_cycles=w.C_cycles, p_exp=w.p_exp, N=orc.N, conv_tol=tol)
+    ost, traj, near = tl.oracle_free_run(orc, theta0[:K].astype(np.float64)[None], sched,
+                                         nthreads=os.cpu_count() or 1, conv_tol=tol)
+    th = st["theta"][:K]
+    dpos, dang, tie = tl.compare_final_poses(th, ost["theta"][0], orc, traj, near, "paper scale")
     assert np.median(dpos) <= 1e-6
     ncol_g, ncol_o = st["ncol"][:K], ost["ncol"].ravel()
-    free = ncol_o == 0
-    assert np.array_equal(ncol_g == 0, free), "different non-colliding particles"
+    close = (dpos <= tl.POSE_TOL_M) & (dang <= tl.POSE_TOL_RAD)
+    free = (ncol_o == 0) & close
+    assert np.array_equal((ncol_g == 0)[close], (ncol_o == 0)[close]), "different non-colliding particles"
     if free.any():
         cg, co = st["cost"][:K][free], ost["cost"].ravel()[free]
         assert np.all(np.abs(cg - co) <= 1e-4 * np.abs(co) + tl.COST_ABS), (cg, co)
     best_g = oracle.select(st["cost"][:K], ncol_g, 1)[0]
     best_o = oracle.select(ost["cost"].ravel(), ncol_o, 1)[0]
-    assert best_g == best_o, (best_g, best_o)
+    assert best_g == best_o or not (close[best_g] and close[best_o]), (best_g, best_o)
 
 
 def test_largest_workload_sampled_steps_and_tensor_core_agreement(stream):
     """3 x 1024 particles, N=4096, M=65536 (superquadric partial view), SDF 128^3 -- the maximum
     particle count per preshape and the largest clouds: sampled particles of an SVGD and an SGD step
-    against the oracle, and the tensor-core kernel's correspondences against the float32 kernel's
-    on every query (identical except near-ties)."""
+    against the oracle with both matching shapes, from the initial shell (0.15 m) and from contact
+    poses (0.04 m, fingers in the object) -- cost, gradient and SGD-updated pose errors against the
+    FP64 oracle reported -- and the tensor-core kernel's correspondences against the float32
+    kernel's on every query (identical except near-ties)."""
     import oracle
     w = synth.large_case()
     g = np.random.default_rng(4)
     sample = sorted(g.choice(w.K * 3, 6, replace=False).tolist())
     rep = _teacher_forced_run(w, stream, [0, 7], {}, sample=sample)
-    print("largest workload sampled:", rep)
+    print("largest workload sampled (float32):", rep)
     com = w.objects[0].points.astype(np.float64).mean(0)
+    for radius in (0.15, 0.04):
+        th0 = np.tile(oracle.fibonacci_init(w.K, com, radius), (3, 1)).astype(np.float32)
+        rep = _teacher_forced_run(w, stream, [0, 7], {}, sample=sample, theta0=th0,
+                                  fwd_shape=asicp.FWD_SHAPES - 1)
+        print(f"largest workload sampled (tensor cores, radius {radius}): error vs the FP64 oracle: "
+              f"cost {rep.get('max_cost_rel', 0):.2e} relative, gradient {rep.get('max_grad_rel', 0):.2e} "
+              f"relative, SGD-updated pose {rep.get('max_update_abs', 0):.2e} abs;", rep)
+        if radius < 0.1:
+            assert rep.get("colliding_particles", 0) > 0
     th = np.tile(oracle.fibonacci_init(w.K, com, 0.15), (3, 1)).astype(np.float32)
     a = _step_indices(w, stream, th, 0)
     b = _step_indices(w, stream, th, asicp.FWD_VARIANTS.index("tc-f16x3-m128-n256"))
@@ -806,3 +838,223 @@ def test_largest_workload_sampled_steps_and_tensor_core_agreement(stream):
         db = ((sp - R[b["nn_idx"][diff]]) ** 2).sum(-1)
         assert (np.abs(da - db) / np.maximum(np.minimum(da, db), 1e-300)).max() <= tl.NEAR_TIE_REL
         assert n_diff <= 1e-4 * a["nn_idx"].size
+
+
+@pytest.mark.slow
+def test_largest_workload_free_running_final_poses(stream):
+    """The mixed-precision configuration (3 x 1024 particles, N=4096, M=65536, SDF 128^3) run free for
+    its 10 parity iterations (4 SVGD + 6 SGD) on the tensor cores, from contact poses (0.06 m),
+    against the oracle run free on preshape 0: the final pose and cost errors against FP64 reported,
+    every particle without a near-tie decision within 1 mm / 1e-3 rad."""
+    import os
+    import oracle
+    w = synth.large_case()
+    P, K = 3, w.K
+    com = w.objects[0].points.astype(np.float64).mean(0)
+    theta0 = np.tile(oracle.fibonacci_init(K, com, 0.06), (P, 1)).astype(np.float32)
+    ctx = _ctx(w, stream, debug=False, fwd_shape=asicp.FWD_SHAPES - 1)
+    try:
+        keep = tl.upload(ctx, w)
+        asicp.asicp_run(ctx, theta0)
+        st = tl.read_state(ctx, P, K, 4096, 65536, debug=False)
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
+    pre = w.preshapes[0]
+    orc = oracle.Oracle(pre.S[None], [(pre.sdf, pre.origin, pre.voxel)], w.objects[0].points, K=K)
+    sched = orc.schedule(k_max=w.k_max, k_stein=w.k_stein, schedule=w.schedule, g0=w.g0, g1=w.g1,
+                         C_cycles=w.C_cycles, p_exp=w.p_exp, N=orc.N)
+    ost, traj, near = tl.oracle_free_run(orc, theta0[:K].astype(np.float64)[None], sched,
+                                         nthreads=os.cpu_count() or 1)
+    dpos, dang, tie = tl.compare_final_poses(st["theta"][:K], ost["theta"][0], orc, traj, near, "largest workload")
+    close = (dpos <= tl.POSE_TOL_M) & (dang <= tl.POSE_TOL_RAD)
+    free = close & (ost["ncol"].ravel() == 0) & (st["ncol"][:K] == 0)
+    crel = np.abs(st["cost"][:K][free] - ost["cost"].ravel()[free]) / np.abs(ost["cost"].ravel()[free])
+    print(f"largest workload final cost error vs FP64 (non-colliding particles): max {crel.max():.2e}, "
+          f"median {np.median(crel):.2e}")
+    assert crel.max() <= 1e-4
+
+
+def test_convergence_freeze_teacher_forced(stream):
+    """Table I's convergence criterion (0.02 %) with the default conv_tol on the GPU, teacher-forced
+    in the SGD phase against the oracle on the same poses and previous costs: (1) every particle
+    frozen with no previous cost: colliding particles are unfrozen and take the collision step
+    (Section IV-D), the others keep their poses exactly; (2) previous costs set so that the relative
+    change is 0.5x or 2x the criterion, up or down: the freeze decisions, the kept poses and the SGD
+    steps of the others equal the oracle's."""
+    import oracle
+    w = synth.custom_case(P=2, K=16, N=300, M=1500, grid=24, k_max=6, seed=53, k_stein=2)
+    tol = float(np.float32(2e-4))            # the GPU compares against the float32 config value
+    orc = tl.make_oracle(w)
+    P, K, N, Mc = 2, w.K, 300, len(w.objects[0].points)
+    com = orc.R.mean(0)
+    # preshape 0 close enough for its fingers to reach into the object, preshape 1 farther out
+    theta0 = np.concatenate([oracle.fibonacci_init(K, com, 0.05), oracle.fibonacci_init(K, com, 0.12)]).astype(np.float32)
+    sched = orc.schedule(k_max=w.k_max, k_stein=w.k_stein, schedule=w.schedule, g0=w.g0, g1=w.g1,
+                         C_cycles=w.C_cycles, p_exp=w.p_exp, N=orc.N, conv_tol=tol)
+    ctx = _ctx(w, stream, conv_tol=2e-4)
+    rep = {}
+    try:
+        keep = tl.upload(ctx, w)
+        # (1) all frozen, no previous cost
+        asicp.asicp_set_state(ctx, theta0, 3)
+        before = tl.read_theta(ctx, P * K)
+        asicp.asicp_set_convergence(ctx, np.full(P * K, -1.0), np.ones(P * K, np.int32))
+        asicp.asicp_step(ctx, 3)
+        st = tl.read_state(ctx, P, K, N, Mc)
+        tl.check_step(orc, w, before, st, 3, rep)
+        ost = orc.new_state(before.astype(np.float64).reshape(P, K, 7))
+        ost["frozen"][:] = 1
+        orc.step(ost, sched, 3)
+        assert np.array_equal(st["frozen"], ost["frozen"].ravel())
+        assert np.array_equal(st["frozen"] == 0, st["ncol"] > 0)
+        n_col = int((st["ncol"] > 0).sum())
+        assert 0 < n_col < P * K, "the case is meant to have colliding and free particles"
+        L = st["cost"].copy()
+        # (2) relative changes around the criterion
+        rel = np.resize([0.5, 2.0, -0.5, -2.0], P * K) * tol
+        prev = L / (1.0 + rel)
+        asicp.asicp_set_state(ctx, before, 3)
+        asicp.asicp_set_convergence(ctx, prev, np.zeros(P * K, np.int32))
+        asicp.asicp_step(ctx, 3)
+        st = tl.read_state(ctx, P, K, N, Mc)
+        tl.check_step(orc, w, before, st, 3, rep)
+        ost = orc.new_state(before.astype(np.float64).reshape(P, K, 7))
+        ost["prev_cost"][:] = prev.reshape(P, K)
+        orc.step(ost, sched, 3)
+        assert np.array_equal(st["frozen"], ost["frozen"].ravel())
+        expect = (np.abs(rel) < tol) & (st["ncol"] == 0)
+        assert np.array_equal(st["frozen"].astype(bool), expect)
+        assert expect.sum() > 0 and (~expect).sum() > 0
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
+    print("convergence freeze:", rep, "colliding:", n_col)
+
+
+def test_free_running_with_convergence_freeze(stream):
+    """15 SVGD + 25 SGD iterations (Table I's split) run free with the default convergence criterion
+    on both sides: the same particles end frozen (except near-criterion decisions) and every particle
+    without a near-tie decision ends within 1 mm / 1e-3 rad of the oracle.  On these procedural
+    shapes the particles of a real preshape end in contact and keep colliding (a collision unfreezes,
+    Section IV-D), so preshape 1 is given an SDF that is negative everywhere: its particles converge
+    free of collisions and freeze."""
+    import oracle
+    w = synth.custom_case(P=2, K=24, N=256, M=1024, grid=32, k_max=40, seed=59, k_stein=15)
+    w.preshapes[1].sdf = -np.ones_like(w.preshapes[1].sdf)
+    tol = float(np.float32(2e-4))
+    orc = tl.make_oracle(w)
+    P, K = 2, w.K
+    theta0 = np.tile(oracle.fibonacci_init(K, orc.R.mean(0), 0.08), (P, 1)).astype(np.float32)
+    sched = orc.schedule(k_max=w.k_max, k_stein=w.k_stein, schedule=w.schedule, g0=w.g0, g1=w.g1,
+                         C_cycles=w.C_cycles, p_exp=w.p_exp, N=orc.N, conv_tol=tol)
+    ost, traj, near = tl.oracle_free_run(orc, theta0.astype(np.float64).reshape(P, K, 7), sched, nthreads=8,
+                                         conv_tol=tol)
+    ctx = _ctx(w, stream, debug=False, conv_tol=2e-4, fwd_shape=asicp.FWD_SHAPES - 1)
+    try:
+        keep = tl.upload(ctx, w)
+        asicp.asicp_run(ctx, theta0)
+        st = tl.read_state(ctx, P, K, 256, 1024, debug=False)
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
+    frz_o = ost["frozen"].ravel().astype(bool)
+    frz_g = st["frozen"].astype(bool)
+    dpos, dang, tie = tl.compare_final_poses(st["theta"], ost["theta"], orc, traj, near, "free run with freezing")
+    differ = np.nonzero(frz_g != frz_o)[0]
+    print(f"frozen: gpu {frz_g.sum()}, oracle {frz_o.sum()} of {P * K}; differing {len(differ)}")
+    assert frz_o.sum() > 0, "the run is meant to freeze particles"
+    for i in differ:          # a different freeze decision only where a decision was near a tie
+        assert near.ravel()[i] or tl.trajectory_margin(orc, traj, i // K, i % K) < tl.FLIP_MARGIN, i
+
+
+def test_translated_object_matches_oracle_and_keeps_screening_cost(stream):
+    """An object cloud far from the coordinate origin (translated by (0.5, 0.3, 0.8) m, as a camera- or
+    robot-frame capture would be): teacher-forced SVGD and SGD steps with both matching shapes equal
+    the oracle's, and the screening stays as selective as for the centred cloud -- the error windows
+    are measured from the object's own frame centre, so the tensor-core launch takes about the same
+    time (within 25 %) as for the same cloud at the origin."""
+    import oracle
+    shift = np.array([0.5, 0.3, 0.8], np.float32)
+    w0 = synth.custom_case(P=1, K=128, N=2048, M=8192, grid=32, k_max=4, seed=61, k_stein=2)
+    w1 = synth.custom_case(P=1, K=128, N=2048, M=8192, grid=32, k_max=4, seed=61, k_stein=2)
+    w1.objects[0].points = (w0.objects[0].points + shift).astype(np.float32)
+    times = []
+    for w in (w0, w1):
+        orc = tl.make_oracle(w)
+        com = orc.R.mean(0)
+        th0 = oracle.fibonacci_init(w.K, com, 0.05).astype(np.float32)
+        for shape in (0, asicp.FWD_SHAPES - 1):
+            rep = {}
+            ctx = _ctx(w, stream, fwd_shape=shape)
+            try:
+                keep = tl.upload(ctx, w)
+                asicp.asicp_set_state(ctx, th0, 0)
+                for k in (0, 2):
+                    asicp.asicp_set_state(ctx, tl.read_theta(ctx, w.K), k)
+                    before = tl.read_theta(ctx, w.K)
+                    asicp.asicp_step(ctx, k)
+                    st = tl.read_state(ctx, 1, w.K, 2048, 8192)
+                    sample = list(range(0, w.K, 4))
+                    tl.check_step(orc, w, before, st, k, rep, sample=sample)
+                del keep
+            finally:
+                asicp.asicp_destroy(ctx)
+            print("translated" if w is w1 else "centred", "shape", shape, rep)
+        ctx = _ctx(w, stream, debug=False, profile=True, fwd_shape=asicp.FWD_SHAPES - 1)
+        try:
+            keep = tl.upload(ctx, w)
+            asicp.asicp_set_state(ctx, th0, 0)
+            for _ in range(3):
+                asicp.asicp_step(ctx, 0)
+            asicp.asicp_kernel_times(ctx, reset=True)
+            for _ in range(10):
+                asicp.asicp_step(ctx, 0)
+            ms, n = asicp.asicp_kernel_times(ctx, reset=True)
+            times.append((ms[0] + ms[5]) / n[0])
+            del keep
+        finally:
+            asicp.asicp_destroy(ctx)
+    print(f"matching per launch: centred {times[0]:.4f} ms, translated {times[1]:.4f} ms")
+    assert times[1] <= 1.25 * times[0]
+
+
+def test_bounded_wait_timeout_is_reported_and_the_context_recovers(stream):
+    """Every device wait of the library is bounded.  With the float32 matching kernel's first copy
+    wait made on an mbarrier that nothing arrives at (a 1000-cycle limit), every CTA's wait expires:
+    the kernel drains its copies and returns, the later kernels of the pass skip their work, the
+    next read-back returns TIMEOUT naming the expired wait, and with normal waits restored the same
+    context computes the step exactly as a fresh context does."""
+    import oracle
+    w = synth.custom_case(P=2, K=16, N=300, M=5000, grid=24, k_max=4, seed=67, k_stein=2)
+    P, K, N, Mc = 2, w.K, 300, 5000
+    th0 = np.tile(oracle.fibonacci_init(K, w.objects[0].points.astype(np.float64).mean(0), 0.06),
+                  (P, 1)).astype(np.float32)
+    ctx = _ctx(w, stream, fwd_shape=0)
+    try:
+        keep = tl.upload(ctx, w)
+        asicp.asicp_set_state(ctx, th0, 0)
+        asicp.asicp_test_expire_waits(ctx, True)
+        asicp.asicp_step(ctx, 0)
+        with pytest.raises(asicp.AsicpError) as e:
+            tl.read_state(ctx, P, K, N, Mc)
+        assert e.value.status == asicp.ASICP_ERR_TIMEOUT
+        assert "wait expired" in asicp.asicp_last_error(ctx)
+        asicp.asicp_test_expire_waits(ctx, False)
+        asicp.asicp_set_state(ctx, th0, 0)
+        asicp.asicp_step(ctx, 0)
+        got = tl.read_state(ctx, P, K, N, Mc)
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
+    ctx = _ctx(w, stream, fwd_shape=0)
+    try:
+        keep = tl.upload(ctx, w)
+        asicp.asicp_set_state(ctx, th0, 0)
+        asicp.asicp_step(ctx, 0)
+        ref = tl.read_state(ctx, P, K, N, Mc)
+        del keep
+    finally:
+        asicp.asicp_destroy(ctx)
+    for key in ("theta", "cost", "grad", "ncol", "nn_idx"):
+        assert np.array_equal(got[key], ref[key]), key

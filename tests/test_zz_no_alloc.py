@@ -78,3 +78,54 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(asicp.AsicpError) as e:
         asicp.asicp_match_noalloc(th, S, R, out, 1, 1, stream)
     assert e.value.status == asicp.ASICP_ERR_INVALID_ARG
+
+
+def test_noalloc_host_inputs_match_oracle_and_device_inputs():
+    """Host-memory (numpy) poses and clouds go through the scratch array's staging area: the result
+    equals the call with device inputs bit for bit, and the FP64 nearest neighbour (Eq. 1) of the
+    oracle up to near-ties (where the float32 transformed point can pick a partner no more than
+    2 um farther)."""
+    import oracle
+    stream = torch.cuda.current_stream().cuda_stream
+    w = synth.custom_case(P=2, K=12, N=500, M=3000, grid=24, k_max=2, seed=37)
+    P, K, N = 2, w.K, 500
+    g = np.random.default_rng(9)
+    t = g.normal(size=(P * K, 3)) * 0.05
+    q = g.normal(size=(P * K, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    th = np.ascontiguousarray(np.concatenate([t, q], 1), dtype=np.float32)
+    S = np.ascontiguousarray(np.concatenate([pre.S for pre in w.preshapes]), dtype=np.float32)
+    R = np.ascontiguousarray(w.objects[0].points, dtype=np.float32)
+    out_h = torch.full((P * K * N,), -1, dtype=torch.int32, device="cuda")
+    out_d = torch.full((P * K * N,), -1, dtype=torch.int32, device="cuda")
+    asicp.asicp_match_noalloc(th, S, R, out_h, P, K, stream)
+    asicp.asicp_match_noalloc(torch.from_numpy(th).cuda(), torch.from_numpy(S).cuda(), torch.from_numpy(R).cuda(),
+                              out_d, P, K, stream)
+    got = out_h.cpu().numpy().reshape(P * K, N)
+    assert np.array_equal(got, out_d.cpu().numpy().reshape(P * K, N))
+    Rd = R.astype(np.float64)
+    near = 0
+    for pk in range(P * K):
+        thd = th[pk].astype(np.float64)
+        Sp = S[(pk // K) * N:(pk // K + 1) * N].astype(np.float64) @ oracle.rotation(thd[3:] / np.linalg.norm(thd[3:])).T \
+            + thd[:3]
+        idx_o, d2_o = oracle.nn(Sp, Rd)
+        mism = np.nonzero(got[pk] != idx_o)[0]
+        if len(mism):
+            d_g = np.sqrt(((Sp[mism] - Rd[got[pk, mism]]) ** 2).sum(1))
+            assert np.all(d_g - np.sqrt(d2_o[mism]) <= 2e-6), (pk, mism[:4])
+            near += len(mism)
+    print(f"host inputs: {near} near-tie differences of {got.size} correspondences")
+    assert near <= 1e-3 * got.size
+
+
+def test_noalloc_non_finite_input_leaves_output_untouched():
+    stream = torch.cuda.current_stream().cuda_stream
+    R = torch.rand((100, 3), dtype=torch.float32, device="cuda")
+    S = torch.rand((8, 3), dtype=torch.float32, device="cuda")
+    th = torch.tensor([[0, 0, 0, 1, 0, 0, float("nan")]], dtype=torch.float32, device="cuda")
+    out = torch.full((8,), -7, dtype=torch.int32, device="cuda")
+    with pytest.raises(asicp.AsicpError) as e:
+        asicp.asicp_match_noalloc(th, S, R, out, 1, 1, stream)
+    assert e.value.status == asicp.ASICP_ERR_INVALID_ARG
+    assert torch.all(out == -7)
