@@ -72,11 +72,13 @@ def flatten(layers) -> np.ndarray:
 
 
 def bf16(x: np.ndarray) -> np.ndarray:
-    """Round float64 values to bfloat16 (nearest, ties to even), returned as float64."""
-    f = np.asarray(x, dtype=np.float32)
-    u = f.view(np.uint32).astype(np.uint64)
-    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
-    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+    """Round float64 values to the nearest bfloat16 (8-bit significand, float32's exponent range,
+    ties to even), returned as float64: one rounding from the float64 value, with the spacing
+    2^(e-8) of the binade [2^(e-1), 2^e) (2^-133 below the normal range)."""
+    x = np.asarray(x, dtype=np.float64)
+    _, e = np.frexp(x)
+    e = np.maximum(e, -125)
+    return np.ldexp(np.rint(np.ldexp(x, 8 - e)), e - 8)
 
 
 def forward(flat: np.ndarray, cloud: np.ndarray, P: int, round_bf16: bool = True):

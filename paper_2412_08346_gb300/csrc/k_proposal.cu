@@ -4,7 +4,11 @@
 // mixture of SE(3) densities; forward, mixture loss, backward, Adam and
 // sampling kernels.  Weights and stored activations are bfloat16 (round to
 // nearest even), every product is accumulated in float32; master weights,
-// gradients and the Adam state are float32.
+// gradients and the Adam state are float32.  The two per-point bfloat16
+// contractions of the encoder (layers 2 and 3, every point of every cloud) run on
+// the tensor cores (tcgen05, kind::f16); the head layers (one row per object) and
+// the backward pass (float32 gradients as operands, which a bfloat16 or tf32 MMA
+// would round) run as float32 SIMT GEMMs.
 //
 // Network (x_i = r_i - centroid; W row-major [out][in]):
 //   h1 = relu(W1 x + b1) 3->64, h2 = relu(W2 h1 + b2) 64->128,
@@ -22,6 +26,7 @@
 // summed in object order, so a training step is deterministic.
 #include "../../include/asicp_proposal.h"
 #include "asicp_internal.cuh"
+#include "tcgen05.cuh"
 
 #include <cuda_bf16.h>
 
@@ -158,6 +163,113 @@ GemmArgs gargs(const void *A, int lda, const void *B, int ldb, void *C, int ldc,
     g.lda = lda; g.ldb = ldb; g.ldc = ldc;
     g.M = M; g.N = N; g.K = K;
     return g;
+}
+
+// ---------------------------------------------------------------- encoder layers on the tensor cores
+// C[r][n] = bf16(relu(sum_k A[r][k] W[n][k] + bias[n])) for the per-point layers 2
+// and 3 (K = 64 -> N = 128, K = 128 -> N = 256), both operands bfloat16: one CTA per
+// 128 points, the 128 x K rows and the whole N x K weight matrix staged in shared
+// memory in the no-swizzle K-major layout, K / 16 tcgen05 MMAs (kind::f16, bf16
+// operands, float32 accumulation in tensor memory) issued by one thread, then
+// each warp reads its 32 rows back 32 columns at a time, adds the bias, applies
+// the ReLU and rounds to bfloat16.  Products of bfloat16 values are exact in
+// float32, as in the SIMT kernel; the order of the float32 additions differs.  The
+// wait for the MMAs is bounded: on expiry the CTA sets *err and writes nothing.
+template <int K, int N>
+__global__ void __launch_bounds__(128) dense_relu_tc_kernel(const bf16 *A, const bf16 *W, const float *bias, bf16 *C,
+                                                            long long rows, int *err)
+{
+    constexpr unsigned kLbo = 128, kSbo = K * 16;     // K-adjacent core matrices; 8-row groups
+    constexpr unsigned kABytes = 128u * K * 2u;
+    constexpr uint32_t kIdesc = tc_idesc_f16(true, N, 128);
+    static_assert(K % 16 == 0 && N % 32 == 0 && N >= 32 && N <= 256 && (N & (N - 1)) == 0, "layer shape");
+    extern __shared__ __align__(1024) unsigned char sm_dense[];
+    unsigned char *sA = sm_dense, *sW = sm_dense + kABytes;
+    __shared__ __align__(8) unsigned long long done;
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const long long r = (long long)blockIdx.x * 128 + tid;
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(A + r * K);
+#pragma unroll
+        for (int j = 0; j < K / 8; ++j) {
+            const uint4 v = r < rows ? src[j] : make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4 *>(sA + kmajor_offset(tid, 8 * j, kLbo, kSbo)) = v;
+        }
+        for (int n = tid; n < N; n += 128) {
+            const uint4 *ws = reinterpret_cast<const uint4 *>(W + (size_t)n * K);
+#pragma unroll
+            for (int j = 0; j < K / 8; ++j) *reinterpret_cast<uint4 *>(sW + kmajor_offset(n, 8 * j, kLbo, kSbo)) = ws[j];
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (tid == 0) {
+        mbar_init(&done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tc_alloc(&s_tmem, N);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    if (tid == 0) {
+        const unsigned a0 = smem_u32(sA), w0 = smem_u32(sW);
+#pragma unroll
+        for (int kk = 0; kk < K / 16; ++kk)
+            tc_mma_f16(tmem, tc_smem_desc(a0 + kk * 2 * kLbo, kLbo, kSbo), tc_smem_desc(w0 + kk * 2 * kLbo, kLbo, kSbo),
+                       kIdesc, (uint32_t)kk);
+        tc_commit(&done);
+    }
+    bool ok = mbar_wait_warp(&done, 0);
+    if (!ok && (tid & 31) == 0) atomicExch(err, kDevTimeout);
+    tc_fence_after();
+#pragma unroll 1
+    for (int c0 = 0; c0 < N; c0 += 32) {
+        float v[32];
+        tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (ok && r < rows) {
+            uint32_t w[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const bf16 lo = __float2bfloat16_rn(fmaxf(v[2 * i] + bias[c0 + 2 * i], 0.f));
+                const bf16 hi = __float2bfloat16_rn(fmaxf(v[2 * i + 1] + bias[c0 + 2 * i + 1], 0.f));
+                w[i] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+            }
+            uint4 *dst = reinterpret_cast<uint4 *>(C + r * N + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        }
+    }
+    if (!ok) mbar_wait_warp(&done, 0);   // the MMAs must be done before the columns are freed (bounded)
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tc_dealloc(tmem, N);
+    }
+}
+
+// Shared memory of a CTA: its operands, and at least enough that no more CTAs fit on
+// an SM than its 512 tensor-memory columns hold (an allocation beyond them would
+// wait for another CTA to finish).
+template <int K, int N>
+constexpr size_t dense_smem_bytes()
+{
+    constexpr size_t operands = 128u * K * 2u + (size_t)N * K * 2u;
+    constexpr size_t per_sm = 228u * 1024u, floor_ = per_sm / (512 / N + 1) + 1024u;
+    return operands > floor_ ? operands : floor_;
+}
+
+template <int K, int N>
+cudaError_t launch_dense_relu_tc(const bf16 *A, const bf16 *W, const float *bias, bf16 *C, long long rows, int *err,
+                                 cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(dense_relu_tc_kernel<K, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dense_smem_bytes<K, N>());
+    if (e != cudaSuccess) return e;
+    dense_relu_tc_kernel<K, N><<<(unsigned)((rows + 127) / 128), 128, dense_smem_bytes<K, N>(), st>>>(A, W, bias, C,
+                                                                                                     rows, err);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- small kernels
@@ -447,7 +559,7 @@ struct asicp_prop {
     long long step = 0;
     int lastB = 0;
     Buf w, m, v, grad, slices, wbf, clouds, tg, cen, x, h1, h2, h3, g, arg, z, o, dO, lossp, dz, dg, dh3, dh2, dh1,
-        outb, drawb, thetab;
+        outb, drawb, thetab, errw;
 };
 
 namespace {
@@ -462,6 +574,18 @@ asicp_status prop_guard(F &&f)
         return e.st;
     } catch (const std::bad_alloc &) {
         return ASICP_ERR_OOM;
+    }
+}
+
+// After a synchronisation: a bounded device wait that expired (the tensor-core
+// layers) is reported as TIMEOUT, once.
+void check_device_error(asicp_prop *pr)
+{
+    int e = 0;
+    pck(cudaMemcpy(&e, pr->errw.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e != kDevOk) {
+        pck(cudaMemset(pr->errw.p, 0, sizeof(int)));
+        throw PropErr{ASICP_ERR_TIMEOUT};
     }
 }
 
@@ -483,14 +607,11 @@ void forward_impl(asicp_prop *pr, const float *clouds_dev, int B)
     layer1_kernel<<<(unsigned)((rows * kH1 + 255) / 256), 256, 0, st>>>(pr->x.as<bf16>(), W + pr->L[0].w,
                                                                         wf + pr->L[0].b, pr->h1.as<bf16>(), rows);
     pck(cudaGetLastError());
-    GemmArgs g2 = gargs(pr->h1.p, kH1, W + pr->L[1].w, kH1, pr->h2.p, kH2, (int)rows, kH2, kH1);
-    g2.bias = wf + pr->L[1].b;
-    g2.relu = 1;
-    pck(gemm<bf16, bf16, bf16, false, true>(g2, 1, st));
-    GemmArgs g3 = gargs(pr->h2.p, kH2, W + pr->L[2].w, kH2, pr->h3.p, kH3, (int)rows, kH3, kH2);
-    g3.bias = wf + pr->L[2].b;
-    g3.relu = 1;
-    pck(gemm<bf16, bf16, bf16, false, true>(g3, 1, st));
+    // layers 2 and 3: bfloat16 contractions over every point, on the tensor cores
+    pck(launch_dense_relu_tc<kH1, kH2>(pr->h1.as<bf16>(), W + pr->L[1].w, wf + pr->L[1].b, pr->h2.as<bf16>(), rows,
+                                        pr->errw.as<int>(), st));
+    pck(launch_dense_relu_tc<kH2, kH3>(pr->h2.as<bf16>(), W + pr->L[2].w, wf + pr->L[2].b, pr->h3.as<bf16>(), rows,
+                                        pr->errw.as<int>(), st));
     maxpool_kernel<<<B, kH3, 0, st>>>(pr->h3.as<bf16>(), pr->npts, pr->g.as<bf16>(), pr->arg.as<int>());
     pck(cudaGetLastError());
     GemmArgs g4 = gargs(pr->g.p, kH3, W + pr->L[3].w, kH3, pr->z.p, kHead, B, kHead, kH3);
@@ -605,6 +726,8 @@ asicp_status asicp_prop_create(int P, int n_points, int max_batch, void *cuda_st
         alloc(pr->dz, B * kHead * 4); alloc(pr->dg, B * kH3 * 4);
         alloc(pr->dh3, rows * kH3 * 4); alloc(pr->dh2, rows * kH2 * 4); alloc(pr->dh1, rows * kH1 * 4);
         alloc(pr->outb, B * pr->nout * 4);
+        alloc(pr->errw, sizeof(int));
+        pck(cudaMemsetAsync(pr->errw.p, 0, sizeof(int), pr->st));
         pck(cudaMemsetAsync(pr->w.p, 0, np * 4, pr->st));
         pck(cudaMemsetAsync(pr->m.p, 0, np * 4, pr->st));
         pck(cudaMemsetAsync(pr->v.p, 0, np * 4, pr->st));
@@ -659,6 +782,7 @@ asicp_status asicp_prop_forward(asicp_prop *pr, const float *clouds, int B, floa
         pck(cudaMemcpyAsync(out, pr->o.p, (size_t)B * pr->nout * 4, cudaMemcpyDefault, pr->st));
         if (centroids) pck(cudaMemcpyAsync(centroids, pr->cen.p, (size_t)B * 3 * 4, cudaMemcpyDefault, pr->st));
         pck(cudaStreamSynchronize(pr->st));
+        check_device_error(pr);
     });
 }
 
@@ -679,6 +803,7 @@ asicp_status asicp_prop_loss_grad(asicp_prop *pr, const float *clouds, const flo
         pck(cudaMemcpyAsync(lp.data(), pr->lossp.p, lp.size() * 4, cudaMemcpyDeviceToHost, pr->st));
         if (grad) pck(cudaMemcpyAsync(grad, pr->grad.p, pr->np * 4, cudaMemcpyDefault, pr->st));
         pck(cudaStreamSynchronize(pr->st));
+        check_device_error(pr);
         double s = 0.0;     // mean over objects of (1 / (P T)) sum over preshapes and targets
         for (float x : lp) s += x;
         *loss = (float)(s / ((double)pr->P * T * B));

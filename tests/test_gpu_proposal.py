@@ -3,10 +3,13 @@ oracle (oracle/proposal.py): forward outputs, loss, parameter gradients, the Ada
 sampling.
 
 Tolerances: both sides round the weights and the stored activations to bfloat16; the GPU
-sums in float32 and the oracle exactly, so an activation can land on the other side of a
-bfloat16 rounding boundary (one bfloat16 ulp, 2^-8 relative) and, rarely, a max-pool can pick
-another point.  Outputs and gradients are therefore compared by norms: <= 2 % relative per
-layer, cosine >= 0.999; the loss within 1e-3 relative."""
+sums in float32 and rounds that sum once, the oracle sums exactly and rounds once, so an
+activation can land on the other side of a bfloat16 rounding boundary (one bfloat16 ulp, 2^-8
+of its magnitude) and, rarely, a max-pool can pick another point.  Outputs and gradients are
+compared element by element: each within ELEM_ULPS bfloat16 ulps of its own magnitude plus
+FLOOR_ULPS ulps of its layer's rms (for values that cancel); the elements that differ by more
+than float32 rounding (a crossed bfloat16 boundary upstream) are counted and capped at
+MAX_CROSSED of the layer (measured on GB300: none); the loss within 1e-3 relative."""
 import numpy as np
 import pytest
 
@@ -37,6 +40,28 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
+ELEM_ULPS = 4.0          # bfloat16 ulps (2^-8 relative) of the element's own magnitude
+FLOOR_ULPS = 1.0         # bfloat16 ulps of the layer's rms
+F32_REL = 1e-5           # float32-level agreement: beyond it an element counts as crossed
+MAX_CROSSED = 0.01
+
+
+def _elementwise(a, b, what, stats):
+    """a (GPU) against b (oracle), element by element; returns the crossed fraction."""
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    rms = float(np.sqrt(np.mean(b ** 2))) if b.size else 0.0
+    err = np.abs(a - b)
+    tol = 2.0 ** -8 * (ELEM_ULPS * np.abs(b) + FLOOR_ULPS * rms) + 1e-30
+    worst = int(np.argmax(err / tol))
+    assert np.all(err <= tol), (f"{what}: element {worst} differs by {err[worst]:.3e} (gpu {a[worst]:.6e}, oracle "
+                                f"{b[worst]:.6e}, bound {tol[worst]:.3e}); {int((err > tol).sum())} of {a.size} beyond")
+    crossed = float(np.mean(err > F32_REL * (np.abs(b) + rms)))
+    stats[what] = (round(crossed, 4), float((err / tol).max()))
+    assert crossed <= MAX_CROSSED, f"{what}: {crossed:.3f} of the elements crossed a bfloat16 boundary"
+    return crossed
+
+
 @pytest.fixture(scope="module")
 def net():
     n = proposal.Proposal(P, NPTS, 8, torch.cuda.current_stream().cuda_stream)
@@ -50,10 +75,12 @@ def test_forward_matches_oracle(net):
     net.set_params(params)
     clouds, _ = _batch(4, 21)
     out, cen = net.forward(clouds, 4)
+    stats = {}
     for b in range(4):
         o, _, c = orc.forward(params, clouds[b], P)
         assert np.allclose(cen[b], c, rtol=0, atol=1e-6)
-        assert _rel(out[b], o) <= 0.02, f"object {b}: {_rel(out[b], o):.3e}"
+        _elementwise(out[b], o, f"object {b} outputs", stats)
+    print("forward (crossed fraction, worst error / bound):", stats)
 
 
 def test_loss_and_gradient_match_oracle(net):
@@ -64,12 +91,12 @@ def test_loss_and_gradient_match_oracle(net):
     lo, go = orc.loss_and_grad(params, list(clouds), list(tg), P)
     assert abs(loss - lo) <= 1e-3 * abs(lo), (loss, lo)
     start = 0
-    for (o, i) in orc.layer_shapes(P):
-        for n in (o * i, o):
-            a, b = grad[start:start + n], go[start:start + n]
-            cos = float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
-            assert _rel(a, b) <= 0.02 and cos >= 0.999, (start, n, _rel(a, b), cos)
+    stats = {}
+    for layer, (o, i) in enumerate(orc.layer_shapes(P)):
+        for kind, n in (("W", o * i), ("b", o)):
+            _elementwise(grad[start:start + n], go[start:start + n], f"d{kind}{layer + 1}", stats)
             start += n
+    print("gradients (crossed fraction, worst error / bound):", stats)
 
 
 def test_adam_step_matches_oracle(net):

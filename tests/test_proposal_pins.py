@@ -21,6 +21,19 @@ def test_bf16_rounding_known_values():
     assert got[0] == 1.0 and got[1] == 1.0 and got[2] == 1 + 2 ** -7 and got[3] == -2.5 and got[5] == 0.0
     assert got[6] == 1.0 and got[7] == 1 + 2 ** -6
     assert abs(got[4] - 3.0e-3) <= 2 ** -8 * 3.0e-3
+    # one rounding from float64: a value just above a tie goes up although its float32 rounding
+    # lands exactly on the tie (which would then go to the even neighbour)
+    just_above = 1 + 2 ** -8 + 2 ** -40
+    assert np.float32(just_above) == np.float32(1 + 2 ** -8)
+    assert pr.bf16(np.array([just_above]))[0] == 1 + 2 ** -7
+    # against a bit-level reference on random float32 values (exact in float64): same result
+    g = np.random.default_rng(1)
+    f = (g.normal(size=2000) * np.exp(g.uniform(-30, 30, 2000))).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    ref = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32).view(np.float32)
+    assert np.array_equal(pr.bf16(f.astype(np.float64)), ref.astype(np.float64))
+    # below float32's normal range the spacing is 2^-133
+    assert pr.bf16(np.array([3 * 2.0 ** -134]))[0] == 2 * 2.0 ** -133
 
 
 def test_single_component_density_is_gaussian_times_watson():
