@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--compare", type=int, default=0, metavar="OBJECTS",
                     help="the plain FP32 GPU method against the tensor-core / batched / shorter-budget forms at "
                          "equal final cost on OBJECTS paper-scale objects; prints its own JSON line")
+    ap.add_argument("--profile-proposal", action="store_true",
+                    help="one forward and one loss/gradient pass of the proposal network on 32 clouds of 2048 points "
+                         "(for profiler captures); no JSON line")
     ap.add_argument("--profile-case", action="store_true",
                     help="one short run of a reduced workload (1 preshape x 256 particles, N=2048, M=8192, "
                          "8 iterations, poses close enough to collide) for profiler captures; no JSON line")
@@ -461,6 +464,25 @@ def run_profile_case(args):
         asicp.asicp_destroy(ctx)
 
 
+def run_profile_proposal(args):
+    """The proposal network's kernels at the training batch size, for ncu."""
+    import torch
+    from paper_2412_08346_gb300 import learned_init, proposal, synth
+    stream = torch.cuda.current_stream().cuda_stream
+    clouds = learned_init.object_clouds(32, 2048, synth.BASE_SEED + 50_000)
+    tg = np.zeros((32, 3, 16, 7), np.float32)
+    tg[..., :3] = clouds.mean(1)[:, None, None, :]
+    tg[..., 3] = 1.0
+    net = proposal.Proposal(3, 2048, 32, stream)
+    try:
+        net.set_params(synth.proposal_params(3, synth.BASE_SEED))
+        out, _ = net.forward(clouds, 32)
+        loss, _ = net.loss_grad(clouds, tg, 32, 16)
+        print(f"proposal: outputs {out.shape}, loss {loss:.4f}")
+    finally:
+        net.close()
+
+
 def run_batched(args):
     """Many objects in one context (one launch per kernel for all of them, one captured loop) against the
     plain path (each object in its own context, run one after the other); same per-object results."""
@@ -778,6 +800,9 @@ def main():
         return
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.profile_proposal:
+        run_profile_proposal(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

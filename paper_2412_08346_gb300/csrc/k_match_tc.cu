@@ -75,13 +75,17 @@ constexpr int kTop = 4;                    // chunks per query the exact stage r
 constexpr unsigned kTileBytes = kCols * kAug * 2;       // 8 KB
 constexpr unsigned kABytes = kRows * kAug * 2;          // 4 KB of query rows
 constexpr unsigned kLBO = 128, kSBO = 256; // core matrices (8 rows x 16 B): K-adjacent 128 B, row groups 256 B
+#ifndef ASICP_TC_DBL_A
+#define ASICP_TC_DBL_A 0
+#endif
+constexpr bool kDblA = ASICP_TC_DBL_A != 0;  // two query-row buffers: the next item's rows written early
 static_assert(kRefTilePts % kCols == 0, "object padding must be whole tiles");
 static_assert(kCols % kChunk == 0, "whole chunks per tile");
 // The first COLS < kCols rows of a prepared tile are themselves a tile of COLS points in
 // the same layout (8-row groups are contiguous), so kernels with narrower tiles read
 // the same buffer.
 template <int COLS>
-constexpr size_t tc_smem_bytes() { return (size_t)kABytes + (size_t)kStages * (COLS * kAug * 2); }
+constexpr size_t tc_smem_bytes() { return (size_t)(kDblA ? 2 : 1) * kABytes + (size_t)kStages * (COLS * kAug * 2); }
 
 // byte offset of element (row, k) in the no-swizzle K-major layout
 __host__ __device__ constexpr unsigned core_offset(int row, int k) { return kmajor_offset(row, k, kLBO, kSBO); }
@@ -113,18 +117,52 @@ __device__ __forceinline__ float ld_min64(uint32_t taddr)
     return m;
 }
 
-// The same over 32 columns (half the registers).
-__device__ __forceinline__ float ld_min32(uint32_t taddr)
+// Write the query row of global query g (valid or not) of an item on the object with
+// frame fr into the row buffer sA at row `row`; returns the screening window 2 delta_tc
+// in lam^2 units (+inf for a query the f16 split cannot represent, so that it takes
+// the whole-cloud scan).
+__device__ __forceinline__ float build_query_row(const FwdArgs &a, long long g, bool valid, float4 fr,
+                                                 unsigned char *sA, int row)
 {
-    uint32_t v[32];
-    float m;
-    asm volatile(
-        "tcgen05.ld.red.sync.aligned.32x32b.x32.min.f32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, %32, [%33];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]), "=f"(m)
-        : "r"(taddr)
-        : "memory");
-    return m;
+    float3 o = make_float3(0.f, 0.f, 0.f);
+    if (valid) {
+        const int pk = (int)(g / a.L.N), i = (int)(g - (long long)pk * a.L.N);
+        const int pre = a.L.part_grp[pk] % a.L.P;
+        const float *th = a.theta + (size_t)pk * 8;
+        float Rm[9];
+        quat_rot_f32(th[3], th[4], th[5], th[6], Rm);
+        const float4 s = a.S[(size_t)pre * a.L.N + i];
+        o = xform_f32(Rm, th[0], th[1], th[2], s.x, s.y, s.z);
+    }
+    // the query relative to the frame centre (a = fl(s' - c))
+    o = make_float3(__fsub_rn(o.x, fr.x), __fsub_rn(o.y, fr.y), __fsub_rn(o.z, fr.z));
+    // alpha = -2 lam a in two f16 parts, unless a part would leave the f16 range
+    const float lam = tc_scale(fr.w);
+    const float c[3] = {-2.f * lam * o.x, -2.f * lam * o.y, -2.f * lam * o.z};
+    const bool far = !(fabsf(c[0]) < 65000.f && fabsf(c[1]) < 65000.f && fabsf(c[2]) < 65000.f);
+    __half v[kAug];
+    for (int k = 0; k < kAug; ++k) v[k] = __float2half_rn(0.f);
+    if (!far) {
+        for (int k = 0; k < 3; ++k) {
+            const __half h = __float2half_rn(c[k]);
+            v[k] = h; v[3 + k] = h; v[6 + k] = __float2half_rn(c[k] - __half2float(h));
+        }
+    }
+    v[9] = v[10] = v[11] = __float2half_rn(4.f);
+    v[12] = __float2half_rn(32768.f);
+    for (int j = 0; j < kAug / 8; ++j) {
+        uint4 pk;
+        pk.x = (uint32_t)__half_as_ushort(v[8 * j + 0]) | ((uint32_t)__half_as_ushort(v[8 * j + 1]) << 16);
+        pk.y = (uint32_t)__half_as_ushort(v[8 * j + 2]) | ((uint32_t)__half_as_ushort(v[8 * j + 3]) << 16);
+        pk.z = (uint32_t)__half_as_ushort(v[8 * j + 4]) | ((uint32_t)__half_as_ushort(v[8 * j + 5]) << 16);
+        pk.w = (uint32_t)__half_as_ushort(v[8 * j + 6]) | ((uint32_t)__half_as_ushort(v[8 * j + 7]) << 16);
+        *reinterpret_cast<uint4 *>(sA + core_offset(row, 8 * j)) = pk;
+    }
+    const float an = sqrtf(o.x * o.x + o.y * o.y + o.z * o.z) * 1.001f;
+    // 2 delta_tc in lam^2 units (1 % margin for evaluating the bound in float32)
+    return far ? __int_as_float(0x7f800000)
+               : 2.02f * (5.9604645e-8f * lam * lam * (20.f * fr.w * fr.w + 61.f * an * fr.w) +
+                          6.1035156e-5f * 1.74f * lam * (2.f * an + fr.w) + 2.45e-4f);
 }
 
 }  // namespace
@@ -181,20 +219,20 @@ size_t tc_ref_bytes(int Mpad) { return (size_t)Mpad / kCols * kTileBytes; }
 //             the accumulator holds that tile     its next phase needs the reduction's acce)
 //   acce      the accumulator has been read        (reduction -> MMA, one arrival per warp)
 //   afull     the item's query rows are written    (reduction warps -> MMA, one arrival per warp)
-// COLS: tile width = accumulator columns (256: two CTAs per SM share the 512
-// tensor-memory columns; 128: four).  LDX: columns per tensor-memory load (64,
-// or 32 with half the registers).
-template <int COLS, int LDX>
+// COLS: tile width = accumulator columns; 512 / COLS CTAs per SM share the 512
+// tensor-memory columns (256: two; 128-column tiles with four CTAs per SM
+// measured slower, their registers capped at 80).
+template <int COLS>
 __global__ void __launch_bounds__(kThreadsTc, 512 / COLS) fwd_match_tc_kernel(const FwdArgs a)
 {
-    static_assert((COLS == 128 || COLS == 256) && (LDX == 32 || LDX == 64), "tile shape");
+    static_assert(COLS == 128 || COLS == 256, "tile width");
     constexpr uint32_t kIdesc = tc_idesc_f16(false, COLS, kRows);
     constexpr unsigned kTile = COLS * kAug * 2;
     constexpr int kTileChunks = COLS / kChunk;
     extern __shared__ __align__(1024) unsigned char smem_tc[];
-    unsigned char *sA = smem_tc;
-    unsigned char *sB = smem_tc + kABytes;
-    __shared__ __align__(8) unsigned long long bfull[kStages], bempty[kStages], acce, afull;
+    unsigned char *sA = smem_tc;                               // [kDblA ? 2 : 1][kABytes]
+    unsigned char *sB = smem_tc + (kDblA ? 2 : 1) * kABytes;
+    __shared__ __align__(8) unsigned long long bfull[kStages], bempty[kStages], acce, afull[2];
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -224,7 +262,8 @@ __global__ void __launch_bounds__(kThreadsTc, 512 / COLS) fwd_match_tc_kernel(co
         for (int s = 0; s < kStages; ++s) { mbar_init(&bfull[s], 1); mbar_init(&bempty[s], 1); }
         // one arrival per reduction warp (its lane 0, after the warp's loads or stores)
         mbar_init(&acce, kQueries / 32);
-        mbar_init(&afull, kQueries / 32);
+        mbar_init(&afull[0], kQueries / 32);
+        mbar_init(&afull[1], kQueries / 32);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) tc_alloc(&s_tmem, COLS);
@@ -270,7 +309,9 @@ __global__ void __launch_bounds__(kThreadsTc, 512 / COLS) fwd_match_tc_kernel(co
             int ia = 0;
             for (int it = it0; it < it1 && !s_abort; it += step, ++ia) {
                 const int ntiles = a.L.obj[item_at(it).obj].Mpad / COLS;
-                if (!mbar_wait(&afull, (unsigned)(ia & 1))) { fail(); break; }
+                // with two row buffers item ia uses buffer ia % 2 (its phase ia / 2), else buffer 0
+                const int ab = kDblA ? (ia & 1) : 0;
+                if (!mbar_wait(&afull[ab], kDblA ? (unsigned)((ia >> 1) & 1) : (unsigned)(ia & 1))) { fail(); break; }
                 tc_fence_after();
                 for (int t = 0; t < ntiles; ++t, ++seq) {
                     const int stage = c_stage;
@@ -279,7 +320,7 @@ __global__ void __launch_bounds__(kThreadsTc, 512 / COLS) fwd_match_tc_kernel(co
                         break;
                     }
                     tc_fence_after();
-                    const unsigned a0 = smem_u32(sA), b0 = smem_u32(sB + (size_t)stage * kTile);
+                    const unsigned a0 = smem_u32(sA + ab * kABytes), b0 = smem_u32(sB + (size_t)stage * kTile);
                     tc_mma_f16(tmem, smem_desc(a0), smem_desc(b0), kIdesc, 0u);
                     // one commit per tile: its completion frees the stage for the copy thread and
                     // hands the accumulator to the reduction warps
@@ -298,60 +339,29 @@ __global__ void __launch_bounds__(kThreadsTc, 512 / COLS) fwd_match_tc_kernel(co
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
         int r_stage = 0;          // stage and lap of the next tile, as on the MMA thread
         unsigned r_lap = 0u;
-        for (int it = it0; it < it1; it += step) {
+        // the first item's query rows
+        float win_cur = 0.f;
+        if (kDblA) {
+            const FwdItem item = item_at(it0);
+            win_cur = build_query_row(a, item.q0 + tid, tid < item.nq, a.L.frame[item.obj], sA, row);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&afull[0]);
+        }
+        int ia = 0;
+        for (int it = it0; it < it1; it += step, ++ia) {
             if (__any_sync(0xffffffffu, s_abort)) break;
-            // the item's query rows; only the screening window (+inf for a query the f16 split
-            // cannot represent, so that it takes the whole-cloud scan) lives through the tiles
-            int ntiles;
-            float win;
-            {
+            // the item's query rows (built here, or during the previous item with two row
+            // buffers); only the screening window lives through the tiles
+            const int ntiles = a.L.obj[item_at(it).obj].Mpad / COLS;
+            float win = win_cur, win_next = 0.f;
+            if (!kDblA) {
+                // the previous item's MMAs are complete (its last accumulator was waited for)
                 const FwdItem item = item_at(it);
-                const float4 fr = a.L.frame[item.obj];
-                ntiles = a.L.obj[item.obj].Mpad / COLS;
-                const long long g = item.q0 + tid;
-                float3 o = make_float3(0.f, 0.f, 0.f);
-                if (tid < item.nq) {
-                    const int pk = (int)(g / a.L.N), i = (int)(g - (long long)pk * a.L.N);
-                    const int pre = a.L.part_grp[pk] % a.L.P;
-                    const float *th = a.theta + (size_t)pk * 8;
-                    float Rm[9];
-                    quat_rot_f32(th[3], th[4], th[5], th[6], Rm);
-                    const float4 s = a.S[(size_t)pre * a.L.N + i];
-                    o = xform_f32(Rm, th[0], th[1], th[2], s.x, s.y, s.z);
-                }
-                // the query relative to the frame centre (a = fl(s' - c))
-                o = make_float3(__fsub_rn(o.x, fr.x), __fsub_rn(o.y, fr.y), __fsub_rn(o.z, fr.z));
-                // the previous item's MMAs are complete (its last accumulator was waited for);
-                // alpha = -2 lam a in two f16 parts, unless a part would leave the f16 range
-                const float lam = tc_scale(fr.w);
-                const float c[3] = {-2.f * lam * o.x, -2.f * lam * o.y, -2.f * lam * o.z};
-                const bool far = !(fabsf(c[0]) < 65000.f && fabsf(c[1]) < 65000.f && fabsf(c[2]) < 65000.f);
-                __half v[kAug];
-                for (int k = 0; k < kAug; ++k) v[k] = __float2half_rn(0.f);
-                if (!far) {
-                    for (int k = 0; k < 3; ++k) {
-                        const __half h = __float2half_rn(c[k]);
-                        v[k] = h; v[3 + k] = h; v[6 + k] = __float2half_rn(c[k] - __half2float(h));
-                    }
-                }
-                v[9] = v[10] = v[11] = __float2half_rn(4.f);
-                v[12] = __float2half_rn(32768.f);
-                for (int j = 0; j < kAug / 8; ++j) {
-                    uint4 pk;
-                    pk.x = (uint32_t)__half_as_ushort(v[8 * j + 0]) | ((uint32_t)__half_as_ushort(v[8 * j + 1]) << 16);
-                    pk.y = (uint32_t)__half_as_ushort(v[8 * j + 2]) | ((uint32_t)__half_as_ushort(v[8 * j + 3]) << 16);
-                    pk.z = (uint32_t)__half_as_ushort(v[8 * j + 4]) | ((uint32_t)__half_as_ushort(v[8 * j + 5]) << 16);
-                    pk.w = (uint32_t)__half_as_ushort(v[8 * j + 6]) | ((uint32_t)__half_as_ushort(v[8 * j + 7]) << 16);
-                    *reinterpret_cast<uint4 *>(sA + core_offset(row, 8 * j)) = pk;
-                }
+                win = build_query_row(a, item.q0 + tid, tid < item.nq, a.L.frame[item.obj], sA, row);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&afull);
-                const float an = sqrtf(o.x * o.x + o.y * o.y + o.z * o.z) * 1.001f;
-                // 2 delta_tc in lam^2 units (1 % margin for evaluating the bound in float32)
-                win = far ? __int_as_float(0x7f800000)
-                          : 2.02f * (5.9604645e-8f * lam * lam * (20.f * fr.w * fr.w + 61.f * an * fr.w) +
-                                     6.1035156e-5f * 1.74f * lam * (2.f * an + fr.w) + 2.45e-4f);
+                if (lane == 0) mbar_arrive(&afull[0]);
             }
             // the kTop best chunk minima (ascending) with their chunk ids, and the best of the rest
             float bk[kTop], brest = __int_as_float(0x7f800000);
@@ -369,11 +379,21 @@ __global__ void __launch_bounds__(kThreadsTc, 512 / COLS) fwd_match_tc_kernel(co
 #pragma unroll
                 for (int h = 0; h < kTileChunks; ++h) {
                     const uint32_t ta = tmem + lane_base + (uint32_t)(h * kChunk);
-                    mv[h] = LDX == 64 ? ld_min64(ta) : fminf(ld_min32(ta), ld_min32(ta + 32));
+                    mv[h] = ld_min64(ta);
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acce);
+                if (kDblA && t == 0 && it + step < it1) {
+                    // every MMA of the previous item is complete (this tile's commit tracks them
+                    // too), so the other row buffer may be rewritten for the next item
+                    const FwdItem nx = item_at(it + step);
+                    win_next = build_query_row(a, nx.q0 + tid, tid < nx.nq, a.L.frame[nx.obj],
+                                               sA + ((ia + 1) & 1) * kABytes, row);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&afull[(ia + 1) & 1]);
+                }
 #pragma unroll
                 for (int h = 0; h < kTileChunks; ++h) {
                     // insert (v, chunk gc); strict < keeps the earlier chunk first on equal minima
@@ -410,6 +430,7 @@ __global__ void __launch_bounds__(kThreadsTc, 512 / COLS) fwd_match_tc_kernel(co
                 }
                 a.cand[item.q0 + tid] = cd;
             }
+            win_cur = win_next;
         }
     }
 
@@ -559,14 +580,7 @@ __global__ void __launch_bounds__(256) tc_exact_kernel(const FwdArgs a)
     }
 }
 
-// The kernel's configuration: tile width (accumulator columns) and columns per load.
-#ifndef ASICP_TC_COLS
-#define ASICP_TC_COLS 256
-#endif
-#ifndef ASICP_TC_LDX
-#define ASICP_TC_LDX 64
-#endif
-constexpr int kTcCols = ASICP_TC_COLS, kTcLdx = ASICP_TC_LDX;
+constexpr int kTcCols = 256;               // the kernel's tile width (accumulator columns)
 
 // 512 / COLS CTAs per SM: each allocates COLS of the 512 tensor-memory columns,
 // and the shared-memory request leaves no room for more.
@@ -578,9 +592,9 @@ int fwd_tc_grid()
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(fwd_match_tc_kernel<kTcCols, kTcLdx>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(fwd_match_tc_kernel<kTcCols>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tc_smem_bytes<kTcCols>());
-        cudaFuncSetAttribute(fwd_match_tc_kernel<kTcCols, kTcLdx>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(fwd_match_tc_kernel<kTcCols>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
         return (512 / kTcCols) * sms;
     });
@@ -590,7 +604,7 @@ int fwd_tc_threads() { return kQueries; }
 
 cudaError_t launch_fwd_match_tc(const FwdArgs &a, cudaStream_t st)
 {
-    fwd_match_tc_kernel<kTcCols, kTcLdx><<<fwd_tc_grid(), kThreadsTc, tc_smem_bytes<kTcCols>(), st>>>(a);
+    fwd_match_tc_kernel<kTcCols><<<fwd_tc_grid(), kThreadsTc, tc_smem_bytes<kTcCols>(), st>>>(a);
     return cudaGetLastError();
 }
 
