@@ -37,11 +37,13 @@ sys.path.insert(0, ROOT)
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
 # DRAM bytes (read + write) of one launch of each forward-matching kernel from the committed ncu
-# captures of the profile case (profiles/fwd_match_kernel_profile-case-P1-K256-N2048-M8192.md,
-# profiles/fwd_match_tc_kernel_profile-case-P1-K256-N2048-M8192.md); every input is L2-resident, so
-# the figure holds for the paper-scale launch too.  None when the kernel has changed since the capture.
+# captures: the float32 kernel's from the profile case
+# (profiles/fwd_match_kernel_profile-case-P1-K256-N2048-M8192.md; every input is L2-resident, so the
+# figure holds for the paper-scale launch too), the tensor-core kernel's from a paper-scale launch
+# (profiles/fwd_match_tc_kernel_dram_paper-scale-P3-K256-N2048-M8192.md).  None when the kernel has
+# changed since the capture.
 FWD_DRAM_BYTES_PER_LAUNCH = 397568        # fwd_match_kernel (float32 shapes)
-TC_DRAM_BYTES_PER_LAUNCH = None           # fwd_match_tc_kernel (tensor-core shape)
+TC_DRAM_BYTES_PER_LAUNCH = 609280         # fwd_match_tc_kernel (tensor-core shape), paper-scale launch
 OPS_PER_PAIR = 4          # algorithmic FP32-lane work per particle*point pair: 3 FMA + 1 compare
 FMA_PER_PAIR = 3          # of which FMA-pipe work (the compare runs as half a 3-input min on the ALU pipe)
 TC_ALG_FLOP_PER_PAIR = 8  # tensor-core shape, algorithmic: |r|^2 - 2 s'.r as an augmented K = 4 contraction
@@ -361,8 +363,8 @@ def roofline_entry(tc, pairs_per_launch, match_avg_s, exact_avg_s, ms, sms, clk)
         return {"bound": "alu" if epi_bound <= tensor_bound else "tensor",
                 "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpairs/s", "frac": achieved / peak,
                 "traffic": TC_DRAM_BYTES_PER_LAUNCH,
-                "traffic_basis": "dram__bytes_read+write of one fwd_match_tc_kernel launch (ncu, profile case); "
-                                 "every input is L2-resident, so it does not grow with the launch",
+                "traffic_basis": "dram__bytes_read+write of one paper-scale fwd_match_tc_kernel launch (ncu, one "
+                                 "pass); the object tiles and gripper clouds are read once, L2-resident after",
                 "kernel": "fwd_match_tc_kernel",
                 "peak_basis": (f"min(tensor bound {tensor_bound / 1e9:.0f} Gpairs/s = {bf16:.0f} TFLOP/s ({bf16_basis}) / "
                                f"{TC_ALG_FLOP_PER_PAIR} flop per pair, epilogue bound {epi_bound / 1e9:.0f} Gpairs/s = "

@@ -78,9 +78,6 @@ __device__ __forceinline__ bool mbar_wait_warp_at(unsigned addr, unsigned parity
     if (!mbar_try_wait_at(addr, parity)) {
         const long long t0 = clock64();
         while (!mbar_try_wait_at(addr, parity)) {
-#ifdef ASICP_WAIT_SLEEP_NS
-            __nanosleep(ASICP_WAIT_SLEEP_NS);
-#endif
             if (clock64() - t0 > kWaitCycles) { ok = false; break; }
         }
     }

@@ -48,9 +48,13 @@
 // columns each) take turns on the tensor pipe and overlap one another's per-item
 // prologue.  The per-tile chain of handoffs (copy landed, MMA issue and commit,
 // completion seen by the reduction warps, tensor-memory loads, accumulator
-// released) sets the pace, not the tensor pipe: splitting a tile's MMA into parts
-// with their own commits, or reading the accumulator with more warps, measured
-// slower.  Every wait is bounded: on expiry the kernel reports ASICP_ERR_TIMEOUT
+// released) sets the pace, not the tensor pipe; every mbarrier wait (150-200 cycles
+// even on a completed phase), arrival, MMA issue or commit adds to it.  Measured
+// slower: splitting a tile's MMA into parts with their own commits, reading the
+// accumulator with more warps, narrower tiles with two or four accumulators per CTA
+// (each tile pays the fixed cost of a wait, a first load and a handoff), and the
+// reduction warps issuing the MMAs after a CTA barrier (the issue from a warp, and
+// the barrier, cost more than the dedicated thread's wake-up).  Every wait is bounded: on expiry the kernel reports ASICP_ERR_TIMEOUT
 // through the error word, drains its own copies and MMAs (bounded), frees its
 // tensor memory and returns.
 #include "asicp_internal.cuh"
@@ -75,17 +79,13 @@ constexpr int kTop = 4;                    // chunks per query the exact stage r
 constexpr unsigned kTileBytes = kCols * kAug * 2;       // 8 KB
 constexpr unsigned kABytes = kRows * kAug * 2;          // 4 KB of query rows
 constexpr unsigned kLBO = 128, kSBO = 256; // core matrices (8 rows x 16 B): K-adjacent 128 B, row groups 256 B
-#ifndef ASICP_TC_DBL_A
-#define ASICP_TC_DBL_A 0
-#endif
-constexpr bool kDblA = ASICP_TC_DBL_A != 0;  // two query-row buffers: the next item's rows written early
 static_assert(kRefTilePts % kCols == 0, "object padding must be whole tiles");
 static_assert(kCols % kChunk == 0, "whole chunks per tile");
 // The first COLS < kCols rows of a prepared tile are themselves a tile of COLS points in
 // the same layout (8-row groups are contiguous), so kernels with narrower tiles read
 // the same buffer.
 template <int COLS>
-constexpr size_t tc_smem_bytes() { return (size_t)(kDblA ? 2 : 1) * kABytes + (size_t)kStages * (COLS * kAug * 2); }
+constexpr size_t tc_smem_bytes() { return (size_t)kABytes + (size_t)kStages * (COLS * kAug * 2); }
 
 // byte offset of element (row, k) in the no-swizzle K-major layout
 __host__ __device__ constexpr unsigned core_offset(int row, int k) { return kmajor_offset(row, k, kLBO, kSBO); }
@@ -230,9 +230,9 @@ __global__ void __launch_bounds__(kThreadsTc, 512 / COLS) fwd_match_tc_kernel(co
     constexpr unsigned kTile = COLS * kAug * 2;
     constexpr int kTileChunks = COLS / kChunk;
     extern __shared__ __align__(1024) unsigned char smem_tc[];
-    unsigned char *sA = smem_tc;                               // [kDblA ? 2 : 1][kABytes]
-    unsigned char *sB = smem_tc + (kDblA ? 2 : 1) * kABytes;
-    __shared__ __align__(8) unsigned long long bfull[kStages], bempty[kStages], acce, afull[2];
+    unsigned char *sA = smem_tc;                               // [kABytes] query rows
+    unsigned char *sB = smem_tc + kABytes;                     // [kStages][kTile] object tiles
+    __shared__ __align__(8) unsigned long long bfull[kStages], bempty[kStages], acce, afull;
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -262,8 +262,7 @@ __global__ void __launch_bounds__(kThreadsTc, 512 / COLS) fwd_match_tc_kernel(co
         for (int s = 0; s < kStages; ++s) { mbar_init(&bfull[s], 1); mbar_init(&bempty[s], 1); }
         // one arrival per reduction warp (its lane 0, after the warp's loads or stores)
         mbar_init(&acce, kQueries / 32);
-        mbar_init(&afull[0], kQueries / 32);
-        mbar_init(&afull[1], kQueries / 32);
+        mbar_init(&afull, kQueries / 32);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) tc_alloc(&s_tmem, COLS);
@@ -309,9 +308,8 @@ __global__ void __launch_bounds__(kThreadsTc, 512 / COLS) fwd_match_tc_kernel(co
             int ia = 0;
             for (int it = it0; it < it1 && !s_abort; it += step, ++ia) {
                 const int ntiles = a.L.obj[item_at(it).obj].Mpad / COLS;
-                // with two row buffers item ia uses buffer ia % 2 (its phase ia / 2), else buffer 0
-                const int ab = kDblA ? (ia & 1) : 0;
-                if (!mbar_wait(&afull[ab], kDblA ? (unsigned)((ia >> 1) & 1) : (unsigned)(ia & 1))) { fail(); break; }
+                // the item's query rows are written
+                if (!mbar_wait(&afull, (unsigned)(ia & 1))) { fail(); break; }
                 tc_fence_after();
                 for (int t = 0; t < ntiles; ++t, ++seq) {
                     const int stage = c_stage;
@@ -320,7 +318,7 @@ __global__ void __launch_bounds__(kThreadsTc, 512 / COLS) fwd_match_tc_kernel(co
                         break;
                     }
                     tc_fence_after();
-                    const unsigned a0 = smem_u32(sA + ab * kABytes), b0 = smem_u32(sB + (size_t)stage * kTile);
+                    const unsigned a0 = smem_u32(sA), b0 = smem_u32(sB + (size_t)stage * kTile);
                     tc_mma_f16(tmem, smem_desc(a0), smem_desc(b0), kIdesc, 0u);
                     // one commit per tile: its completion frees the stage for the copy thread and
                     // hands the accumulator to the reduction warps
@@ -339,30 +337,16 @@ __global__ void __launch_bounds__(kThreadsTc, 512 / COLS) fwd_match_tc_kernel(co
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
         int r_stage = 0;          // stage and lap of the next tile, as on the MMA thread
         unsigned r_lap = 0u;
-        // the first item's query rows
-        float win_cur = 0.f;
-        if (kDblA) {
-            const FwdItem item = item_at(it0);
-            win_cur = build_query_row(a, item.q0 + tid, tid < item.nq, a.L.frame[item.obj], sA, row);
+        for (int it = it0; it < it1; it += step) {
+            if (__any_sync(0xffffffffu, s_abort)) break;
+            // the item's query rows (the previous item's MMAs are complete: its last
+            // accumulator was waited for); only the screening window lives through the tiles
+            const int ntiles = a.L.obj[item_at(it).obj].Mpad / COLS;
+            const FwdItem item = item_at(it);
+            const float win = build_query_row(a, item.q0 + tid, tid < item.nq, a.L.frame[item.obj], sA, row);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(&afull[0]);
-        }
-        int ia = 0;
-        for (int it = it0; it < it1; it += step, ++ia) {
-            if (__any_sync(0xffffffffu, s_abort)) break;
-            // the item's query rows (built here, or during the previous item with two row
-            // buffers); only the screening window lives through the tiles
-            const int ntiles = a.L.obj[item_at(it).obj].Mpad / COLS;
-            float win = win_cur, win_next = 0.f;
-            if (!kDblA) {
-                // the previous item's MMAs are complete (its last accumulator was waited for)
-                const FwdItem item = item_at(it);
-                win = build_query_row(a, item.q0 + tid, tid < item.nq, a.L.frame[item.obj], sA, row);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&afull[0]);
-            }
+            if (lane == 0) mbar_arrive(&afull);
             // the kTop best chunk minima (ascending) with their chunk ids, and the best of the rest
             float bk[kTop], brest = __int_as_float(0x7f800000);
             int ck[kTop];
@@ -384,16 +368,6 @@ __global__ void __launch_bounds__(kThreadsTc, 512 / COLS) fwd_match_tc_kernel(co
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acce);
-                if (kDblA && t == 0 && it + step < it1) {
-                    // every MMA of the previous item is complete (this tile's commit tracks them
-                    // too), so the other row buffer may be rewritten for the next item
-                    const FwdItem nx = item_at(it + step);
-                    win_next = build_query_row(a, nx.q0 + tid, tid < nx.nq, a.L.frame[nx.obj],
-                                               sA + ((ia + 1) & 1) * kABytes, row);
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&afull[(ia + 1) & 1]);
-                }
 #pragma unroll
                 for (int h = 0; h < kTileChunks; ++h) {
                     // insert (v, chunk gc); strict < keeps the earlier chunk first on equal minima
@@ -417,7 +391,6 @@ __global__ void __launch_bounds__(kThreadsTc, 512 / COLS) fwd_match_tc_kernel(co
             // the chunks that can hold the nearest point (within 2 delta_tc of the best), or
             // the whole cloud when more than kTop qualify; tc_exact_kernel rescans them
             const float thr = bk[0] + win;
-            const FwdItem item = item_at(it);
             if (tid < item.nq) {
                 int4 cd;
                 if (brest <= thr) {
@@ -430,7 +403,6 @@ __global__ void __launch_bounds__(kThreadsTc, 512 / COLS) fwd_match_tc_kernel(co
                 }
                 a.cand[item.q0 + tid] = cd;
             }
-            win_cur = win_next;
         }
     }
 
