@@ -84,6 +84,9 @@ def parse():
     ap.add_argument("--profile-proposal", action="store_true",
                     help="one forward and one loss/gradient pass of the proposal network on 32 clouds of 2048 points "
                          "(for profiler captures); no JSON line")
+    ap.add_argument("--oracle-configs", action="store_true",
+                    help="time the FP64 oracle on the host cores for configurations 1-4 (1 and 2 in full, 3 on two "
+                         "objects x 10 iterations, 4 on one iteration; the partial ones extrapolated and labelled)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one short run of a reduced workload (1 preshape x 256 particles, N=2048, M=8192, "
                          "8 iterations, poses close enough to collide) for profiler captures; no JSON line")
@@ -212,6 +215,90 @@ def run_reference(args, rank, world):
             "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": nthreads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def host_cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_timed_run(pre, obj_points, K, k_max, k_stein, schedule, nthreads, iters, evaluate):
+    """One FP64 oracle run from the Fibonacci shell: `iters` iterations (and the final evaluation
+    when evaluate is set); returns (seconds, forward pairs)."""
+    import oracle
+    P, N, M = len(pre), pre[0].S.shape[0], len(obj_points)
+    orc = oracle.Oracle(np.stack([p.S for p in pre]), [(p.sdf, p.origin, p.voxel) for p in pre], obj_points, K=K)
+    th = np.tile(oracle.fibonacci_init(K, orc.R.mean(0), 0.15), (P, 1)).reshape(P, K, 7)
+    sched = orc.schedule(k_max=k_max, k_stein=k_stein, schedule=schedule, N=N)
+    st = orc.new_state(th)
+    t0 = time.perf_counter()
+    for k in range(iters):
+        orc.step(st, sched, k, nthreads)
+    if evaluate:
+        orc.evaluate(st, nthreads)
+    return time.perf_counter() - t0, P * K * N * M * (iters + (1 if evaluate else 0))
+
+
+def run_oracle_configs(args):
+    """--oracle-configs: the FP64 oracle's time per configuration on this host's cores."""
+    import oracle
+    from paper_2412_08346_gb300 import synth
+    oracle.build()
+    cores = os.cpu_count() or 1
+    rows = []
+
+    def add(config, what, threads, secs, pairs, scale, full_pairs):
+        rows.append({"config": config, "timed": what, "threads": threads, "seconds": secs,
+                     "pairs_per_s": pairs / secs, "full_run_pairs": full_pairs,
+                     "full_run_seconds": secs * scale, "extrapolated": scale != 1.0})
+
+    # config 1: the small box case in full (50 SVGD iterations + the final evaluation)
+    w = synth.small_box_case()
+    for thr in (1, cores):
+        secs, pairs = oracle_timed_run(w.preshapes, w.objects[0].points, w.K, w.k_max, w.k_stein, w.schedule,
+                                       thr, w.k_max, True)
+        add(1, f"{w.name}, in full", thr, secs, pairs, 1.0, pairs)
+    # config 2: the paper-scale grasp set in full on every core; one thread on 2 iterations
+    w = synth.paper_scale_case()
+    secs, pairs = oracle_timed_run(w.preshapes, w.objects[0].points, w.K, w.k_max, w.k_stein, w.schedule,
+                                   cores, w.k_max, True)
+    add(2, f"{w.name}, in full", cores, secs, pairs, 1.0, pairs)
+    full = pairs
+    secs, pairs = oracle_timed_run(w.preshapes, w.objects[0].points, w.K, w.k_max, w.k_stein, w.schedule,
+                                   1, 2, False)
+    add(2, f"{w.name}, 2 iterations", 1, secs, pairs, full / pairs, full)
+    # config 3: two objects of the batched case, every preshape with its own particle count, 10 iterations
+    wb, Kb = synth.batched_case(64)
+    secs, pairs, full = 0.0, 0, 0
+    for o in range(2):
+        for p in range(len(wb.preshapes)):
+            s_, p_ = oracle_timed_run([wb.preshapes[p]], wb.objects[o].points, int(Kb[o, p]), wb.k_max,
+                                      wb.k_stein, wb.schedule, cores, 10, False)
+            secs += s_
+            pairs += p_
+            full += p_ // 10 * (wb.k_max + 1)
+    add(3, f"2 of the 64 objects of {wb.name}, 10 iterations", cores, secs, pairs, full / pairs, full)
+    # config 4: the largest workload, one iteration
+    w = synth.large_case(k_max=100)
+    secs, pairs = oracle_timed_run(w.preshapes, w.objects[0].points, w.K, w.k_max, w.k_stein, w.schedule,
+                                   cores, 1, False)
+    add(4, f"{w.name}, 1 iteration", cores, secs, pairs, 101.0, pairs * 101)
+    line = {"metric": "FP64 oracle time per configuration on the host cores", "unit": "s", "kind": "oracle",
+            "cpu": host_cpu_model(), "cores": cores, "dtype": "f64", "data": "synthetic", "configs": rows}
     print(json.dumps(line), flush=True)
 
 
@@ -799,6 +886,9 @@ def main():
         return
     if args.k_sweep:
         run_k_sweep(args)
+        return
+    if args.oracle_configs:
+        run_oracle_configs(args)
         return
     if args.profile_case:
         run_profile_case(args)
