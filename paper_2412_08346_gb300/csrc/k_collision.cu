@@ -13,6 +13,8 @@ constexpr int kColThreads = 256;       // reverse matching
 constexpr int kTestThreads = 128;      // collision test: one CTA per particle, small enough that every
                                        // particle of a paper-scale launch is resident at once
 constexpr int kColU = 4;          // collision points per thread per compaction round
+constexpr int kPairB = 4;         // matching pairs per thread whose loads overlap (57.5 us per paper-scale
+                                  // launch against 61.8 us one pair at a time; 72 registers, 7 CTAs per SM)
 
 // Trilinear interpolation of a node-centred grid at gripper-frame point (x, y, z).
 // Returns false when the point lies outside the grid's node box (the grid covers
@@ -90,9 +92,7 @@ __global__ void __launch_bounds__(kTestThreads) collide_kernel(const CollideArgs
         for (int c = 0; c < kFwdSums; ++c) acc[c] = dfloat{0.f, 0.f};
         const float4 *S = a.S + (size_t)p * N;
         const int *idx = a.nn_idx + (size_t)pk * N;
-        for (int i = threadIdx.x; i < N; i += kTestThreads) {
-            const float4 s = S[i];
-            const float4 r = __ldg(om.R + idx[i]);
+        auto add_pair = [&](float4 r, float4 s) {
             const float rv[3] = {r.x, r.y, r.z}, sv[3] = {s.x, s.y, s.z};
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
@@ -101,7 +101,21 @@ __global__ void __launch_bounds__(kTestThreads) collide_kernel(const CollideArgs
                 for (int v = 0; v < 3; ++v) df_add_prod(acc[3 + 3 * u + v], rv[u], sv[v]);
                 df_add_prod(acc[12], rv[u], rv[u]);
             }
+        };
+        // kPairB pairs per thread at a time: their index loads, then their object-point loads,
+        // are in flight together (the pairs are still added in the same order)
+        int i = threadIdx.x;
+        for (; i + (kPairB - 1) * kTestThreads < N; i += kPairB * kTestThreads) {
+            int id[kPairB];
+            float4 s[kPairB], r[kPairB];
+#pragma unroll
+            for (int u = 0; u < kPairB; ++u) { id[u] = idx[i + u * kTestThreads]; s[u] = S[i + u * kTestThreads]; }
+#pragma unroll
+            for (int u = 0; u < kPairB; ++u) r[u] = __ldg(om.R + id[u]);
+#pragma unroll
+            for (int u = 0; u < kPairB; ++u) add_pair(r[u], s[u]);
         }
+        for (; i < N; i += kTestThreads) add_pair(__ldg(om.R + idx[i]), S[i]);
         block_reduce_store<kFwdSums>(acc, sred, a.fsums + (size_t)pk * kFwdSums);
     }
 
@@ -342,75 +356,79 @@ __global__ void __launch_bounds__(kColThreads) collide_nn_kernel(const CollideAr
         for (int w8 = 0; w8 < kWarps; ++w8) sm2 = fmaxf(sm2, s_smax[w8]);
         const float smax = sqrtf(sm2) * 1.0001f;
 
-        // 1. screening of this warp's colliding points, lane l over chunk l
-        unsigned long long qx[kQW], qy[kQW], qz[kQW];
-        float cm[kQW];
-#pragma unroll
-        for (int q = 0; q < kQW; ++q) {
-            const float4 c = sC[warp * kQW + q];
-            const float ax = __fsub_rn(c.x, tx), ay = __fsub_rn(c.y, ty), az = __fsub_rn(c.z, tz);
-            qx[q] = pk2(ax, ax); qy[q] = pk2(ay, ay); qz[q] = pk2(az, az);
-            cm[q] = __int_as_float(0x7f800000);
-        }
-        for (int m = 0; m < slots; ++m) {
-            const ulonglong2 A = sXA[m * 32 + lane];
-            const ulonglong2 B = sXB[m * 32 + lane];
-#pragma unroll
-            for (int q = 0; q < kQW; ++q) {
-                const unsigned long long d = ffma2(qx[q], A.x, ffma2(qy[q], A.y, ffma2(qz[q], B.x, B.y)));
-                float d0, d1;
-                upk2(d, d0, d1);
-                cm[q] = fmin3(cm[q], d0, d1);
-            }
-        }
-        // best chunk l1 (lowest lane on ties) and whether another chunk may hold the nearest point
+        // colliding points of this warp (warp-uniform): a warp whose eight slots are all past the
+        // particle's count (the padding of its last item) skips the matching; its records are zeros
         const int g = lane >> 2, gs = lane & 3;       // lane group g works on colliding point g
-        int my_l1 = 0;
-        unsigned full_scan = 0u;
-#pragma unroll
-        for (int q = 0; q < kQW; ++q) {
-            const unsigned key = ord_key(cm[q]);
-            const unsigned k1 = __reduce_min_sync(0xffffffffu, key);
-            const int l1 = __ffs(__ballot_sync(0xffffffffu, key == k1)) - 1;
-            const unsigned k2 = __reduce_min_sync(0xffffffffu, lane == l1 ? 0xffffffffu : key);
-            const float4 c = sC[warp * kQW + q];
-            const float ax = __fsub_rn(c.x, tx), ay = __fsub_rn(c.y, ty), az = __fsub_rn(c.z, tz);
-            const float cn = sqrtf(ax * ax + ay * ay + az * az) * 1.001f;
-            const float win = 2.02f * 5.9604645e-8f * (9.f * smax * smax + 10.1f * cn * smax);
-            if (key_val(k2) <= key_val(k1) + win) full_scan |= 1u << q;
-            if (g == q) my_l1 = l1;
-        }
-        // 2. exact choice: four lanes per colliding point over its chunk l1
         const float4 cq = sC[warp * kQW + g];
         float best = __int_as_float(0x7f800000);
         int bi = 0x7fffffff;
-        for (int k = gs; k < KC; k += 4) {
-            const int r = my_l1 + 32 * k;
-            if (r >= N) break;
-            const float4 e = sE[my_l1 * KCs + k];
-            const float d = dist2_f32(e.x, e.y, e.z, cq.x, cq.y, cq.z);
-            if (d < best) { best = d; bi = r; }
-        }
-        argmin_xor(best, bi, 1);
-        argmin_xor(best, bi, 2);
-        if (bi >= N) bi = 0;     // no finite distance at all (not reached with finite inputs)
-        // rare: the whole cloud, lane l over chunk l
-        while (full_scan) {
-            const int q = __ffs(full_scan) - 1;
-            full_scan &= full_scan - 1;
-            const float4 c = sC[warp * kQW + q];
-            float fb = __int_as_float(0x7f800000);
-            int fi = 0x7fffffff;
-            for (int k = 0; k < KC; ++k) {
-                const int r = lane + 32 * k;
-                if (r >= N) break;
-                const float4 e = sE[lane * KCs + k];
-                const float d = dist2_f32(e.x, e.y, e.z, c.x, c.y, c.z);
-                if (d < fb) { fb = d; fi = r; }
-            }
+        if (l0 + warp * kQW < n) {
+            // 1. screening of this warp's colliding points, lane l over chunk l
+            unsigned long long qx[kQW], qy[kQW], qz[kQW];
+            float cm[kQW];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) argmin_xor(fb, fi, o);
-            if (g == q) { best = fb; bi = fi < N ? fi : 0; }
+            for (int q = 0; q < kQW; ++q) {
+                const float4 c = sC[warp * kQW + q];
+                const float ax = __fsub_rn(c.x, tx), ay = __fsub_rn(c.y, ty), az = __fsub_rn(c.z, tz);
+                qx[q] = pk2(ax, ax); qy[q] = pk2(ay, ay); qz[q] = pk2(az, az);
+                cm[q] = __int_as_float(0x7f800000);
+            }
+            for (int m = 0; m < slots; ++m) {
+                const ulonglong2 A = sXA[m * 32 + lane];
+                const ulonglong2 B = sXB[m * 32 + lane];
+#pragma unroll
+                for (int q = 0; q < kQW; ++q) {
+                    const unsigned long long d = ffma2(qx[q], A.x, ffma2(qy[q], A.y, ffma2(qz[q], B.x, B.y)));
+                    float d0, d1;
+                    upk2(d, d0, d1);
+                    cm[q] = fmin3(cm[q], d0, d1);
+                }
+            }
+            // best chunk l1 (lowest lane on ties) and whether another chunk may hold the nearest point
+            int my_l1 = 0;
+            unsigned full_scan = 0u;
+#pragma unroll
+            for (int q = 0; q < kQW; ++q) {
+                const unsigned key = ord_key(cm[q]);
+                const unsigned k1 = __reduce_min_sync(0xffffffffu, key);
+                const int l1 = __ffs(__ballot_sync(0xffffffffu, key == k1)) - 1;
+                const unsigned k2 = __reduce_min_sync(0xffffffffu, lane == l1 ? 0xffffffffu : key);
+                const float4 c = sC[warp * kQW + q];
+                const float ax = __fsub_rn(c.x, tx), ay = __fsub_rn(c.y, ty), az = __fsub_rn(c.z, tz);
+                const float cn = sqrtf(ax * ax + ay * ay + az * az) * 1.001f;
+                const float win = 2.02f * 5.9604645e-8f * (9.f * smax * smax + 10.1f * cn * smax);
+                if (key_val(k2) <= key_val(k1) + win) full_scan |= 1u << q;
+                if (g == q) my_l1 = l1;
+            }
+            // 2. exact choice: four lanes per colliding point over its chunk l1
+            for (int k = gs; k < KC; k += 4) {
+                const int r = my_l1 + 32 * k;
+                if (r >= N) break;
+                const float4 e = sE[my_l1 * KCs + k];
+                const float d = dist2_f32(e.x, e.y, e.z, cq.x, cq.y, cq.z);
+                if (d < best) { best = d; bi = r; }
+            }
+            argmin_xor(best, bi, 1);
+            argmin_xor(best, bi, 2);
+            if (bi >= N) bi = 0;     // no finite distance at all (not reached with finite inputs)
+            // rare: the whole cloud, lane l over chunk l
+            while (full_scan) {
+                const int q = __ffs(full_scan) - 1;
+                full_scan &= full_scan - 1;
+                const float4 c = sC[warp * kQW + q];
+                float fb = __int_as_float(0x7f800000);
+                int fi = 0x7fffffff;
+                for (int k = 0; k < KC; ++k) {
+                    const int r = lane + 32 * k;
+                    if (r >= N) break;
+                    const float4 e = sE[lane * KCs + k];
+                    const float d = dist2_f32(e.x, e.y, e.z, c.x, c.y, c.z);
+                    if (d < fb) { fb = d; fi = r; }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) argmin_xor(fb, fi, o);
+                if (g == q) { best = fb; bi = fi < N ? fi : 0; }
+            }
         }
         if (gs == 0) {
             const int j = warp * kQW + g;

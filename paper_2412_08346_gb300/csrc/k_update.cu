@@ -33,13 +33,14 @@ __device__ void residual_moments(const double R[9], const double t[3], double n,
                                  const double SS[9], const double xs[3], const double XS[9], double xx,
                                  double *se2, double Se[3], double E[9])
 {
-    double Rs[3], RtR[9];
+    double Rs[3];
     for (int a = 0; a < 3; ++a) Rs[a] = R[a * 3 + 0] * ss[0] + R[a * 3 + 1] * ss[1] + R[a * 3 + 2] * ss[2];
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-            RtR[a * 3 + b] = R[0 * 3 + a] * R[0 * 3 + b] + R[1 * 3 + a] * R[1 * 3 + b] + R[2 * 3 + a] * R[2 * 3 + b];
-    double quad = 0.0, cross = 0.0;
-    for (int a = 0; a < 9; ++a) { quad += RtR[a] * SS[a]; cross += R[a] * XS[a]; }
+    // R is the homogeneous form of the quaternion's rotation (|q|^2 times a rotation), so
+    // R^T R = |q|^4 I and sum_i |R s_i|^2 = |q|^4 tr(SS); |q|^4 is the squared norm of a column
+    const double q4 = R[0] * R[0] + R[3] * R[3] + R[6] * R[6];
+    const double quad = q4 * (SS[0] + SS[4] + SS[8]);
+    double cross = 0.0;
+    for (int a = 0; a < 9; ++a) cross += R[a] * XS[a];
     const double tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
     const double tRs = t[0] * Rs[0] + t[1] * Rs[1] + t[2] * Rs[2];
     const double tx = t[0] * xs[0] + t[1] * xs[1] + t[2] * xs[2];
