@@ -60,7 +60,11 @@ typedef enum {
  *   init_radius   radius of the Fibonacci-sphere initial poses around the CoM (Section V)
  *   debug         1: keep per-query correspondences, transformed points and collision
  *                  lists so asicp_get_state can return them (costs memory and bandwidth)
- *   profile       1: time the main kernels with CUDA events (asicp_kernel_times)
+ *   profile       1: time the main kernels with CUDA events (asicp_kernel_times);
+ *                  2: time the forward-matching (screening) kernel only.  The events
+ *                  are nodes of the captured iteration loop and add a few
+ *                  microseconds each to a pass (profile 1: ~5 % of a paper-scale
+ *                  grasp set on GB300)
  *   cuda_stream   cudaStream_t for all work, NULL for the default stream
  *   n_objects     objects optimised together in one pass (one grasp set each, default 1);
  *                  every kernel covers all of them, each particle matched against its
@@ -239,7 +243,8 @@ asicp_status asicp_best_grasps_at(asicp_ctx *ctx, int object, int topk, float *t
 asicp_status asicp_get_state(asicp_ctx *ctx, const asicp_state_view *view);
 
 /* With config.profile = 1: accumulated device time (ms) and launch count of the
- * path's kernels since the last reset.  ms[ASICP_KERNEL_KINDS] / launches[...]
+ * path's kernels since the last reset (profile = 2: the forward-matching entry
+ * only, the others stay 0).  ms[ASICP_KERNEL_KINDS] / launches[...]
  * order: forward matching (screening; with the float32 shapes also the exact
  * choice), collision test (with the matching sums), reverse matching, finalize
  * (cost, gradient, convergence, SGD step), Stein (SVGD step: the Stein direction

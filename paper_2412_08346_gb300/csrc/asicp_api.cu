@@ -387,13 +387,16 @@ void timed(asicp_ctx *c, int kind, L &&launch, const char *what)
     // inside a capture, an external record makes the event a graph node that every
     // replay records (a plain record would only express a capture dependency)
     const unsigned flags = c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-    if (c->cfg.profile) {
+    // profile 1: every kernel; 2: the forward-matching (screening) kernel only.  Each event
+    // record is a node of the captured loop and costs a few microseconds of the replay.
+    const bool on = c->cfg.profile == 1 || (c->cfg.profile == 2 && kind == kTimeMatch);
+    if (on) {
         a = c->take_event();
         b = c->take_event();
         ck(cudaEventRecordWithFlags(a, st, flags), "cudaEventRecord");
     }
     ck(launch(st), what);
-    if (c->cfg.profile) {
+    if (on) {
         ck(cudaEventRecordWithFlags(b, st, flags), "cudaEventRecord");
         (c->capturing ? c->graph_events : c->events).push_back({kind, a, b});
     }

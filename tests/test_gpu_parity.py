@@ -415,6 +415,29 @@ def test_kernel_times_from_graph_replays(stream):
         assert all(t > 0 for t, c in zip(ms, n) if c)
 
 
+def test_kernel_times_of_the_matching_kernel_only(stream):
+    """profile = 2 times the forward-matching kernel alone (one launch per pass); the other kernels
+    run untimed, and the results equal those of an untimed context."""
+    w = synth.custom_case(P=1, K=8, N=128, M=600, grid=16, k_max=3, seed=41)
+    shape = asicp.FWD_SHAPES - 1
+    out = []
+    for prof in (0, 2):
+        ctx = _ctx(w, stream, debug=False, profile=prof, fwd_shape=shape)
+        try:
+            keep = tl.upload(ctx, w)
+            for _ in range(2):
+                asicp.asicp_run(ctx)
+            if prof:
+                ms, n = asicp.asicp_kernel_times(ctx, reset=True)
+            out.append(tl.read_theta(ctx, w.K))
+            del keep
+        finally:
+            asicp.asicp_destroy(ctx)
+    assert n == [2 * (w.k_max + 1), 0, 0, 0, 0, 0]
+    assert ms[0] > 0 and ms[1:] == [0.0] * 5
+    assert np.array_equal(out[0], out[1])
+
+
 def _uneven_batch(seed=43):
     """4 objects with uneven point counts and per-(object, preshape) particle counts."""
     g = np.random.default_rng(seed)
