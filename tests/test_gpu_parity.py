@@ -995,8 +995,9 @@ def test_translated_object_matches_oracle_and_keeps_screening_cost(stream):
     """An object cloud far from the coordinate origin (translated by (0.5, 0.3, 0.8) m, as a camera- or
     robot-frame capture would be): teacher-forced SVGD and SGD steps with both matching shapes equal
     the oracle's, and the screening stays as selective as for the centred cloud -- the error windows
-    are measured from the object's own frame centre, so the tensor-core launch takes about the same
-    time (within 25 %) as for the same cloud at the origin."""
+    are measured from the object's own frame centre, so the tensor-core screening and exact choice
+    take the same time (within 5 %; measured within 0.2 % on GB300) as for the same cloud at the
+    origin: the exact choice would rescan far more chunks if the windows grew."""
     import oracle
     shift = np.array([0.5, 0.3, 0.8], np.float32)
     w0 = synth.custom_case(P=1, K=128, N=2048, M=8192, grid=32, k_max=4, seed=61, k_stein=2)
@@ -1039,7 +1040,7 @@ def test_translated_object_matches_oracle_and_keeps_screening_cost(stream):
         finally:
             asicp.asicp_destroy(ctx)
     print(f"matching per launch: centred {times[0]:.4f} ms, translated {times[1]:.4f} ms")
-    assert times[1] <= 1.25 * times[0]
+    assert times[1] <= 1.05 * times[0]
 
 
 def test_bounded_wait_timeout_is_reported_and_the_context_recovers(stream):
