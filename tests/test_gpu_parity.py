@@ -627,7 +627,7 @@ def _step_indices(w, stream, theta0, shape, k=0):
 
 
 def test_tensor_core_matching_equals_float32_matching(stream):
-    """The tensor-core kernel (split-TF32 screening + exact choice) against the float32 kernel at the
+    """The tensor-core kernel (split-f16 screening + exact choice) against the float32 kernel at the
     paper's N and M (3 preshapes x 64 particles, N=2048, M=8192; 1.2e6 queries): identical indices
     except near-ties (|d2 difference| <= 1e-6 relative in float64), and ties broken alike."""
     w = synth.custom_case(P=3, K=64, N=2048, M=8192, grid=32, k_max=2, seed=synth.BASE_SEED + 2)
