@@ -86,7 +86,7 @@ def parse():
                          "(for profiler captures); no JSON line")
     ap.add_argument("--oracle-configs", action="store_true",
                     help="time the FP64 oracle on the host cores for configurations 1-4 (1 and 2 in full, 3 on two "
-                         "objects x 10 iterations, 4 on one iteration; the partial ones extrapolated and labelled)")
+                         "objects in full, 4 on 10 of its 100 iterations, extrapolated and labelled)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one short run of a reduced workload (1 preshape x 256 particles, N=2048, M=8192, "
                          "8 iterations, poses close enough to collide) for profiler captures; no JSON line")
@@ -281,22 +281,21 @@ def run_oracle_configs(args):
     secs, pairs = oracle_timed_run(w.preshapes, w.objects[0].points, w.K, w.k_max, w.k_stein, w.schedule,
                                    1, 2, False)
     add(2, f"{w.name}, 2 iterations", 1, secs, pairs, full / pairs, full)
-    # config 3: two objects of the batched case, every preshape with its own particle count, 10 iterations
+    # config 3: two objects of the batched case in full, every preshape with its own particle count
     wb, Kb = synth.batched_case(64)
-    secs, pairs, full = 0.0, 0, 0
+    secs, pairs = 0.0, 0
     for o in range(2):
         for p in range(len(wb.preshapes)):
             s_, p_ = oracle_timed_run([wb.preshapes[p]], wb.objects[o].points, int(Kb[o, p]), wb.k_max,
-                                      wb.k_stein, wb.schedule, cores, 10, False)
+                                      wb.k_stein, wb.schedule, cores, wb.k_max, True)
             secs += s_
             pairs += p_
-            full += p_ // 10 * (wb.k_max + 1)
-    add(3, f"2 of the 64 objects of {wb.name}, 10 iterations", cores, secs, pairs, full / pairs, full)
-    # config 4: the largest workload, one iteration
+    add(3, f"2 of the 64 objects of {wb.name}, in full", cores, secs, pairs, 1.0, pairs)
+    # config 4: the largest workload, 10 of its 100 iterations
     w = synth.large_case(k_max=100)
     secs, pairs = oracle_timed_run(w.preshapes, w.objects[0].points, w.K, w.k_max, w.k_stein, w.schedule,
-                                   cores, 1, False)
-    add(4, f"{w.name}, 1 iteration", cores, secs, pairs, 101.0, pairs * 101)
+                                   cores, 10, False)
+    add(4, f"{w.name}, 10 iterations", cores, secs, pairs, 10.1, pairs * 101 // 10)
     line = {"metric": "FP64 oracle time per configuration on the host cores", "unit": "s", "kind": "oracle",
             "cpu": host_cpu_model(), "cores": cores, "dtype": "f64", "data": "synthetic", "configs": rows}
     print(json.dumps(line), flush=True)
